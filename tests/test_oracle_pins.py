@@ -1,0 +1,359 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle.
+
+Each test ties one part of the oracle to something fixed outside it: a
+library routine (scipy.signal.convolve2d / correlate2d, torch conv2d,
+scipy.optimize.nnls), a dense matrix built from library convolutions of unit
+vectors, the adjoint identity, closed forms (delta-PSF coadd), fixed points
+(noise-free truth), and the invariants of Sec. 2 (non-negativity,
+order-independence, the monotone likelihood of EM). A dropped term, a wrong
+sign or index or a transposed operand in the oracle fails at least one.
+"""
+import numpy as np
+import pytest
+import scipy.signal as ss
+from scipy.optimize import nnls
+
+import oracle
+import synth
+
+
+def rng(s=0):
+    return np.random.default_rng(s)
+
+
+def rand_psf(K, g, positive=True):
+    f = g.uniform(0.0, 1.0, (K, K)) if positive else g.standard_normal((K, K))
+    return f / np.abs(f).sum()
+
+
+# -- convolution conventions (Eq. (1)) ----------------------------------------
+
+@pytest.mark.parametrize("H,W,K", [(9, 7, 1), (9, 7, 3), (12, 17, 5),
+                                   (16, 11, 15), (5, 6, 9), (3, 4, 7)])
+def test_conv_matches_scipy_convolve2d(H, W, K):
+    g = rng(H * 100 + K)
+    x = g.standard_normal((H, W))
+    f = g.standard_normal((K, K))
+    ref = ss.convolve2d(x, f, mode="same", boundary="fill")
+    np.testing.assert_allclose(oracle.conv_same(x, f), ref, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("H,W,K", [(9, 7, 3), (12, 17, 5), (16, 11, 15), (3, 4, 7)])
+def test_corr_matches_scipy_correlate2d(H, W, K):
+    g = rng(H * 10 + K)
+    w = g.standard_normal((H, W))
+    f = g.standard_normal((K, K))
+    ref = ss.correlate2d(w, f, mode="same", boundary="fill")
+    np.testing.assert_allclose(oracle.corr_same(w, f), ref, rtol=1e-13, atol=1e-13)
+
+
+def test_conv_matches_torch_conv2d_flipped():
+    torch = pytest.importorskip("torch")
+    g = rng(5)
+    x = g.standard_normal((20, 13))
+    f = g.standard_normal((7, 7))
+    # torch conv2d is a cross-correlation; a true convolution flips the kernel
+    ref = torch.nn.functional.conv2d(
+        torch.from_numpy(x)[None, None], torch.from_numpy(f[::-1, ::-1].copy())[None, None],
+        padding=3)[0, 0].numpy()
+    np.testing.assert_allclose(oracle.conv_same(x, f), ref, rtol=1e-13, atol=1e-13)
+    ref2 = torch.nn.functional.conv2d(
+        torch.from_numpy(x)[None, None], torch.from_numpy(f)[None, None],
+        padding=3)[0, 0].numpy()
+    np.testing.assert_allclose(oracle.corr_same(x, f), ref2, rtol=1e-13, atol=1e-13)
+
+
+def test_convolution_orientation_elliptical():
+    # an off-centre single tap moves flux in the direction of the tap offset
+    f = np.zeros((5, 5))
+    f[3, 4] = 1.0                      # tap at (+1, +2) from the centre
+    x = np.zeros((9, 9))
+    x[4, 4] = 1.0
+    z = oracle.conv_same(x, f)
+    assert z[5, 6] == 1.0 and z.sum() == 1.0
+
+
+# -- D^r of Eq. (3) -------------------------------------------------------------
+
+@pytest.mark.parametrize("r", [1, 2, 3])
+def test_downsample_is_block_sum_and_upsample_replicates(r):
+    g = rng(r)
+    zf = g.standard_normal((4 * r, 5 * r))
+    np.testing.assert_allclose(oracle.downsample(zf, r),
+                               zf.reshape(4, r, 5, r).sum(axis=(1, 3)), rtol=1e-14)
+    w = g.standard_normal((4, 5))
+    np.testing.assert_array_equal(oracle.upsample(w, r),
+                                  np.kron(w, np.ones((r, r))))
+
+
+# -- adjoint pair ----------------------------------------------------------------
+
+@pytest.mark.parametrize("K", [1, 3, 15, 43])
+@pytest.mark.parametrize("r", [1, 2])
+@pytest.mark.parametrize("H,W", [(13, 9), (6, 20)])
+def test_adjoint_identity(K, r, H, W):
+    g = rng(K * 7 + r + H)
+    x = g.standard_normal((r * H, r * W))
+    w = g.standard_normal((H, W))
+    f = g.standard_normal((K, K))
+    lhs = float(np.vdot(oracle.forward(x, f, r), w))
+    rhs = float(np.vdot(x, oracle.adjoint(w, f, r)))
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs), np.abs(x).sum())
+
+
+# -- dense brute force on 8x8 -----------------------------------------------------
+
+def dense_operator(H, W, f, r):
+    """A = D^r F as a dense (H W) x (rH rW) matrix from library convolutions of
+    unit vectors."""
+    Hf, Wf = r * H, r * W
+    A = np.zeros((H * W, Hf * Wf))
+    for k in range(Hf * Wf):
+        e = np.zeros(Hf * Wf)
+        e[k] = 1.0
+        z = ss.convolve2d(e.reshape(Hf, Wf), f, mode="same")
+        A[:, k] = synth.block_sum(z, r).ravel()
+    return A
+
+
+@pytest.mark.parametrize("K,r", [(3, 1), (5, 1), (3, 2), (5, 2)])
+def test_em_step_matches_dense_brute_force(K, r):
+    g = rng(K + 10 * r)
+    H = W = 8 // r
+    n = 3
+    f = np.stack([rand_psf(K, g) for _ in range(n)])
+    x = g.uniform(0.5, 2.0, (r * H, r * W))
+    y = g.normal(2.0, 1.0, (n, H, W))
+    v = g.uniform(0.5, 2.0, (n, H, W))
+    mask = (g.uniform(size=(n, H, W)) > 0.2).astype(np.uint8)
+    u, bad = oracle.weights(v, mask)
+    assert bad == 0
+    N = np.zeros(r * r * H * W)
+    Den = np.zeros(r * r * H * W)
+    for t in range(n):
+        A = dense_operator(H, W, f[t], r)
+        U = np.diag(u[t].ravel())
+        N += A.T @ U @ y[t].ravel()
+        Den += A.T @ U @ A @ x.ravel()
+    x_ref = np.where(Den > 0, x.ravel() * np.maximum(N, 0) / np.where(Den > 0, Den, 1), x.ravel())
+    yy = np.where(mask != 0, y, 0.0)
+    N_or = oracle.numerator(yy, u, f, r)
+    np.testing.assert_allclose(N_or.ravel(), N, rtol=1e-13, atol=1e-14)
+    x1, den = oracle.em_step(x, N_or, u, f, r, return_den=True)
+    np.testing.assert_allclose(den.ravel(), Den, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(x1.ravel(), x_ref, rtol=1e-13, atol=1e-14)
+
+
+# -- closed forms and fixed points --------------------------------------------------
+
+@pytest.mark.parametrize("K", [1, 5])
+def test_delta_psf_gives_weighted_coadd(K):
+    g = rng(K)
+    n, H, W = 4, 10, 12
+    f = np.zeros((n, K, K))
+    f[:, K // 2, K // 2] = 1.0
+    y = g.normal(1.0, 2.0, (n, H, W))          # includes negative data
+    v = g.uniform(0.5, 3.0, (n, H, W))
+    mask = (g.uniform(size=(n, H, W)) > 0.3).astype(np.uint8)
+    mask[:, 0, 0] = 0                           # pixel masked in every frame
+    y[mask == 0] = np.nan
+    u, _ = oracle.weights(v, mask, y)
+    yy = np.where(mask != 0, y, 0.0)
+    N = oracle.numerator(yy, u, f)
+    x0 = g.uniform(0.1, 5.0, (H, W))
+    x1 = oracle.em_step(x0, N, u, f)
+    su = u.sum(0)
+    coadd = np.where(su > 0, np.maximum((u * yy).sum(0), 0) / np.where(su > 0, su, 1), x0)
+    np.testing.assert_allclose(x1, coadd, rtol=1e-15, atol=0)
+    assert x1[0, 0] == x0[0, 0]
+    # a fixed point afterwards (zeros absorbed)
+    np.testing.assert_allclose(oracle.em_step(x1, N, u, f), x1, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("r,K", [(1, 7), (2, 9)])
+def test_noise_free_truth_is_fixed_point(r, K):
+    g = rng(3 + r)
+    n, H, W = 3, 12, 10
+    x_true = g.uniform(0.2, 3.0, (r * H, r * W))
+    f = np.stack([rand_psf(K, g) for _ in range(n)])
+    y = np.stack([synth.block_sum(ss.convolve2d(x_true, f[t], mode="same"), r)
+                  for t in range(n)])
+    v = g.uniform(1.0, 4.0, (n, H, W))
+    mask = (g.uniform(size=(n, H, W)) > 0.1).astype(np.uint8)
+    u, _ = oracle.weights(v, mask)
+    yy = np.where(mask != 0, y, 0.0)
+    N = oracle.numerator(yy, u, f, r)
+    x1 = oracle.em_step(x_true, N, u, f, r)
+    np.testing.assert_allclose(x1, x_true, rtol=1e-12)
+
+
+def small_problem(seed=0, H=40, W=36, n=3, K=7, r=1, mask_frac=0.1):
+    g = rng(seed)
+    x_true = synth.render_sky(r * H, r * W, 12, 2, g, mu=5.0, sigma=1.0,
+                              re_range=(1.5, 3.0))
+    f = np.stack([synth.moffat_psf(K, g.uniform(2, 3), 3.0) for _ in range(n)])
+    v = np.empty((n, H, W))
+    y = np.empty((n, H, W))
+    for t in range(n):
+        z = synth.block_sum(ss.convolve2d(x_true, f[t], mode="same"), r)
+        v[t] = 50.0 + np.maximum(z, 0)
+        y[t] = z + np.sqrt(v[t]) * g.standard_normal((H, W))
+    mask = (g.uniform(size=(n, H, W)) > mask_frac).astype(np.uint8)
+    y[mask == 0] = np.nan
+    return x_true, y, v, f, mask
+
+
+@pytest.mark.parametrize("r", [1, 2])
+def test_monotone_likelihood_and_nonnegativity(r):
+    x_true, y, v, f, mask = small_problem(seed=11 + r, r=r, H=32 // r * 2 // 2, W=28)
+    u, _ = oracle.weights(v, mask, y)
+    yy = np.where(mask != 0, y, 0.0)
+    assert (yy < 0).any()
+    N = oracle.numerator(yy, u, f, r)
+    x = np.full((r * y.shape[1], r * y.shape[2]), oracle.default_x0(yy, u, r))
+    ll_prev = oracle.loglik(x, yy, v, u, f, r)
+    iters = 200 if r == 1 else 80
+    for _ in range(iters):
+        x = oracle.em_step(x, N, u, f, r)
+        assert (x >= 0).all()
+        ll = oracle.loglik(x, yy, v, u, f, r)
+        assert ll >= ll_prev - 1e-12 * abs(ll_prev)
+        ll_prev = ll
+
+
+def test_scaling_and_permutation_equivariance():
+    x_true, y, v, f, mask = small_problem(seed=21)
+    u, _ = oracle.weights(v, mask, y)
+    yy = np.where(mask != 0, y, 0.0)
+    x0 = np.full(yy.shape[1:], 3.0)
+    N = oracle.numerator(yy, u, f)
+    xa = oracle.em_run(x0, N, u, f, 5)
+    # y, x0 -> 2^s (y, x0) scales every iterate by 2^s exactly
+    s = 2.0 ** 7
+    xb = oracle.em_run(x0 * s, oracle.numerator(yy * s, u, f), u, f, 5)
+    np.testing.assert_array_equal(xb, xa * s)
+    # v -> 2^s v leaves the iterates unchanged exactly
+    u2, _ = oracle.weights(v * 4.0, mask, y)
+    xc = oracle.em_run(x0, oracle.numerator(yy, u2, f), u2, f, 5)
+    np.testing.assert_array_equal(xc, xa)
+    # exposure order does not matter (Sec. 2: all frames at once)
+    p = [2, 0, 1]
+    xd = oracle.em_run(x0, oracle.numerator(yy[p], u[p], f[p]), u[p], f[p], 5)
+    np.testing.assert_allclose(xd, xa, rtol=1e-13)
+
+
+def test_shift_equivariance_interior():
+    g = rng(4)
+    n, K, H, W = 2, 5, 40, 40
+    f = np.stack([rand_psf(K, g) for _ in range(n)])
+    base = np.zeros((H, W))
+    base[15:22, 14:20] = g.uniform(1, 5, (7, 6))
+    res = []
+    for dy, dx in [(0, 0), (3, 2)]:
+        xt = np.roll(np.roll(base, dy, 0), dx, 1)
+        y = np.stack([ss.convolve2d(xt, f[t], mode="same") for t in range(n)])
+        u = np.full((n, H, W), 0.5)
+        N = oracle.numerator(y, u, f)
+        res.append(oracle.em_run(np.ones((H, W)), N, u, f, 2))
+    a = res[0][12:26, 12:26]
+    b = res[1][15:29, 14:28]
+    np.testing.assert_allclose(b, a, rtol=1e-14)
+
+
+def test_literal_weights_equal_inside_weights_for_constant_u():
+    g = rng(9)
+    n, H, W, K = 3, 14, 11, 5
+    f = np.stack([rand_psf(K, g) for _ in range(n)])
+    y = g.normal(3.0, 1.0, (n, H, W))
+    v = np.stack([np.full((H, W), g.uniform(0.5, 2.0)) for _ in range(n)])
+    u, _ = oracle.weights(v)
+    x0 = g.uniform(0.5, 1.5, (H, W))
+    a = oracle.em_step(x0, oracle.numerator(y, u, f), u, f)
+    b = oracle.em_step_literal(x0, y, u, f)
+    np.testing.assert_allclose(a, b, rtol=1e-13)
+
+
+def test_flux_of_forward_and_adjoint():
+    g = rng(12)
+    for r in (1, 2):
+        K = 7
+        f = rand_psf(K, g)
+        x = np.zeros((r * 20, r * 20))
+        x[r * 8:r * 12, r * 8:r * 12] = g.uniform(1, 2, (4 * r, 4 * r))
+        # D^r is a block SUM: flux is conserved by the forward model
+        assert abs(oracle.forward(x, f, r).sum() - x.sum()) < 1e-12 * x.sum()
+        w = np.zeros((20, 20))
+        w[8:12, 8:12] = g.uniform(1, 2, (4, 4))
+        assert abs(oracle.adjoint(w, f, r).sum() - r * r * w.sum()) < 1e-12 * w.sum()
+
+
+def test_em_converges_to_nnls_solution():
+    g = rng(17)
+    n, H, W = 2, 6, 6
+    f = np.zeros((n, 3, 3))
+    f[:, 1, 1] = 0.6
+    f[:, 0, 1] = f[:, 2, 1] = f[:, 1, 0] = f[:, 1, 2] = 0.1
+    x_true = g.uniform(0.0, 3.0, (H, W))
+    x_true[g.uniform(size=(H, W)) < 0.3] = 0.0
+    v = g.uniform(0.5, 2.0, (n, H, W))
+    y = np.stack([ss.convolve2d(x_true, f[t], mode="same") for t in range(n)])
+    y += 0.8 * g.standard_normal(y.shape)
+    u, _ = oracle.weights(v)
+    A = np.vstack([np.sqrt(u[t].ravel())[:, None] * dense_operator(H, W, f[t], 1)
+                   for t in range(n)])
+    b = np.concatenate([np.sqrt(u[t].ravel()) * y[t].ravel() for t in range(n)])
+    x_nnls, _ = nnls(A, b, maxiter=10000)
+    assert (x_nnls == 0).any()                  # the constraint is active
+    N = oracle.numerator(y, u, f)
+    x = oracle.em_run(np.ones((H, W)), N, u, f, 100000)
+    np.testing.assert_allclose(x.ravel(), x_nnls, rtol=1e-6, atol=1e-6)
+
+
+# -- likelihood, weights, initial guess ----------------------------------------------
+
+def test_loglik_matches_library_formula():
+    x_true, y, v, f, mask = small_problem(seed=5, r=1)
+    u, bad = oracle.weights(v, mask, y)
+    assert bad == 0
+    yy = np.where(mask != 0, y, 0.0)
+    x = np.abs(x_true) + 1.0
+    ref = 0.0
+    for t in range(y.shape[0]):
+        z = ss.convolve2d(x, f[t], mode="same")
+        m = mask[t] != 0
+        ref += ((y[t][m] - z[m]) ** 2 / v[t][m]).sum() + np.log(2 * np.pi * v[t][m]).sum()
+    np.testing.assert_allclose(oracle.loglik(x, yy, v, u, f), -0.5 * ref, rtol=1e-12)
+
+
+def test_weights_mask_and_validation():
+    v = np.array([[1.0, 2.0], [0.0, -1.0]])[None]
+    y = np.array([[1.0, np.nan], [3.0, 4.0]])[None]
+    m = np.array([[1, 0], [0, 1]], np.uint8)[None]
+    u, bad = oracle.weights(v, m, y)
+    np.testing.assert_array_equal(u[0], [[1.0, 0.0], [0.0, 0.0]])
+    assert bad == 1                             # v = -1 at a valid pixel
+    u2, bad2 = oracle.weights(np.abs(v) + 1, m, y)
+    assert bad2 == 0 and u2[0, 1, 0] == 0.0
+
+
+def test_default_x0_closed_form():
+    y = np.full((3, 4, 5), 6.0)
+    u = np.full((3, 4, 5), 0.25)
+    assert oracle.default_x0(y, u, 1) == 6.0
+    assert oracle.default_x0(y, u, 2) == 1.5
+    assert oracle.default_x0(-y, u, 1) == 1.0
+
+
+@pytest.mark.parametrize("r,K", [(1, 5), (2, 7)])
+def test_em_step_at_matches_full_step(r, K):
+    x_true, y, v, f, mask = small_problem(seed=30 + r, r=r, H=16, W=14, K=K)
+    u, _ = oracle.weights(v, mask, y)
+    yy = np.where(mask != 0, y, 0.0)
+    N = oracle.numerator(yy, u, f, r)
+    x0 = np.abs(x_true) + 0.5
+    x1, den = oracle.em_step(x0, N, u, f, r, return_den=True)
+    idx = np.array([0, 5, x0.size // 2 + 3, x0.size - 1, x0.shape[1] * 3 + 1])
+    xo, No, Do = oracle.em_step_at(x0, y, u, f, idx, r)   # NaN y where masked
+    np.testing.assert_allclose(Do, den.ravel()[idx], rtol=1e-12)
+    np.testing.assert_allclose(No, N.ravel()[idx], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(xo, x1.ravel()[idx], rtol=1e-12)
