@@ -1,0 +1,143 @@
+/*
+ * emd.h -- C ABI of the GB300 (sm_103a) EM multi-frame deconvolution library.
+ *
+ * The library runs the expectation-maximization update of Sec. 2 of
+ * Sukurdeep, Navarro & Budavari (arXiv:2302.05804) on one GPU:
+ *
+ *   Eq. (1)  y_t = f_t * x + eta_t,   eta_t ~ N(0, v_t)        (r = 1)
+ *   Eq. (3)  y_t = D^r(h_t * x) + eta_t                        (r > 1)
+ *   Eq. (2)  x <- x . max(N, 0) / Den   where Den > 0 (x unchanged elsewhere)
+ *              N   = sum_t F_t^T (u_t . y_t)      (once per frame set)
+ *              Den = sum_t F_t^T (u_t . F_t x)    (every iteration)
+ *            u_t = 1/v_t on valid pixels, 0 on masked pixels.
+ *
+ * "*" is the zero-padded "same" 2-D convolution with an odd K x K PSF
+ * centred at ((K-1)/2, (K-1)/2); F_t^T is the matching correlation; D^r sums
+ * r x r blocks of the fine grid and its transpose replicates a coarse pixel
+ * over its block.
+ *
+ * Conventions shared by every call:
+ *   - H, W are EXPOSURE sizes. The latent image x is (rH) x (rW).
+ *   - All arrays are C order (row-major), densely packed:
+ *       y, v   : n x H x W   float32
+ *       mask   : n x H x W   uint8, 0 = masked, nonzero = valid (NULL: all valid)
+ *       f      : n x K x K   float32 (fine-grid PSFs when r > 1)
+ *       x      : (rH) x (rW) float32
+ *   - Array arguments may be host or device pointers (CUDA unified
+ *     addressing decides). The library copies inputs into device memory it
+ *     owns; callers may reuse their buffers once the call returns.
+ *   - Work is ordered on the context's stream (emd_set_stream; default: the
+ *     legacy default stream). Calls that read back to the host, and calls
+ *     given host pointers, synchronise that stream before returning.
+ *   - Return codes: EMD_OK (0) or a negative EMD_E* code; emd_last_error()
+ *     then describes the failure (thread-local).
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef EMD_H
+#define EMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct emd_ctx emd_ctx;
+
+enum emd_status {
+    EMD_OK = 0,
+    EMD_EINVAL = -1,      /* bad argument (sizes, parity of K, NULL, mode)   */
+    EMD_ENOMEM = -2,      /* device allocation failed                        */
+    EMD_ECUDA = -3,       /* a CUDA call or kernel failed                    */
+    EMD_ESTATE = -4,      /* call out of order (e.g. iterate before frames)  */
+    EMD_EDATA = -5,       /* a valid pixel has v <= 0 or a non-finite y or v */
+    EMD_ETIMEOUT = -6,    /* a bounded device-side wait gave up              */
+    EMD_EUNSUPPORTED = -7 /* configuration not built in this library         */
+};
+
+/* Arithmetic of the two convolutions of each iteration (Eq. (2)). */
+enum emd_precision {
+    EMD_PREC_FP32 = 0,        /* FP32 FMA direct convolution (default)        */
+    EMD_PREC_BF16 = 1,        /* tensor cores, BF16 operands, FP32 accumulate */
+    EMD_PREC_FP16 = 2,        /* tensor cores, FP16 operands, FP32 accumulate */
+    EMD_PREC_SPLIT_BF16 = 3,  /* tensor cores, hi+lo BF16 split, 3 products   */
+    EMD_PREC_SPLIT_FP16 = 4   /* tensor cores, hi+lo FP16 split, 3 products   */
+};
+
+/* Largest PSF footprint the direct kernels accept: with
+ * hc = floor(((K-1)/2 + r - 1) / r), hc must not exceed EMD_MAX_HC. */
+#define EMD_MAX_HC 23
+
+/*
+ * emd_create -- new context for n exposures of H x W pixels, K x K PSFs
+ * (K odd, on the fine grid when r > 1) and super-resolution factor r >= 1
+ * (Eq. (3); r = 1 is Eq. (1)). Allocates all device memory the context
+ * will use (emd_ctx_bytes reports how much) on the current device.
+ * Returns NULL on error (emd_last_error explains): H, W, n < 1, K even or
+ * < 1, r < 1, hc > EMD_MAX_HC, or out of device memory.
+ */
+emd_ctx *emd_create(int H, int W, int n, int psf_k, int r);
+
+/* Device bytes a context of this shape holds (0 for invalid shapes). */
+size_t emd_ctx_bytes(int H, int W, int n, int psf_k, int r);
+
+/* Destroy a context and free its device memory. NULL is ignored. */
+void emd_destroy(emd_ctx *ctx);
+
+/* Thread-local description of the last error ("" if none). */
+const char *emd_last_error(void);
+
+/* Order all later work of ctx on `stream` (a cudaStream_t; NULL = legacy
+ * default stream). The library never synchronises the device, only this
+ * stream. */
+int emd_set_stream(emd_ctx *ctx, void *stream);
+
+/*
+ * emd_set_frames -- load a frame set (Sec. 2: exposures y, PSFs f and
+ * variance maps v, plus per-pixel masks) and prepare the iteration:
+ *   u_t = mask ? 1/v_t : 0,  N = sum_t F_t^T (u_t . y_t),
+ *   the constant sum of log(2 pi v) of the log-likelihood, and the default
+ *   start x^(0) = c with c = (sum u y / sum u) / r^2 when positive, else 1
+ *   (Sec. 2 only asks for a strictly positive start).
+ * y, v: n x H x W; f: n x K x K; mask: n x H x W or NULL. Masked pixels of y
+ * and v may hold anything (NaN included); they are never read
+ * arithmetically. A valid pixel with v <= 0 or non-finite y or v fails with
+ * EMD_EDATA (the context keeps no frames then).
+ */
+int emd_set_frames(emd_ctx *ctx, const float *y, const float *v,
+                   const float *f, const uint8_t *mask);
+
+/* Replace the current iterate by x0 ((rH) x (rW)). Negative entries are
+ * taken as 0. Requires frames. */
+int emd_set_x(emd_ctx *ctx, const float *x0);
+
+/* Run k >= 0 iterations of Eq. (2) on the current iterate (stream-ordered,
+ * asynchronous). EMD_ETIMEOUT if a bounded device wait gave up. */
+int emd_iterate(emd_ctx *ctx, int k);
+
+/* Copy the current iterate to out ((rH) x (rW) float32). */
+int emd_get_x(emd_ctx *ctx, float *out);
+
+/*
+ * emd_loglik -- log-likelihood of the current iterate under Eq. (1)/(3):
+ *   l = -1/2 sum_{t,i valid} [ u (y - z)^2 + log(2 pi v) ],  z = D^r(f_t * x),
+ * accumulated in FP64. chi2 (the data term sum u (y-z)^2) is returned in
+ * *chi2 when chi2 is not NULL. Synchronises the stream.
+ */
+int emd_loglik(emd_ctx *ctx, double *out, double *chi2);
+
+/* Select the convolution arithmetic (enum emd_precision). Modes not built
+ * into this library return EMD_EUNSUPPORTED and leave the mode unchanged. */
+int emd_set_precision(emd_ctx *ctx, int mode);
+
+/* Inspection: the numerator N ((rH) x (rW)) and the weights u (n x H x W)
+ * prepared by emd_set_frames. */
+int emd_get_numerator(emd_ctx *ctx, float *out);
+int emd_get_weights(emd_ctx *ctx, float *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMD_H */

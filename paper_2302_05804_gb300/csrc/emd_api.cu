@@ -1,0 +1,414 @@
+// emd_api.cu -- the C ABI of include/emd.h: context life cycle, argument
+// validation, host/device marshalling and the launch sequence of the EM
+// iteration (Sec. 2, Eq. (2)). All device memory of a context is one
+// allocation carved into the buffers described in emd_internal.cuh.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "emd_internal.cuh"
+
+using emd::Shape;
+
+namespace {
+
+thread_local std::string g_err;
+
+void set_err(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t x0, x1, N, Den, u, y, kf, ka, fraw, part, sums, err, total;
+};
+
+Layout make_layout(const Shape& s) {
+  Layout L{};
+  const size_t lat = (size_t)s.R2 * s.g.plane * sizeof(float);
+  const size_t exp = (size_t)s.n * s.g.plane * sizeof(float);
+  const size_t ker = (size_t)s.n * s.R2 * s.Kc * s.KP * sizeof(float);
+  size_t parts = (size_t)emd::kRedBlocks * 3;
+  if ((size_t)emd::fused_blocks(s) > parts) parts = emd::fused_blocks(s);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+  L.x0 = take(lat);
+  L.x1 = take(lat);
+  L.N = take(lat);
+  L.Den = take(lat);
+  L.u = take(exp);
+  L.y = take(exp);
+  L.kf = take(ker);
+  L.ka = take(ker);
+  L.fraw = take((size_t)s.n * s.K * s.K * sizeof(float));
+  L.part = take(parts * sizeof(double));
+  L.sums = take(8 * sizeof(double));
+  L.err = take(sizeof(int));
+  L.total = off;
+  return L;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct emd_ctx {
+  Shape s;
+  Layout L;
+  int device = 0;
+  cudaStream_t st = nullptr;
+  char* arena = nullptr;
+  float* x[2] = {nullptr, nullptr};
+  int cur = 0;
+  float *N = nullptr, *Den = nullptr, *u = nullptr, *y = nullptr;
+  float *kf = nullptr, *ka = nullptr, *fraw = nullptr;
+  double *part = nullptr, *sums = nullptr;
+  int* err = nullptr;
+  double logdet = 0.0, suy = 0.0, su = 0.0;
+  bool frames = false;
+  int prec = EMD_PREC_FP32;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      set_err("%s failed: %s", #call, cudaGetErrorString(e_));                     \
+      return EMD_ECUDA;                                                            \
+    }                                                                              \
+  } while (0)
+
+int check_ctx(emd_ctx* c, bool need_frames) {
+  if (!c) {
+    set_err("null context");
+    return EMD_EINVAL;
+  }
+  if (need_frames && !c->frames) {
+    set_err("no frames loaded (call emd_set_frames first)");
+    return EMD_ESTATE;
+  }
+  return EMD_OK;
+}
+
+// read the device error word (synchronises the stream) and clear it
+int check_device_error(emd_ctx* c) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (h) CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
+  if (h & emd::kErrTimeout) {
+    set_err("a bounded device-side wait gave up");
+    return EMD_ETIMEOUT;
+  }
+  return EMD_OK;
+}
+
+emd::FusedArgs fused_args(emd_ctx* c) {
+  emd::FusedArgs a{};
+  a.x = c->x[c->cur];
+  a.xn = c->x[c->cur ^ 1];
+  a.u = c->u;
+  a.y = c->y;
+  a.kf = c->kf;
+  a.ka = c->ka;
+  a.N = c->N;
+  a.Nw = c->N;
+  a.Den = c->Den;
+  a.err = c->err;
+  return a;
+}
+
+// copy an (n x H x W) natural array into n padded planes
+int put_planes(emd_ctx* c, float* planes, const float* src, int count) {
+  const emd::Geom& g = c->s.g;
+  for (int t = 0; t < count; ++t) {
+    CK(cudaMemcpy2DAsync(planes + (size_t)t * g.plane + (size_t)g.B * g.P + g.B,
+                         (size_t)g.P * sizeof(float), src + (size_t)t * g.H * g.W,
+                         (size_t)g.W * sizeof(float), (size_t)g.W * sizeof(float), g.H,
+                         cudaMemcpyDefault, c->st));
+  }
+  return EMD_OK;
+}
+
+int get_planes(emd_ctx* c, float* dst, const float* planes, int count) {
+  const emd::Geom& g = c->s.g;
+  for (int t = 0; t < count; ++t) {
+    CK(cudaMemcpy2DAsync(dst + (size_t)t * g.H * g.W, (size_t)g.W * sizeof(float),
+                         planes + (size_t)t * g.plane + (size_t)g.B * g.P + g.B,
+                         (size_t)g.P * sizeof(float), (size_t)g.W * sizeof(float), g.H,
+                         cudaMemcpyDefault, c->st));
+  }
+  return EMD_OK;
+}
+
+// latent planes -> natural (rH x rW) at out (host or device)
+int latent_out(emd_ctx* c, const float* planes, float* out) {
+  if (!out) {
+    set_err("null output pointer");
+    return EMD_EINVAL;
+  }
+  const size_t nat = (size_t)c->s.R2 * c->s.H * c->s.W;
+  if (c->s.r == 1) {
+    int rc = get_planes(c, out, planes, 1);
+    if (rc) return rc;
+  } else if (is_device_ptr(out)) {
+    CK(emd::launch_gather_latent(c->s, planes, out, c->st));
+  } else {
+    // the Den scratch holds the natural image on its way to the host
+    CK(emd::launch_gather_latent(c->s, planes, c->Den, c->st));
+    CK(cudaMemcpyAsync(out, c->Den, nat * sizeof(float), cudaMemcpyDeviceToHost, c->st));
+  }
+  CK(cudaStreamSynchronize(c->st));
+  return EMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* emd_last_error(void) { return g_err.c_str(); }
+
+size_t emd_ctx_bytes(int H, int W, int n, int psf_k, int r) {
+  Shape s;
+  const char* why = nullptr;
+  if (!emd::make_shape(H, W, n, psf_k, r, &s, &why)) return 0;
+  return make_layout(s).total;
+}
+
+emd_ctx* emd_create(int H, int W, int n, int psf_k, int r) {
+  Shape s;
+  const char* why = nullptr;
+  if (!emd::make_shape(H, W, n, psf_k, r, &s, &why)) {
+    set_err("emd_create: %s", why);
+    return nullptr;
+  }
+  emd_ctx* c = new emd_ctx();
+  c->s = s;
+  c->L = make_layout(s);
+  cudaGetDevice(&c->device);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, c->L.total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_err("emd_create: cudaMalloc(%zu bytes) failed: %s", c->L.total, cudaGetErrorString(e));
+    delete c;
+    return nullptr;
+  }
+  c->arena = static_cast<char*>(p);
+  e = cudaMemset(c->arena, 0, c->L.total);
+  if (e != cudaSuccess) {
+    set_err("emd_create: cudaMemset failed: %s", cudaGetErrorString(e));
+    cudaFree(p);
+    delete c;
+    return nullptr;
+  }
+  c->x[0] = reinterpret_cast<float*>(c->arena + c->L.x0);
+  c->x[1] = reinterpret_cast<float*>(c->arena + c->L.x1);
+  c->N = reinterpret_cast<float*>(c->arena + c->L.N);
+  c->Den = reinterpret_cast<float*>(c->arena + c->L.Den);
+  c->u = reinterpret_cast<float*>(c->arena + c->L.u);
+  c->y = reinterpret_cast<float*>(c->arena + c->L.y);
+  c->kf = reinterpret_cast<float*>(c->arena + c->L.kf);
+  c->ka = reinterpret_cast<float*>(c->arena + c->L.ka);
+  c->fraw = reinterpret_cast<float*>(c->arena + c->L.fraw);
+  c->part = reinterpret_cast<double*>(c->arena + c->L.part);
+  c->sums = reinterpret_cast<double*>(c->arena + c->L.sums);
+  c->err = reinterpret_cast<int*>(c->arena + c->L.err);
+  g_err.clear();
+  return c;
+}
+
+void emd_destroy(emd_ctx* c) {
+  if (!c) return;
+  DeviceGuard dg(c->device);
+  if (c->st) cudaStreamSynchronize(c->st);
+  else cudaDeviceSynchronize();
+  cudaFree(c->arena);
+  delete c;
+}
+
+int emd_set_stream(emd_ctx* c, void* stream) {
+  if (int rc = check_ctx(c, false)) return rc;
+  c->st = static_cast<cudaStream_t>(stream);
+  return EMD_OK;
+}
+
+int emd_set_precision(emd_ctx* c, int mode) {
+  if (int rc = check_ctx(c, false)) return rc;
+  if (mode == EMD_PREC_FP32) {
+    c->prec = mode;
+    return EMD_OK;
+  }
+  if (mode < 0 || mode > EMD_PREC_SPLIT_FP16) {
+    set_err("unknown precision mode %d", mode);
+    return EMD_EINVAL;
+  }
+  set_err("precision mode %d is not built into this library", mode);
+  return EMD_EUNSUPPORTED;
+}
+
+int emd_set_frames(emd_ctx* c, const float* y, const float* v, const float* f,
+                   const uint8_t* mask) {
+  if (int rc = check_ctx(c, false)) return rc;
+  if (!y || !v || !f) {
+    set_err("emd_set_frames: y, v and f must not be NULL");
+    return EMD_EINVAL;
+  }
+  DeviceGuard dg(c->device);
+  const Shape& s = c->s;
+  c->frames = false;
+  const size_t npix = (size_t)s.n * s.H * s.W;
+  if (int rc = put_planes(c, c->y, y, s.n)) return rc;
+  if (int rc = put_planes(c, c->u, v, s.n)) return rc;  // v, converted in place below
+  CK(cudaMemcpyAsync(c->fraw, f, (size_t)s.n * s.K * s.K * sizeof(float), cudaMemcpyDefault,
+                     c->st));
+  const uint8_t* dmask = nullptr;
+  void* tmp = nullptr;
+  if (mask) {
+    if (is_device_ptr(mask)) {
+      dmask = mask;
+    } else {
+      CK(cudaMallocAsync(&tmp, npix, c->st));
+      CK(cudaMemcpyAsync(tmp, mask, npix, cudaMemcpyHostToDevice, c->st));
+      dmask = static_cast<const uint8_t*>(tmp);
+    }
+  }
+  CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
+  emd::SetupArgs sa{dmask, c->u, c->y, c->part, c->err};
+  CK(emd::launch_setup(s, sa, c->st));
+  if (tmp) CK(cudaFreeAsync(tmp, c->st));
+  CK(emd::launch_reduce_final(c->part, emd::kRedBlocks, 3, c->sums, c->st));
+  CK(emd::launch_build_kernels(s, c->fraw, c->kf, c->ka, c->st));
+  double h[3];
+  int herr = 0;
+  CK(cudaMemcpyAsync(h, c->sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (herr & emd::kErrData) {
+    CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
+    set_err("emd_set_frames: a valid pixel has v <= 0 or a non-finite y or v");
+    return EMD_EDATA;
+  }
+  c->logdet = h[0];
+  c->suy = h[1];
+  c->su = h[2];
+  // numerator N = sum_t F_t^T (u_t y_t)
+  emd::FusedArgs a = fused_args(c);
+  CK(emd::launch_fused(s, a, 1, c->part, c->st));
+  // default strictly positive start
+  double x0 = 1.0;
+  if (c->su > 0.0) {
+    const double cc = c->suy / c->su / ((double)s.r * s.r);
+    if (cc > 0.0) x0 = cc;
+  }
+  CK(emd::launch_fill_latent(s, c->x[c->cur], (float)x0, c->st));
+  c->frames = true;
+  return check_device_error(c);
+}
+
+int emd_set_x(emd_ctx* c, const float* x0) {
+  if (int rc = check_ctx(c, true)) return rc;
+  if (!x0) {
+    set_err("emd_set_x: null pointer");
+    return EMD_EINVAL;
+  }
+  DeviceGuard dg(c->device);
+  const Shape& s = c->s;
+  const size_t nat = (size_t)s.R2 * s.H * s.W;
+  const float* src = x0;
+  if (!is_device_ptr(x0)) {
+    CK(cudaMemcpyAsync(c->Den, x0, nat * sizeof(float), cudaMemcpyHostToDevice, c->st));
+    src = c->Den;
+  }
+  CK(emd::launch_scatter_latent(s, src, c->x[c->cur], 1, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return EMD_OK;
+}
+
+int emd_iterate(emd_ctx* c, int k) {
+  if (int rc = check_ctx(c, true)) return rc;
+  if (k < 0) {
+    set_err("emd_iterate: k must be >= 0");
+    return EMD_EINVAL;
+  }
+  DeviceGuard dg(c->device);
+  for (int it = 0; it < k; ++it) {
+    emd::FusedArgs a = fused_args(c);
+    CK(emd::launch_fused(c->s, a, 0, c->part, c->st));
+    c->cur ^= 1;
+  }
+  return EMD_OK;
+}
+
+int emd_get_x(emd_ctx* c, float* out) {
+  if (int rc = check_ctx(c, true)) return rc;
+  DeviceGuard dg(c->device);
+  if (int rc = latent_out(c, c->x[c->cur], out)) return rc;
+  return check_device_error(c);
+}
+
+int emd_get_numerator(emd_ctx* c, float* out) {
+  if (int rc = check_ctx(c, true)) return rc;
+  DeviceGuard dg(c->device);
+  return latent_out(c, c->N, out);
+}
+
+int emd_get_weights(emd_ctx* c, float* out) {
+  if (int rc = check_ctx(c, true)) return rc;
+  if (!out) {
+    set_err("null output pointer");
+    return EMD_EINVAL;
+  }
+  DeviceGuard dg(c->device);
+  if (int rc = get_planes(c, out, c->u, c->s.n)) return rc;
+  CK(cudaStreamSynchronize(c->st));
+  return EMD_OK;
+}
+
+int emd_loglik(emd_ctx* c, double* out, double* chi2) {
+  if (int rc = check_ctx(c, true)) return rc;
+  if (!out) {
+    set_err("null output pointer");
+    return EMD_EINVAL;
+  }
+  DeviceGuard dg(c->device);
+  emd::FusedArgs a = fused_args(c);
+  CK(emd::launch_fused(c->s, a, 2, c->part, c->st));
+  CK(emd::launch_reduce_final(c->part, emd::fused_blocks(c->s), 1, c->sums + 3, c->st));
+  double h = 0.0;
+  CK(cudaMemcpyAsync(&h, c->sums + 3, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  if (int rc = check_device_error(c)) return rc;
+  *out = -0.5 * (h + c->logdet);
+  if (chi2) *chi2 = h;
+  return EMD_OK;
+}
+
+}  // extern "C"

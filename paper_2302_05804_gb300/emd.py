@@ -1,0 +1,237 @@
+"""Thin Python binding of the C ABI in include/emd.h (argument marshalling
+only; every step of the EM iteration runs in the CUDA library).
+
+Functions carry the C names. Array arguments may be numpy arrays (host) or
+torch tensors (host or CUDA); they must be C-contiguous with the dtype the
+ABI states (float32, or uint8 for masks). The library refuses to run
+without its compiled extension: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+EMD_OK = 0
+EMD_EINVAL = -1
+EMD_ENOMEM = -2
+EMD_ECUDA = -3
+EMD_ESTATE = -4
+EMD_EDATA = -5
+EMD_ETIMEOUT = -6
+EMD_EUNSUPPORTED = -7
+
+EMD_PREC_FP32 = 0
+EMD_PREC_BF16 = 1
+EMD_PREC_FP16 = 2
+EMD_PREC_SPLIT_BF16 = 3
+EMD_PREC_SPLIT_FP16 = 4
+
+EXPORTS = [
+    "emd_create", "emd_ctx_bytes", "emd_destroy", "emd_last_error", "emd_set_stream",
+    "emd_set_frames", "emd_set_x", "emd_iterate", "emd_get_x", "emd_loglik",
+    "emd_set_precision", "emd_get_numerator", "emd_get_weights",
+]
+
+
+class EMDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libemd.so; raise if it is missing (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(
+                    f"{path} is missing: build the CUDA extension first "
+                    "(python -m paper_2302_05804_gb300.build)")
+            _build.build()
+        lib = C.CDLL(path)
+        vp, i, dp = C.c_void_p, C.c_int, C.POINTER(C.c_double)
+        lib.emd_create.argtypes = [i, i, i, i, i]
+        lib.emd_create.restype = vp
+        lib.emd_ctx_bytes.argtypes = [i, i, i, i, i]
+        lib.emd_ctx_bytes.restype = C.c_size_t
+        lib.emd_destroy.argtypes = [vp]
+        lib.emd_destroy.restype = None
+        lib.emd_last_error.argtypes = []
+        lib.emd_last_error.restype = C.c_char_p
+        lib.emd_set_stream.argtypes = [vp, vp]
+        lib.emd_set_frames.argtypes = [vp, vp, vp, vp, vp]
+        lib.emd_set_x.argtypes = [vp, vp]
+        lib.emd_iterate.argtypes = [vp, i]
+        lib.emd_get_x.argtypes = [vp, vp]
+        lib.emd_loglik.argtypes = [vp, dp, dp]
+        lib.emd_set_precision.argtypes = [vp, i]
+        lib.emd_get_numerator.argtypes = [vp, vp]
+        lib.emd_get_weights.argtypes = [vp, vp]
+        for name in ("emd_set_stream", "emd_set_frames", "emd_set_x", "emd_iterate",
+                     "emd_get_x", "emd_loglik", "emd_set_precision", "emd_get_numerator",
+                     "emd_get_weights"):
+            getattr(lib, name).restype = i
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != EMD_OK:
+        raise EMDError(rc, load().emd_last_error().decode())
+
+
+def _ptr(a, dtype, name: str):
+    """Data pointer of a contiguous numpy array or torch tensor of dtype."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"{name}: need a C-contiguous {np.dtype(dtype)} array")
+        return a.ctypes.data
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        tdt = {np.float32: torch.float32, np.uint8: torch.uint8}[np.dtype(dtype).type]
+        if a.dtype != tdt or not a.is_contiguous():
+            raise TypeError(f"{name}: need a contiguous {tdt} tensor")
+        return a.data_ptr()
+    raise TypeError(f"{name}: unsupported array type {type(a)}")
+
+
+# -- C-ABI wrappers (same names) ---------------------------------------------
+
+def emd_create(H: int, W: int, n: int, psf_k: int, r: int = 1) -> int:
+    h = load().emd_create(H, W, n, psf_k, r)
+    if not h:
+        raise EMDError(EMD_EINVAL, load().emd_last_error().decode())
+    return h
+
+
+def emd_ctx_bytes(H: int, W: int, n: int, psf_k: int, r: int = 1) -> int:
+    return int(load().emd_ctx_bytes(H, W, n, psf_k, r))
+
+
+def emd_destroy(ctx) -> None:
+    if ctx:
+        load().emd_destroy(ctx)
+
+
+def emd_last_error() -> str:
+    return load().emd_last_error().decode()
+
+
+def emd_set_stream(ctx, stream) -> None:
+    """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(load().emd_set_stream(ctx, stream))
+
+
+def emd_set_frames(ctx, y, v, f, mask=None) -> None:
+    _check(load().emd_set_frames(ctx, _ptr(y, np.float32, "y"), _ptr(v, np.float32, "v"),
+                                 _ptr(f, np.float32, "f"), _ptr(mask, np.uint8, "mask")))
+
+
+def emd_set_x(ctx, x0) -> None:
+    _check(load().emd_set_x(ctx, _ptr(x0, np.float32, "x0")))
+
+
+def emd_iterate(ctx, k: int) -> None:
+    _check(load().emd_iterate(ctx, int(k)))
+
+
+def emd_get_x(ctx, out) -> None:
+    _check(load().emd_get_x(ctx, _ptr(out, np.float32, "out")))
+
+
+def emd_get_numerator(ctx, out) -> None:
+    _check(load().emd_get_numerator(ctx, _ptr(out, np.float32, "out")))
+
+
+def emd_get_weights(ctx, out) -> None:
+    _check(load().emd_get_weights(ctx, _ptr(out, np.float32, "out")))
+
+
+def emd_loglik(ctx):
+    """Returns (loglik, chi2), both FP64."""
+    ll, chi = C.c_double(), C.c_double()
+    _check(load().emd_loglik(ctx, C.byref(ll), C.byref(chi)))
+    return ll.value, chi.value
+
+
+def emd_set_precision(ctx, mode: int) -> None:
+    _check(load().emd_set_precision(ctx, int(mode)))
+
+
+# -- convenience wrapper --------------------------------------------------------
+
+class Deconvolver:
+    """Owns one context: ``Deconvolver(H, W, n, K, r)``, then
+    ``set_frames``, ``iterate``, ``x()``, ``loglik()``."""
+
+    def __init__(self, H, W, n, K, r=1, stream=None):
+        self.H, self.W, self.n, self.K, self.r = H, W, n, K, r
+        self.ctx = emd_create(H, W, n, K, r)
+        if stream is not None:
+            emd_set_stream(self.ctx, stream)
+
+    def close(self):
+        if self.ctx:
+            emd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_frames(self, y, v, f, mask=None):
+        emd_set_frames(self.ctx, y, v, f, mask)
+
+    def set_x(self, x0):
+        emd_set_x(self.ctx, x0)
+
+    def iterate(self, k):
+        emd_iterate(self.ctx, k)
+
+    def set_precision(self, mode):
+        emd_set_precision(self.ctx, mode)
+
+    def x(self, out=None):
+        if out is None:
+            out = np.empty((self.r * self.H, self.r * self.W), np.float32)
+        emd_get_x(self.ctx, out)
+        return out
+
+    def numerator(self):
+        out = np.empty((self.r * self.H, self.r * self.W), np.float32)
+        emd_get_numerator(self.ctx, out)
+        return out
+
+    def weights(self):
+        out = np.empty((self.n, self.H, self.W), np.float32)
+        emd_get_weights(self.ctx, out)
+        return out
+
+    def loglik(self):
+        return emd_loglik(self.ctx)

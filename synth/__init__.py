@@ -118,32 +118,34 @@ def draw_masks(n: int, H: int, W: int, frac: float,
     if frac <= 0:
         return m
     target = frac * H * W
+    offs = {rr: [(dy, dx) for dy in range(-rr, rr + 1) for dx in range(-rr, rr + 1)
+                 if dy * dy + dx * dx <= rr * rr] for rr in (1, 2, 3)}
     for t in range(n):
-        bad = 0
         mt = m[t]
         # about a third of the budget in columns, the rest in cosmic rays
-        while bad < target / 3.0:
+        while H * W - int(mt.sum()) < target / 3.0:
             c = int(rng.integers(0, W))
             if rng.uniform() < 0.5:
                 r0, r1 = 0, H
             else:
                 r0 = int(rng.integers(0, H))
                 r1 = min(H, r0 + int(rng.integers(H // 8 + 1, H // 2 + 2)))
-            bad += int(mt[r0:r1, c].sum())
             mt[r0:r1, c] = 0
-        while bad < target:
-            k = max(1, int(target - bad) // 8)
+        while True:
+            bad = H * W - int(mt.sum())
+            if bad >= target:
+                break
+            k = max(1, int(target - bad) // 12)
             cy = rng.integers(0, H, k)
             cx = rng.integers(0, W, k)
             rad = rng.integers(1, 4, k)
-            for yy, xx, rr in zip(cy, cx, rad):
-                y0, y1 = max(0, yy - rr), min(H, yy + rr + 1)
-                x0, x1 = max(0, xx - rr), min(W, xx + rr + 1)
-                gy, gx = np.mgrid[y0:y1, x0:x1]
-                disc = (gy - yy) ** 2 + (gx - xx) ** 2 <= rr * rr
-                sub = mt[y0:y1, x0:x1]
-                bad += int((sub & disc).sum())
-                sub[disc] = 0
+            for rr, oo in offs.items():
+                sel = rad == rr
+                yy0, xx0 = cy[sel], cx[sel]
+                for dy, dx in oo:
+                    yy = np.clip(yy0 + dy, 0, H - 1)
+                    xx = np.clip(xx0 + dx, 0, W - 1)
+                    mt[yy, xx] = 0
     return m
 
 
@@ -204,7 +206,33 @@ RECIPES = {
 
 
 def make_problem(recipe: str = "parity", *, seed_offset: int = 0,
-                 noise_free: bool = False, dtype=np.float32, **over) -> Problem:
+                 noise_free: bool = False, dtype=np.float32, cache: bool = True,
+                 **over) -> Problem:
+    """Cached front of ``_make_problem``: when the environment variable
+    EMD_SYNTH_CACHE names a directory, problems are stored there as .npz and
+    reloaded on the next call with the same arguments."""
+    cdir = os.environ.get("EMD_SYNTH_CACHE")
+    if not (cache and cdir):
+        return _make_problem(recipe, seed_offset=seed_offset, noise_free=noise_free,
+                             dtype=dtype, **over)
+    key = "_".join([recipe, str(seed_offset), str(int(noise_free)), np.dtype(dtype).name]
+                   + [f"{k}{over[k]}" for k in sorted(over)])
+    path = os.path.join(cdir, key + ".npz")
+    if os.path.exists(path):
+        z = np.load(path, allow_pickle=True)
+        return Problem(y=z["y"], v=z["v"], f=z["f"], mask=z["mask"], x_true=z["x_true"],
+                       r=int(z["r"]), meta=z["meta"].item())
+    p = _make_problem(recipe, seed_offset=seed_offset, noise_free=noise_free,
+                      dtype=dtype, **over)
+    os.makedirs(cdir, exist_ok=True)
+    np.savez(path + ".tmp.npz", y=p.y, v=p.v, f=p.f, mask=p.mask, x_true=p.x_true, r=p.r,
+             meta=np.array(p.meta, dtype=object))
+    os.replace(path + ".tmp.npz", path)
+    return p
+
+
+def _make_problem(recipe: str = "parity", *, seed_offset: int = 0,
+                  noise_free: bool = False, dtype=np.float32, **over) -> Problem:
     """Draw a seeded problem following ``RECIPES[recipe]``; keyword overrides
     rescale it (e.g. ``H=512, W=384, n=5``). Source counts scale with the
     latent area when H or W are overridden and counts are not given."""

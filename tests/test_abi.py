@@ -1,0 +1,71 @@
+"""The C-ABI library loads and exports every entry point include/*.h declares
+(no GPU needed: only host-side calls are made)."""
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(emd_\w+)\s*\(", src):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2302_05804_gb300 import build, emd
+    build.build()
+    return emd.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert "emd_iterate" in names and "emd_set_frames" in names
+    for n in sorted(names):
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_binding_names_match_header():
+    from paper_2302_05804_gb300 import emd
+    for n in declared_symbols():
+        assert hasattr(emd, n), f"python binding lacks {n}"
+
+
+def test_ctx_bytes_host_only(lib):
+    from paper_2302_05804_gb300 import emd
+    b = emd.emd_ctx_bytes(256, 256, 4, 15, 1)
+    assert b > 2 * 4 * 256 * 256 * 4      # u and y planes at least
+    big = emd.emd_ctx_bytes(4096, 4096, 33, 43, 1)
+    assert 4.4e9 < big < 6e9
+    # invalid shapes: even PSF, r = 0, empty image, oversized footprint
+    assert emd.emd_ctx_bytes(256, 256, 4, 14, 1) == 0
+    assert emd.emd_ctx_bytes(256, 256, 4, 15, 0) == 0
+    assert emd.emd_ctx_bytes(0, 256, 4, 15, 1) == 0
+    assert emd.emd_ctx_bytes(256, 256, 0, 15, 1) == 0
+    assert emd.emd_ctx_bytes(256, 256, 4, 101, 1) == 0
+    assert emd.emd_ctx_bytes(256, 256, 4, 85, 2) > 0   # hc = 21 on the coarse grid
+
+
+def test_create_rejects_bad_shapes_before_touching_the_gpu(lib):
+    from paper_2302_05804_gb300 import emd
+    for args in [(64, 64, 2, 4, 1), (64, 64, 2, 5, 0), (-1, 64, 2, 5, 1)]:
+        with pytest.raises(emd.EMDError) as ei:
+            emd.emd_create(*args)
+        assert ei.value.code == emd.EMD_EINVAL
+        assert emd.emd_last_error()
+
+
+def test_null_context_is_an_error(lib):
+    from paper_2302_05804_gb300 import emd
+    with pytest.raises(emd.EMDError) as ei:
+        emd.emd_iterate(None, 1)
+    assert ei.value.code == emd.EMD_EINVAL

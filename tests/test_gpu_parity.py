@@ -1,0 +1,241 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 against the oracle): 1e-5 after one iteration and
+1e-4 after 50 for the FP32 path; the set of zero weights (masks) is compared
+bit for bit. Every case passes the same explicit x0 to both sides.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def emd():
+    from paper_2302_05804_gb300 import emd as m
+    m.load()
+    return m
+
+
+def make(recipe="parity", **kw):
+    return synth.make_problem(recipe, **kw)
+
+
+def start(p, seed=0):
+    g = np.random.default_rng(seed)
+    Hf, Wf = p.r * p.H, p.r * p.W
+    return (g.uniform(0.5, 1.5, (Hf, Wf)) * max(np.nanmean(p.y), 1.0) / p.r ** 2).astype(np.float32)
+
+
+def gpu_run(emd, p, x0, k, prec=0):
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    try:
+        d.set_frames(p.y, p.v, p.f, p.mask)
+        if prec:
+            d.set_precision(prec)
+        d.set_x(x0)
+        d.iterate(k)
+        return d.x()
+    finally:
+        d.close()
+
+
+def oracle_run(p, x0, k):
+    u, y, N, _ = oracle.prepare(p)
+    return oracle.em_run(x0.astype(np.float64), N, u, p.f, k, p.r)
+
+
+# -- set-up: weights, masks, numerator ----------------------------------------
+
+def test_weights_mask_bitexact_and_numerator(emd):
+    p = make(mask_frac=0.05)
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    d.set_frames(p.y, p.v, p.f, p.mask)
+    u_g = d.weights()
+    N_g = d.numerator()
+    d.close()
+    u_o, _ = oracle.weights(p.v, p.mask, p.y)
+    np.testing.assert_array_equal(u_g == 0, p.mask == 0)
+    np.testing.assert_allclose(u_g, u_o, rtol=2e-7)
+    yy = np.where(p.mask != 0, p.y.astype(np.float64), 0.0)
+    N_o = oracle.numerator(yy, u_o, p.f)
+    assert rel_l2(N_g, N_o) < 1e-6
+
+
+# -- the iteration ---------------------------------------------------------------
+
+def test_parity_config_one_and_fifty_iterations(emd):
+    # 256^2, n=4, 15x15 Moffat PSFs, zero background, 50 iterations, FP32
+    p = make()
+    x0 = start(p)
+    x1 = gpu_run(emd, p, x0, 1)
+    assert rel_l2(x1, oracle_run(p, x0, 1)) <= 1e-5
+    x50 = gpu_run(emd, p, x0, 50)
+    assert rel_l2(x50, oracle_run(p, x0, 50)) <= 1e-4
+    assert (x50 >= 0).all()
+
+
+CASES = [
+    # (H, W, n, K, r, mask_frac) -- ragged tiles, K > H, delta PSF, r = 2, 3
+    (200, 150, 3, 15, 1, 0.05),
+    (130, 257, 2, 43, 1, 0.05),
+    (5, 7, 2, 9, 1, 0.0),
+    (64, 64, 1, 1, 1, 0.1),
+    (129, 128, 2, 3, 1, 0.0),
+    (96, 80, 2, 15, 2, 0.05),
+    (33, 47, 3, 21, 2, 0.0),
+    (40, 36, 2, 7, 3, 0.05),
+    (70, 90, 2, 47, 1, 0.02),
+]
+
+
+@pytest.mark.parametrize("H,W,n,K,r,mf", CASES)
+def test_parity_shapes(emd, H, W, n, K, r, mf):
+    p = make("hsc", H=H, W=W, n=n, K=K, r=r, mask_frac=mf,
+             fwhm=(1.5 * r, 3.0 * r), n_points=max(3, H * W // 400), n_gal=2)
+    x0 = start(p, seed=H + W)
+    x1 = gpu_run(emd, p, x0, 1)
+    assert rel_l2(x1, oracle_run(p, x0, 1)) <= 1e-5
+    x5 = gpu_run(emd, p, x0, 5)
+    assert rel_l2(x5, oracle_run(p, x0, 5)) <= 2e-5
+
+
+def test_delta_psf_gives_coadd(emd):
+    p = make("hsc", H=48, W=40, n=3, K=1, r=1, mask_frac=0.2, n_points=20, n_gal=1)
+    x0 = start(p)
+    x1 = gpu_run(emd, p, x0, 1).astype(np.float64)
+    u, y, _, _ = oracle.prepare(p)
+    su = u.sum(0)
+    coadd = np.where(su > 0, np.maximum((u * y).sum(0), 0) / np.where(su > 0, su, 1), x0)
+    np.testing.assert_allclose(x1, coadd, rtol=2e-6, atol=1e-6 * np.abs(coadd).max())
+
+
+def test_loglik_parity(emd):
+    p = make(mask_frac=0.03)
+    x0 = start(p)
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    d.set_frames(p.y, p.v, p.f, p.mask)
+    d.set_x(x0)
+    ll_g, chi_g = d.loglik()
+    d.iterate(3)
+    x3 = d.x()
+    ll3_g, _ = d.loglik()
+    d.close()
+    u, y, _, _ = oracle.prepare(p)
+    v = np.where(p.mask != 0, p.v.astype(np.float64), 1.0)
+    chi_o = oracle.chi2(x0, y, u, p.f)
+    ll_o = oracle.loglik(x0, y, v, u, p.f)
+    assert abs(chi_g - chi_o) <= 1e-6 * chi_o
+    assert abs(ll_g - ll_o) <= 1e-6 * abs(ll_o)
+    assert abs(ll3_g - oracle.loglik(x3, y, v, u, p.f)) <= 1e-6 * abs(ll_o)
+
+
+# -- invariants on the GPU --------------------------------------------------------
+
+def test_monotone_likelihood_and_nonnegativity(emd):
+    p = make(mask_frac=0.05)
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    d.set_frames(p.y, p.v, p.f, p.mask)
+    prev = d.loglik()[0]
+    for _ in range(20):
+        d.iterate(1)
+        ll = d.loglik()[0]
+        assert ll >= prev - 1e-7 * abs(prev)
+        prev = ll
+    assert (d.x() >= 0).all()
+    d.close()
+
+
+def test_power_of_two_scaling_is_bitexact(emd):
+    p = make(mask_frac=0.05)
+    x0 = start(p)
+    a = gpu_run(emd, p, x0, 4)
+    q = synth.Problem(y=p.y * np.float32(8.0), v=p.v, f=p.f, mask=p.mask, x_true=p.x_true)
+    b = gpu_run(emd, q, x0 * np.float32(8.0), 4)
+    np.testing.assert_array_equal(b, a * np.float32(8.0))
+    q = synth.Problem(y=p.y, v=p.v * np.float32(0.25), f=p.f, mask=p.mask, x_true=p.x_true)
+    c = gpu_run(emd, q, x0, 4)
+    np.testing.assert_array_equal(c, a)
+
+
+def test_exposure_order_independence(emd):
+    p = make(mask_frac=0.05)
+    x0 = start(p)
+    a = gpu_run(emd, p, x0, 3)
+    perm = [2, 0, 3, 1]
+    q = synth.Problem(y=np.ascontiguousarray(p.y[perm]), v=np.ascontiguousarray(p.v[perm]),
+                      f=np.ascontiguousarray(p.f[perm]), mask=np.ascontiguousarray(p.mask[perm]),
+                      x_true=p.x_true)
+    b = gpu_run(emd, q, x0, 3)
+    assert rel_l2(b, a) < 1e-6
+
+
+def test_checkpoint_resume_is_bitexact(emd):
+    p = make(mask_frac=0.05)
+    x0 = start(p)
+    a = gpu_run(emd, p, x0, 7)
+    mid = gpu_run(emd, p, x0, 3)
+    b = gpu_run(emd, p, mid, 4)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_device_pointers_match_host_pointers(emd):
+    torch = pytest.importorskip("torch")
+    p = make("hsc", H=96, W=80, n=2, K=15, r=2, mask_frac=0.05, n_points=30, n_gal=2)
+    x0 = start(p)
+    a = gpu_run(emd, p, x0, 2)
+    dev = lambda z: torch.from_numpy(z).cuda()
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    d.set_frames(dev(p.y), dev(p.v), dev(p.f), dev(p.mask))
+    d.set_x(dev(x0))
+    d.iterate(2)
+    out = torch.empty((p.r * p.H, p.r * p.W), dtype=torch.float32, device="cuda")
+    emd.emd_get_x(d.ctx, out)
+    d.close()
+    np.testing.assert_array_equal(out.cpu().numpy(), a)
+
+
+def test_set_get_x_roundtrip_clamps_negatives(emd):
+    p = make("hsc", H=40, W=30, n=2, K=7, r=2, n_points=5, n_gal=1)
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    d.set_frames(p.y, p.v, p.f, p.mask)
+    z = np.random.default_rng(3).standard_normal((80, 60)).astype(np.float32)
+    d.set_x(z)
+    np.testing.assert_array_equal(d.x(), np.maximum(z, 0))
+    d.close()
+
+
+# -- errors ---------------------------------------------------------------------------
+
+def test_invalid_data_and_state_errors(emd):
+    p = make("hsc", H=32, W=32, n=2, K=5, n_points=5, n_gal=1, mask_frac=0.0)
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    with pytest.raises(emd.EMDError) as ei:
+        d.iterate(1)
+    assert ei.value.code == emd.EMD_ESTATE
+    v = p.v.copy()
+    v[1, 3, 4] = -1.0
+    with pytest.raises(emd.EMDError) as ei:
+        d.set_frames(p.y, v, p.f, p.mask)
+    assert ei.value.code == emd.EMD_EDATA
+    # the same bad pixel masked out is fine, and NaN in masked y is ignored
+    m = p.mask.copy()
+    m[1, 3, 4] = 0
+    y = p.y.copy()
+    y[1, 3, 4] = np.nan
+    d.set_frames(y, v, p.f, m)
+    d.iterate(1)
+    assert np.isfinite(d.x()).all()
+    with pytest.raises(emd.EMDError) as ei:
+        d.iterate(-1)
+    assert ei.value.code == emd.EMD_EINVAL
+    d.close()
