@@ -366,20 +366,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       for (int e = tid; e < (Kc * KP) >> 2; e += kThreads)
         reinterpret_cast<float4*>(ksa)[e] = kg[e];
       __syncthreads();
+      // each exposure's adjoint is summed from zero and then added to the
+      // running Den: a per-exposure FMA chain of Kc^2 terms instead of one
+      // chain of n Kc^2 terms keeps the FP32 rounding of Den near 1e-7
       float acc2[2][16];
       const long long pbase = (long long)phi * g.plane;
 #pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        const long long grow =
-            pbase + (long long)(g.B + i0 + kHalf * q + 2 * amy + p) * g.P + g.B + j0 + 16 * amx;
+      for (int p = 0; p < 2; ++p)
 #pragma unroll
-        for (int c = 0; c < 16; ++c) acc2[p][c] = (t == 0) ? 0.f : a.Den[grow + c];
-      }
+        for (int c = 0; c < 16; ++c) acc2[p][c] = 0.f;
       if (!timed_out) corr_tile<2, 16>(acc2, ws, 2 * amy, 16 * amx, ksa, KP, Kc);
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int i = i0 + kHalf * q + 2 * amy + p;
         const long long grow = pbase + (long long)(g.B + i) * g.P + g.B + j0 + 16 * amx;
+        if (t > 0) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) acc2[p][c] = a.Den[grow + c] + acc2[p][c];
+        }
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int j = j0 + 16 * amx + c;
