@@ -203,6 +203,8 @@ def run_reference(args):
 def config_of(args, extra=None):
     d = workload_shape(args.workload)
     H, W, n, K, r = d["H"], d["W"], d["n"], d["K"], d["r"]
+    if getattr(args, "size", 0) and args.impl == "ours":
+        H = W = args.size
     c = {"workload": f"{args.workload}: {n} exposures of {H}x{W}, "
                      f"{K}x{K} PSFs, r={r}, latent {r * H}x{r * W}",
          "H": H, "W": W, "n": n, "K": K, "r": r,
@@ -225,7 +227,8 @@ def run_ours(args):
     import synth
     from paper_2302_05804_gb300 import emd
 
-    p = synth.make_problem(args.workload)
+    over = {"H": args.size, "W": args.size} if args.size else {}
+    p = synth.make_problem(args.workload, **over)
     Hf, Wf = p.r * p.H, p.r * p.W
     prec = {"fp32": 0, "bf16": 1, "fp16": 2, "split_bf16": 3, "split_fp16": 4}[args.precision]
 
@@ -336,6 +339,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["hsc", "sr2", "parity"], default="hsc")
+    ap.add_argument("--size", type=int, default=0,
+                    help="override the exposure side (profiling of small cases)")
     ap.add_argument("--precision", default="fp32",
                     choices=["fp32", "bf16", "fp16", "split_bf16", "split_fp16"])
     ap.add_argument("--e2e-iters", type=int, default=10)
