@@ -136,6 +136,38 @@ int emd_set_precision(emd_ctx *ctx, int mode);
 int emd_get_numerator(emd_ctx *ctx, float *out);
 int emd_get_weights(emd_ctx *ctx, float *out);
 
+/*
+ * emd_frame_stats_noalloc -- per-exposure FP64 frame statistics without any
+ * device allocation. The paper has no counterpart: this exists for callers
+ * that cannot call cudaMalloc (work issued during CUDA-graph stream capture,
+ * real-time pipelines that reserve device memory up front, frameworks that
+ * own all device memory through their own allocator).
+ *
+ * Inputs are caller-owned DEVICE buffers in natural layout: y, v (n x H x W
+ * float32) and mask (n x H x W uint8, 0 = masked) or NULL. The output out
+ * is a caller-owned DEVICE buffer of n x 4 doubles; for exposure t:
+ *   out[4t+0] = sum over valid pixels of log(2 pi v)
+ *   out[4t+1] = sum over valid pixels of u y,  u = 1/v (FP32 reciprocal)
+ *   out[4t+2] = sum over valid pixels of u
+ *   out[4t+3] = number of valid pixels with v <= 0 or non-finite y or v
+ *               (they are left out of the three sums)
+ * These are the statistics emd_set_frames computes for a context.
+ *
+ * Work is queued on `stream` (a cudaStream_t, NULL = legacy default stream)
+ * and the call returns without synchronising. Scratch lives in one
+ * fixed-size array inside the library's device image (room for
+ * EMD_NOALLOC_MAX_EXPOSURES exposures; every GPU that loads the library
+ * holds it until the process exits). n > EMD_NOALLOC_MAX_EXPOSURES is
+ * rejected with EMD_EINVAL, as are NULL or host pointers and sizes < 1.
+ * The first call on a device looks up the scratch array's device address;
+ * make that first call before any stream capture. All calls share the one
+ * scratch array, so calls that overlap on the GPU (concurrent streams or
+ * threads) race and must be serialised by the caller.
+ */
+#define EMD_NOALLOC_MAX_EXPOSURES 64
+int emd_frame_stats_noalloc(const float *y, const float *v, const uint8_t *mask,
+                            int H, int W, int n, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

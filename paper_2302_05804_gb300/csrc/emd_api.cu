@@ -67,6 +67,10 @@ bool is_device_ptr(const void* p) {
 
 }  // namespace
 
+namespace emd {
+void set_error_message(const char* msg) { g_err = msg; }
+}  // namespace emd
+
 struct emd_ctx {
   Shape s;
   Layout L;

@@ -79,6 +79,9 @@ struct SetupArgs {
   int* err;
 };
 
+// sets the thread-local message returned by emd_last_error (emd_api.cu)
+void set_error_message(const char* msg);
+
 // kernels (emd_direct.cu)
 cudaError_t launch_setup(const Shape& s, const SetupArgs& a, cudaStream_t st);
 cudaError_t launch_reduce_final(const double* part, int nblocks, int ncols,

@@ -34,7 +34,7 @@ EMD_PREC_SPLIT_FP16 = 4
 EXPORTS = [
     "emd_create", "emd_ctx_bytes", "emd_destroy", "emd_last_error", "emd_set_stream",
     "emd_set_frames", "emd_set_x", "emd_iterate", "emd_get_x", "emd_loglik",
-    "emd_set_precision", "emd_get_numerator", "emd_get_weights",
+    "emd_set_precision", "emd_get_numerator", "emd_get_weights", "emd_frame_stats_noalloc",
 ]
 
 
@@ -84,6 +84,8 @@ def load(build_if_missing: bool = False):
         lib.emd_set_precision.argtypes = [vp, i]
         lib.emd_get_numerator.argtypes = [vp, vp]
         lib.emd_get_weights.argtypes = [vp, vp]
+        lib.emd_frame_stats_noalloc.argtypes = [vp, vp, vp, i, i, i, vp, vp]
+        lib.emd_frame_stats_noalloc.restype = i
         for name in ("emd_set_stream", "emd_set_frames", "emd_set_x", "emd_iterate",
                      "emd_get_x", "emd_loglik", "emd_set_precision", "emd_get_numerator",
                      "emd_get_weights"):
@@ -176,6 +178,18 @@ def emd_loglik(ctx):
     ll, chi = C.c_double(), C.c_double()
     _check(load().emd_loglik(ctx, C.byref(ll), C.byref(chi)))
     return ll.value, chi.value
+
+
+def emd_frame_stats_noalloc(y, v, mask, H: int, W: int, n: int, out, stream=None) -> None:
+    """Per-exposure FP64 statistics (n x 4 doubles into the device tensor
+    ``out``) from device tensors y, v, mask; allocates no device memory."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    if out is None:
+        raise TypeError("out: need a device tensor of n*4 float64")
+    _check(load().emd_frame_stats_noalloc(_ptr(y, np.float32, "y"), _ptr(v, np.float32, "v"),
+                                          _ptr(mask, np.uint8, "mask"), H, W, n,
+                                          out.data_ptr(), stream))
 
 
 def emd_set_precision(ctx, mode: int) -> None:
