@@ -86,6 +86,14 @@ struct emd_ctx {
   double logdet = 0.0, suy = 0.0, su = 0.0;
   bool frames = false;
   int prec = EMD_PREC_FP32;
+  // tensor-core path (allocated when a tensor-core mode is first selected)
+  emd::TcShape ts{};
+  char* tc_arena = nullptr;
+  size_t tc_bytes = 0;
+  uint16_t* xb = nullptr;
+  uint16_t* hank = nullptr;
+  CUtensorMap xmap;
+  bool hank_ready = false;
 };
 
 namespace {
@@ -256,6 +264,7 @@ void emd_destroy(emd_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   cudaFree(c->arena);
+  if (c->tc_arena) cudaFree(c->tc_arena);
   delete c;
 }
 
@@ -275,8 +284,46 @@ int emd_set_precision(emd_ctx* c, int mode) {
     set_err("unknown precision mode %d", mode);
     return EMD_EINVAL;
   }
-  set_err("precision mode %d is not built into this library", mode);
-  return EMD_EUNSUPPORTED;
+  if (mode == EMD_PREC_FP16 || mode == EMD_PREC_SPLIT_FP16) {
+    set_err("precision mode %d is not built into this library", mode);
+    return EMD_EUNSUPPORTED;
+  }
+  DeviceGuard dg(c->device);
+  emd::TcShape t;
+  const char* why = nullptr;
+  if (!emd::make_tc_shape(c->s, mode, &t, &why)) {
+    set_err("emd_set_precision: %s", why);
+    return EMD_EUNSUPPORTED;
+  }
+  const size_t need = emd::tc_buffer_bytes(c->s, t);
+  if (!c->tc_arena || c->tc_bytes < need) {
+    if (c->tc_arena) {
+      CK(cudaStreamSynchronize(c->st));
+      cudaFree(c->tc_arena);
+      c->tc_arena = nullptr;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_err("emd_set_precision: cudaMalloc(%zu) failed: %s", need, cudaGetErrorString(e));
+      return EMD_ENOMEM;
+    }
+    CK(cudaMemset(p, 0, need));
+    c->tc_arena = static_cast<char*>(p);
+    c->tc_bytes = need;
+  }
+  const size_t xb_bytes = (4ull * c->s.R2 * c->s.g.plane * sizeof(uint16_t) + 255) & ~(size_t)255;
+  c->xb = reinterpret_cast<uint16_t*>(c->tc_arena);
+  c->hank = reinterpret_cast<uint16_t*>(c->tc_arena + xb_bytes);
+  if (emd::make_x_tensormap(c->s, t, c->xb, &c->xmap) != 0) {
+    set_err("emd_set_precision: cuTensorMapEncodeTiled failed");
+    return EMD_ECUDA;
+  }
+  c->ts = t;
+  c->prec = mode;
+  c->hank_ready = false;
+  return EMD_OK;
 }
 
 int emd_set_frames(emd_ctx* c, const float* y, const float* v, const float* f,
@@ -289,6 +336,7 @@ int emd_set_frames(emd_ctx* c, const float* y, const float* v, const float* f,
   DeviceGuard dg(c->device);
   const Shape& s = c->s;
   c->frames = false;
+  c->hank_ready = false;
   const size_t npix = (size_t)s.n * s.H * s.W;
   if (int rc = put_planes(c, c->y, y, s.n)) return rc;
   if (int rc = put_planes(c, c->u, v, s.n)) return rc;  // v, converted in place below
@@ -364,6 +412,31 @@ int emd_iterate(emd_ctx* c, int k) {
     return EMD_EINVAL;
   }
   DeviceGuard dg(c->device);
+  if (c->prec != EMD_PREC_FP32 && k > 0) {
+    // tensor-core path: 16-bit operands of the PSFs (once per frame set) and
+    // of the current x, then one kernel launch per iteration
+    if (!c->hank_ready) {
+      CK(emd::launch_build_hankel(c->s, c->ts, c->kf, c->ka, c->hank, 1.0f, c->st));
+      c->hank_ready = true;
+    }
+    CK(emd::launch_split_x(c->s, c->ts, c->x[c->cur], c->xb, c->cur, 1.0f, c->st));
+    for (int it = 0; it < k; ++it) {
+      emd::TcLaunch L{};
+      L.x = c->x[c->cur];
+      L.xn = c->x[c->cur ^ 1];
+      L.N = c->N;
+      L.u = c->u;
+      L.xb = c->xb;
+      L.hank = c->hank;
+      L.pp = c->cur;
+      L.zscale = L.wscale = L.dscale = L.xscale_next = 1.0f;
+      L.write_xb = 1;
+      L.err = c->err;
+      CK(emd::launch_tc_iter(c->s, c->ts, L, c->xmap, c->st));
+      c->cur ^= 1;
+    }
+    return EMD_OK;
+  }
   for (int it = 0; it < k; ++it) {
     emd::FusedArgs a = fused_args(c);
     CK(emd::launch_fused(c->s, a, 0, c->part, c->st));

@@ -152,7 +152,7 @@ template <int RY, int RX, bool CHECK>
 __device__ __forceinline__ void corr_row(float (&acc)[RY][RX], const float* __restrict__ row,
                                          const float* __restrict__ ks, int KP, int Kc, int s) {
   const float4* row4 = reinterpret_cast<const float4*>(row);
-#pragma unroll 1
+#pragma unroll 2
   for (int bq = 0; bq < (KP >> 2); ++bq) {
     float xv[RX + 4];
 #pragma unroll
@@ -168,13 +168,16 @@ __device__ __forceinline__ void corr_row(float (&acc)[RY][RX], const float* __re
       const int a = s - p;
       if (!CHECK || (a >= 0 && a < Kc)) {
         const float4 kv = reinterpret_cast<const float4*>(ks + a * KP)[bq];
+        // one tap at a time across the 16 outputs: each accumulator still
+        // takes its taps in order, consecutive FMAs share the kernel operand
 #pragma unroll
-        for (int c = 0; c < RX; ++c) {
-          acc[p][c] = fmaf(kv.x, xv[c + 0], acc[p][c]);
-          acc[p][c] = fmaf(kv.y, xv[c + 1], acc[p][c]);
-          acc[p][c] = fmaf(kv.z, xv[c + 2], acc[p][c]);
-          acc[p][c] = fmaf(kv.w, xv[c + 3], acc[p][c]);
-        }
+        for (int c = 0; c < RX; ++c) acc[p][c] = fmaf(kv.x, xv[c + 0], acc[p][c]);
+#pragma unroll
+        for (int c = 0; c < RX; ++c) acc[p][c] = fmaf(kv.y, xv[c + 1], acc[p][c]);
+#pragma unroll
+        for (int c = 0; c < RX; ++c) acc[p][c] = fmaf(kv.z, xv[c + 2], acc[p][c]);
+#pragma unroll
+        for (int c = 0; c < RX; ++c) acc[p][c] = fmaf(kv.w, xv[c + 3], acc[p][c]);
       }
     }
   }

@@ -19,10 +19,11 @@
 //     (the forward model as a correlation) and ka = unflipped (the adjoint).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/emd.h"
+#include "emd.h"
 
 namespace emd {
 
@@ -99,5 +100,41 @@ cudaError_t launch_scatter_latent(const Shape& s, const float* nat, float* plane
                                   int clamp_neg, cudaStream_t st);
 cudaError_t launch_gather_latent(const Shape& s, const float* planes, float* nat,
                                  cudaStream_t st);
+
+// ---- tensor-core path (emd_tc.cu) ----
+struct TcShape {
+  int mode, fp16, nprod;
+  int TC;           // Den columns per CTA (64); Den rows per CTA = 128 (MMA M)
+  int Nf, Kf, Ka;   // forward N, forward K extent, adjoint K extent (= Nf)
+  int XRp, WRp;     // staged x-band rows and w rows (multiples of 8)
+  int Sf, Sa;       // Hankel core matrices per filter row (forward, adjoint)
+  int gxt, gyt;     // tiles
+  int stage_bytes;  // one ring stage (forward hi + lo)
+  int hank_block;   // bytes of the Hankel block of one (t, phi, a)
+  size_t smem;
+};
+
+struct TcLaunch {
+  const float* x;
+  float* xn;
+  const float* N;
+  const float* u;
+  uint16_t* xb;          // [2 ping-pong][2 hi/lo][R2] 16-bit planes
+  const uint16_t* hank;  // Hankel blocks
+  int pp;                // ping-pong slot of the current x
+  float zscale, wscale, dscale, xscale_next;
+  int write_xb;
+  int* err;
+};
+
+bool make_tc_shape(const Shape& s, int mode, TcShape* t, const char** why);
+size_t tc_buffer_bytes(const Shape& s, const TcShape& t);
+int make_x_tensormap(const Shape& s, const TcShape& t, void* xb, CUtensorMap* map);
+cudaError_t launch_build_hankel(const Shape& s, const TcShape& t, const float* kf, const float* ka,
+                                uint16_t* hank, float gscale, cudaStream_t st);
+cudaError_t launch_split_x(const Shape& s, const TcShape& t, const float* x, uint16_t* xb, int pp,
+                           float xscale, cudaStream_t st);
+cudaError_t launch_tc_iter(const Shape& s, const TcShape& t, const TcLaunch& L,
+                           const CUtensorMap& map, cudaStream_t st);
 
 }  // namespace emd

@@ -1,0 +1,97 @@
+"""Tensor-core (tcgen05 Toeplitz GEMM) forms of the EM iteration vs the FP64
+oracle, through the C ABI.
+
+Tolerances follow from the operand rounding (FP32 accumulation in tensor
+memory):
+  * BF16, one product: x, w and the PSF taps are rounded to 8 significant
+    bits (unit roundoff 2^-9); with non-negative terms a sum of products
+    keeps a relative error of at most ~3 * 2^-9, and one update x N / Den
+    inherits it: relative L2 <= 5e-3 after one iteration.
+  * split BF16 (x_hi f_hi + x_hi f_lo + x_lo f_hi): the dropped x_lo f_lo
+    term and the residue rounding are ~2^-16 relative per product: relative
+    L2 <= 1e-4 after one iteration (the bar the split form must meet).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+BF16, SPLIT_BF16 = 1, 3
+TOL1 = {BF16: 5e-3, SPLIT_BF16: 1e-4}
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def start(p, seed=0):
+    g = np.random.default_rng(seed)
+    return (g.uniform(0.5, 1.5, (p.r * p.H, p.r * p.W)) * max(np.nanmean(p.y), 1.0)
+            / p.r ** 2).astype(np.float32)
+
+
+def run(p, x0, k, mode):
+    from paper_2302_05804_gb300 import emd
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    try:
+        d.set_frames(p.y, p.v, p.f, p.mask)
+        d.set_precision(mode)
+        d.set_x(x0)
+        d.iterate(k)
+        return d.x()
+    finally:
+        d.close()
+
+
+CASES = [
+    ("parity", {}),
+    ("hsc", dict(H=130, W=257, n=2, K=43, mask_frac=0.05, n_points=80, n_gal=2)),
+    ("hsc", dict(H=256, W=192, n=3, K=15, r=2, fwhm=(3.0, 6.0), mask_frac=0.05,
+                 n_points=60, n_gal=2)),
+    ("hsc", dict(H=5, W=7, n=2, K=9, mask_frac=0.0, n_points=3, n_gal=1)),
+    ("hsc", dict(H=64, W=64, n=1, K=1, mask_frac=0.1, n_points=10, n_gal=1)),
+]
+
+
+@pytest.mark.parametrize("mode", [BF16, SPLIT_BF16])
+@pytest.mark.parametrize("recipe,kw", CASES)
+def test_tc_one_iteration(mode, recipe, kw):
+    p = synth.make_problem(recipe, **kw)
+    x0 = start(p, seed=p.H)
+    x1 = run(p, x0, 1, mode)
+    u, y, N, _ = oracle.prepare(p)
+    xo = oracle.em_run(x0, N, u, p.f, 1, p.r)
+    err = rel_l2(x1, xo)
+    print(f"mode {mode} {recipe} {kw.get('H', 256)}x{kw.get('W', 256)} K={p.K} r={p.r}: "
+          f"rel L2 after 1 iteration = {err:.3e}")
+    assert err <= TOL1[mode]
+    assert (x1 >= 0).all()
+
+
+def test_tc_split_ten_iterations_and_mode_switch():
+    from paper_2302_05804_gb300 import emd
+    p = synth.make_problem("parity", mask_frac=0.05)
+    x0 = start(p)
+    u, y, N, _ = oracle.prepare(p)
+    x10 = run(p, x0, 10, SPLIT_BF16)
+    err = rel_l2(x10, oracle.em_run(x0, N, u, p.f, 10))
+    print(f"split bf16: rel L2 after 10 iterations = {err:.3e}")
+    assert err <= 1e-3
+    # switching back to FP32 in the same context gives the FP32 result
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    d.set_frames(p.y, p.v, p.f, p.mask)
+    d.set_precision(SPLIT_BF16)
+    d.set_x(x0)
+    d.iterate(2)
+    d.set_precision(0)
+    d.set_x(x0)
+    d.iterate(3)
+    a = d.x()
+    d.close()
+    b = run(p, x0, 3, 0)
+    np.testing.assert_array_equal(a, b)
