@@ -136,6 +136,54 @@ int emd_set_precision(emd_ctx *ctx, int mode);
 int emd_get_numerator(emd_ctx *ctx, float *out);
 int emd_get_weights(emd_ctx *ctx, float *out);
 
+/* ---------------------------------------------------------------------------
+ * Batching: many deconvolution jobs (contexts of any shapes) advance one EM
+ * iteration per emd_batch_step, all in ONE persistent kernel launch (CUDA
+ * pairs of CTAs claim (job, 128x128 tile) work items from a device counter;
+ * items of finished jobs are skipped). The step (counter reset, persistent
+ * kernel, per-job advance) is captured once as a CUDA graph and replayed.
+ * Jobs may join or leave between steps (continuous batching); a job gives
+ * bit-for-bit the same iterates in a batch as with emd_iterate alone.
+ *
+ * Work-list order and the number of resident CTA pairs are chosen by an
+ * online autotuner: the first steps of each new job mix (a signature of the
+ * active jobs' size class, Kc, r and exposure count) each run one candidate
+ * configuration, timed with CUDA events; the fastest is kept for that mix.
+ * Batched jobs use the FP32 kernel (EMD_PREC_FP32).
+ * -------------------------------------------------------------------------*/
+typedef struct emd_batch emd_batch;
+
+/* New batch with room for max_jobs (1..4096) jobs; NULL on error. The batch
+ * runs on a stream of its own. */
+emd_batch *emd_batch_create(int max_jobs);
+void emd_batch_destroy(emd_batch *b);
+
+/* Add a context that has frames (and, optionally, a start from emd_set_x)
+ * to run `iterations` more iterations. Returns the slot (>= 0) or a negative
+ * EMD_E* code. The context must not be iterated on its own while it is in
+ * the batch. */
+int emd_batch_add(emd_batch *b, emd_ctx *job, int iterations);
+
+/* Remove the job in `slot` (finished or not); its context keeps the iterate
+ * reached so far. */
+int emd_batch_remove(emd_batch *b, int slot);
+
+/* One iteration for every job that has iterations left (asynchronous on the
+ * batch stream). *finished (may be NULL) receives the number of jobs that
+ * ran their last iteration in this step. */
+int emd_batch_step(emd_batch *b, int *finished);
+
+/* Iterations left for the job in `slot` (0 when finished), or an error. */
+int emd_batch_remaining(emd_batch *b, int slot);
+
+/* Wait for all queued steps; call before reading a job's results with
+ * emd_get_x / emd_loglik. EMD_ETIMEOUT if a bounded device wait gave up. */
+int emd_batch_sync(emd_batch *b);
+
+/* The autotuner's current choice: resident CTA pairs, work order (0 =
+ * job-major, 1 = most expensive jobs first) and the maximum pairs. */
+int emd_batch_config(emd_batch *b, int *clusters, int *order, int *max_clusters);
+
 /*
  * emd_frame_stats_noalloc -- per-exposure FP64 frame statistics without any
  * device allocation. The paper has no counterpart: this exists for callers

@@ -6,7 +6,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <map>
 #include <string>
+#include <vector>
 
 #include "emd_internal.cuh"
 
@@ -94,6 +97,9 @@ struct emd_ctx {
   uint16_t* hank = nullptr;
   CUtensorMap xmap;
   bool hank_ready = false;
+  float* scales = nullptr;       // device {z, w, Den, x} operand scales
+  unsigned int* xmax = nullptr;  // device max of x (FP16 modes)
+  float gscale = 1.f, umax = 0.f, fsum = 0.f;
 };
 
 namespace {
@@ -284,10 +290,6 @@ int emd_set_precision(emd_ctx* c, int mode) {
     set_err("unknown precision mode %d", mode);
     return EMD_EINVAL;
   }
-  if (mode == EMD_PREC_FP16 || mode == EMD_PREC_SPLIT_FP16) {
-    set_err("precision mode %d is not built into this library", mode);
-    return EMD_EUNSUPPORTED;
-  }
   DeviceGuard dg(c->device);
   emd::TcShape t;
   const char* why = nullptr;
@@ -316,6 +318,8 @@ int emd_set_precision(emd_ctx* c, int mode) {
   const size_t xb_bytes = (4ull * c->s.R2 * c->s.g.plane * sizeof(uint16_t) + 255) & ~(size_t)255;
   c->xb = reinterpret_cast<uint16_t*>(c->tc_arena);
   c->hank = reinterpret_cast<uint16_t*>(c->tc_arena + xb_bytes);
+  c->scales = reinterpret_cast<float*>(c->tc_arena + need - 256);
+  c->xmax = reinterpret_cast<unsigned int*>(c->tc_arena + need - 128);
   if (emd::make_x_tensormap(c->s, t, c->xb, &c->xmap) != 0) {
     set_err("emd_set_precision: cuTensorMapEncodeTiled failed");
     return EMD_ECUDA;
@@ -415,12 +419,48 @@ int emd_iterate(emd_ctx* c, int k) {
   if (c->prec != EMD_PREC_FP32 && k > 0) {
     // tensor-core path: 16-bit operands of the PSFs (once per frame set) and
     // of the current x, then one kernel launch per iteration
+    const bool fp16 = c->ts.fp16 != 0;
     if (!c->hank_ready) {
-      CK(emd::launch_build_hankel(c->s, c->ts, c->kf, c->ka, c->hank, 1.0f, c->st));
+      const Shape& s = c->s;
+      c->gscale = 1.f;
+      if (fp16) {
+        // PSF scale and the bound on |z| / max x, from the kernels on the host
+        const size_t nk = (size_t)s.n * s.R2 * s.Kc * s.KP;
+        std::vector<float> kf(nk);
+        CK(cudaMemcpyAsync(kf.data(), c->kf, nk * sizeof(float), cudaMemcpyDeviceToHost, c->st));
+        CK(emd::launch_max_nonneg(c->u, (long long)s.n * s.g.plane, c->xmax, c->st));
+        unsigned int ub = 0;
+        CK(cudaMemcpyAsync(&ub, c->xmax, sizeof(ub), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        float gmax = 0.f, fsum = 0.f;
+        for (int t = 0; t < s.n; ++t) {
+          float tsum = 0.f;
+          for (size_t e = (size_t)t * s.R2 * s.Kc * s.KP; e < (size_t)(t + 1) * s.R2 * s.Kc * s.KP; ++e) {
+            gmax = fmaxf(gmax, fabsf(kf[e]));
+            tsum += fabsf(kf[e]);
+          }
+          fsum = fmaxf(fsum, tsum);
+        }
+        memcpy(&c->umax, &ub, sizeof(float));
+        c->fsum = fsum;
+        if (gmax > 0.f) c->gscale = exp2f(floorf(log2f(16384.f / gmax)));
+      } else {
+        const float one[4] = {1.f, 1.f, 1.f, 1.f};
+        CK(cudaMemcpyAsync(c->scales, one, sizeof(one), cudaMemcpyHostToDevice, c->st));
+        CK(cudaStreamSynchronize(c->st));
+      }
+      CK(emd::launch_build_hankel(c->s, c->ts, c->kf, c->ka, c->hank, c->gscale, c->st));
       c->hank_ready = true;
     }
-    CK(emd::launch_split_x(c->s, c->ts, c->x[c->cur], c->xb, c->cur, 1.0f, c->st));
     for (int it = 0; it < k; ++it) {
+      if (fp16 || it == 0) {
+        if (fp16) {
+          CK(emd::launch_max_nonneg(c->x[c->cur], (long long)c->s.R2 * c->s.g.plane, c->xmax,
+                                    c->st));
+          CK(emd::launch_fp16_scales(c->xmax, c->gscale, c->umax, c->fsum, c->scales, c->st));
+        }
+        CK(emd::launch_split_x(c->s, c->ts, c->x[c->cur], c->xb, c->cur, c->scales, c->st));
+      }
       emd::TcLaunch L{};
       L.x = c->x[c->cur];
       L.xn = c->x[c->cur ^ 1];
@@ -429,8 +469,8 @@ int emd_iterate(emd_ctx* c, int k) {
       L.xb = c->xb;
       L.hank = c->hank;
       L.pp = c->cur;
-      L.zscale = L.wscale = L.dscale = L.xscale_next = 1.0f;
-      L.write_xb = 1;
+      L.scales = c->scales;
+      L.write_xb = fp16 ? 0 : 1;
       L.err = c->err;
       CK(emd::launch_tc_iter(c->s, c->ts, L, c->xmap, c->st));
       c->cur ^= 1;
@@ -485,6 +525,362 @@ int emd_loglik(emd_ctx* c, double* out, double* chi2) {
   if (int rc = check_device_error(c)) return rc;
   *out = -0.5 * (h + c->logdet);
   if (chi2) *chi2 = h;
+  return EMD_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batching: one persistent kernel per step over all active jobs
+// ===========================================================================
+
+namespace {
+
+constexpr int kBatchItemCap = 1 << 20;  // (job, tile) work items per step
+
+struct TuneChoice {
+  int clusters = 0;
+  int order = 1;  // 0: job-major, 1: most expensive jobs first
+};
+
+}  // namespace
+
+struct emd_batch {
+  int max_jobs = 0;
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::vector<emd_ctx*> job;   // per slot; nullptr when free
+  std::vector<int> remaining;  // host mirror of the device table
+  char* arena = nullptr;
+  emd::BatchJob* d_jobs = nullptr;
+  int2* d_items = nullptr;
+  int* d_nitems = nullptr;
+  int* d_counter = nullptr;
+  int* d_err = nullptr;
+  size_t smem = 0;
+  int max_clusters = 0;
+  bool dirty = true;
+  int njobs_table = 0;
+  // captured step graphs, one per cluster count
+  std::map<int, cudaGraphExec_t> graphs;
+  // autotuner: decision per composition, and the candidates still to try
+  std::map<std::string, TuneChoice> tuned;
+  std::string sig;
+  std::vector<TuneChoice> trying;
+  std::vector<float> trial_ms;
+  TuneChoice cur;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  long long steps = 0;
+};
+
+namespace {
+
+std::string composition_signature(emd_batch* b) {
+  std::vector<std::string> parts;
+  for (size_t i = 0; i < b->job.size(); ++i) {
+    emd_ctx* c = b->job[i];
+    if (!c || b->remaining[i] <= 0) continue;
+    int sb = 0;
+    for (int v = c->s.H > c->s.W ? c->s.H : c->s.W; v > 1; v >>= 1) ++sb;
+    char buf[64];
+    snprintf(buf, sizeof(buf), "%d.%d.%d.%d", sb, c->s.Kc, c->s.r, (c->s.n + 7) / 8);
+    parts.push_back(buf);
+  }
+  std::sort(parts.begin(), parts.end());
+  std::string out;
+  for (auto& p : parts) out += p + ";";
+  return out;
+}
+
+int upload_table(emd_batch* b) {
+  std::vector<emd::BatchJob> tab(b->job.size());
+  struct It { long long cost; int job, tile; };
+  std::vector<It> its;
+  for (size_t i = 0; i < b->job.size(); ++i) {
+    emd_ctx* c = b->job[i];
+    emd::BatchJob& J = tab[i];
+    memset(&J, 0, sizeof(J));
+    if (!c) continue;
+    J.s = c->s;
+    for (int k = 0; k < 2; ++k) {
+      const int save = c->cur;
+      c->cur = k;
+      J.a[k] = fused_args(c);
+      c->cur = save;
+    }
+    J.cur = c->cur;
+    J.remaining = b->remaining[i];
+    if (J.remaining <= 0) continue;
+    const long long cost = (long long)c->s.n * c->s.R2 * c->s.Kc * c->s.Kc;
+    for (int t = 0; t < c->s.gx * c->s.gy; ++t) its.push_back({cost, (int)i, t});
+  }
+  if (its.size() > (size_t)kBatchItemCap) {
+    set_err("emd_batch_step: more than %d tiles in one step", kBatchItemCap);
+    return EMD_EINVAL;
+  }
+  if (b->cur.order == 1)
+    std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+  std::vector<int2> items(its.size());
+  for (size_t k = 0; k < its.size(); ++k) items[k] = make_int2(its[k].job, its[k].tile);
+  const int n = (int)items.size();
+  CK(cudaMemcpyAsync(b->d_jobs, tab.data(), tab.size() * sizeof(emd::BatchJob),
+                     cudaMemcpyHostToDevice, b->st));
+  if (n) CK(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int2),
+                            cudaMemcpyHostToDevice, b->st));
+  CK(cudaMemcpyAsync(b->d_nitems, &n, sizeof(int), cudaMemcpyHostToDevice, b->st));
+  CK(cudaStreamSynchronize(b->st));
+  b->njobs_table = (int)tab.size();
+  return EMD_OK;
+}
+
+int get_graph(emd_batch* b, int clusters, cudaGraphExec_t* out) {
+  auto it = b->graphs.find(clusters);
+  if (it != b->graphs.end()) {
+    *out = it->second;
+    return EMD_OK;
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = emd::launch_batch(b->d_jobs, b->max_jobs, b->d_items, b->d_nitems, b->d_counter,
+                                    b->d_err, clusters, b->smem, b->st);
+  cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    set_err("batch graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return EMD_ECUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    set_err("batch graph instantiate failed: %s", cudaGetErrorString(e));
+    return EMD_ECUDA;
+  }
+  b->graphs[clusters] = ex;
+  *out = ex;
+  return EMD_OK;
+}
+
+int batch_check(emd_batch* b) {
+  if (!b) {
+    set_err("null batch");
+    return EMD_EINVAL;
+  }
+  return EMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+emd_batch* emd_batch_create(int max_jobs) {
+  if (max_jobs < 1 || max_jobs > 4096) {
+    set_err("emd_batch_create: max_jobs must be in [1, 4096]");
+    return nullptr;
+  }
+  emd_batch* b = new emd_batch();
+  b->max_jobs = max_jobs;
+  cudaGetDevice(&b->device);
+  b->job.assign(max_jobs, nullptr);
+  b->remaining.assign(max_jobs, 0);
+  const size_t jb = (sizeof(emd::BatchJob) * max_jobs + 255) & ~(size_t)255;
+  const size_t ib = (sizeof(int2) * (size_t)kBatchItemCap + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (cudaMalloc(&p, jb + ib + 1024) != cudaSuccess) {
+    cudaGetLastError();
+    set_err("emd_batch_create: out of device memory");
+    delete b;
+    return nullptr;
+  }
+  b->arena = static_cast<char*>(p);
+  cudaMemset(b->arena, 0, jb + ib + 1024);
+  b->d_jobs = reinterpret_cast<emd::BatchJob*>(b->arena);
+  b->d_items = reinterpret_cast<int2*>(b->arena + jb);
+  b->d_nitems = reinterpret_cast<int*>(b->arena + jb + ib);
+  b->d_counter = reinterpret_cast<int*>(b->arena + jb + ib + 256);
+  b->d_err = reinterpret_cast<int*>(b->arena + jb + ib + 512);
+  b->smem = emd::batch_smem_bytes();
+  b->max_clusters = emd::batch_max_clusters(b->smem);
+  if (b->max_clusters <= 0) {
+    set_err("emd_batch_create: the persistent kernel cannot be resident");
+    cudaFree(b->arena);
+    delete b;
+    return nullptr;
+  }
+  b->cur.clusters = b->max_clusters;
+  if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+    set_err("emd_batch_create: stream creation failed");
+    cudaFree(b->arena);
+    delete b;
+    return nullptr;
+  }
+  b->own_stream = true;
+  cudaEventCreate(&b->e0);
+  cudaEventCreate(&b->e1);
+  return b;
+}
+
+void emd_batch_destroy(emd_batch* b) {
+  if (!b) return;
+  DeviceGuard dg(b->device);
+  cudaStreamSynchronize(b->st);
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  if (b->own_stream) cudaStreamDestroy(b->st);
+  cudaEventDestroy(b->e0);
+  cudaEventDestroy(b->e1);
+  cudaFree(b->arena);
+  delete b;
+}
+
+int emd_batch_add(emd_batch* b, emd_ctx* c, int iterations) {
+  if (int rc = batch_check(b)) return rc;
+  if (int rc = check_ctx(c, true)) return rc;
+  if (iterations < 0) {
+    set_err("emd_batch_add: iterations must be >= 0");
+    return EMD_EINVAL;
+  }
+  if (c->prec != EMD_PREC_FP32) {
+    set_err("emd_batch_add: batched jobs run the FP32 kernel (set precision FP32)");
+    return EMD_EUNSUPPORTED;
+  }
+  if (c->device != b->device) {
+    set_err("emd_batch_add: job and batch are on different devices");
+    return EMD_EINVAL;
+  }
+  for (int i = 0; i < b->max_jobs; ++i)
+    if (b->job[i] == c) {
+      set_err("emd_batch_add: job already in the batch");
+      return EMD_EINVAL;
+    }
+  for (int i = 0; i < b->max_jobs; ++i) {
+    if (!b->job[i]) {
+      // the job's own stream work (set_frames, set_x) must be done first
+      DeviceGuard dg(c->device);
+      CK(cudaStreamSynchronize(c->st));
+      b->job[i] = c;
+      b->remaining[i] = iterations;
+      b->dirty = true;
+      return i;
+    }
+  }
+  set_err("emd_batch_add: no free slot (max_jobs = %d)", b->max_jobs);
+  return EMD_ESTATE;
+}
+
+int emd_batch_remove(emd_batch* b, int slot) {
+  if (int rc = batch_check(b)) return rc;
+  if (slot < 0 || slot >= b->max_jobs || !b->job[slot]) {
+    set_err("emd_batch_remove: no job in slot %d", slot);
+    return EMD_EINVAL;
+  }
+  DeviceGuard dg(b->device);
+  CK(cudaStreamSynchronize(b->st));
+  b->job[slot] = nullptr;
+  b->remaining[slot] = 0;
+  b->dirty = true;
+  return EMD_OK;
+}
+
+int emd_batch_remaining(emd_batch* b, int slot) {
+  if (int rc = batch_check(b)) return rc;
+  if (slot < 0 || slot >= b->max_jobs || !b->job[slot]) {
+    set_err("emd_batch_remaining: no job in slot %d", slot);
+    return EMD_EINVAL;
+  }
+  return b->remaining[slot];
+}
+
+int emd_batch_step(emd_batch* b, int* finished) {
+  if (int rc = batch_check(b)) return rc;
+  DeviceGuard dg(b->device);
+  if (finished) *finished = 0;
+  int active = 0;
+  for (int i = 0; i < b->max_jobs; ++i)
+    if (b->job[i] && b->remaining[i] > 0) ++active;
+  if (!active) return EMD_OK;
+  // autotuner: a new composition tries each candidate on one real step
+  const std::string sig = composition_signature(b);
+  bool timing = false;
+  if (sig != b->sig) {
+    b->sig = sig;
+    b->trying.clear();
+    b->trial_ms.clear();
+    auto it = b->tuned.find(sig);
+    if (it != b->tuned.end()) {
+      if (it->second.order != b->cur.order) b->dirty = true;
+      b->cur = it->second;
+    } else {
+      const int full = b->max_clusters, part = b->max_clusters - b->max_clusters / 4;
+      for (int order = 0; order < 2; ++order)
+        for (int cl : {full, part}) b->trying.push_back({cl, order});
+      b->dirty = true;
+    }
+  }
+  if (!b->trying.empty()) {
+    const TuneChoice next = b->trying[b->trial_ms.size()];
+    if (next.order != b->cur.order) b->dirty = true;
+    b->cur = next;
+    timing = true;
+  }
+  if (b->dirty) {
+    if (int rc = upload_table(b)) return rc;
+    b->dirty = false;
+  }
+  cudaGraphExec_t ex;
+  if (int rc = get_graph(b, b->cur.clusters, &ex)) return rc;
+  if (timing) CK(cudaEventRecord(b->e0, b->st));
+  CK(cudaGraphLaunch(ex, b->st));
+  if (timing) {
+    CK(cudaEventRecord(b->e1, b->st));
+    CK(cudaEventSynchronize(b->e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, b->e0, b->e1);
+    b->trial_ms.push_back(ms);
+    if (b->trial_ms.size() == b->trying.size()) {
+      size_t best = 0;
+      for (size_t k = 1; k < b->trial_ms.size(); ++k)
+        if (b->trial_ms[k] < b->trial_ms[best]) best = k;
+      if (b->trying[best].order != b->cur.order) b->dirty = true;
+      b->cur = b->trying[best];
+      b->tuned[b->sig] = b->cur;
+      b->trying.clear();
+    }
+  }
+  ++b->steps;
+  // host mirror of the advance kernel
+  for (int i = 0; i < b->max_jobs; ++i) {
+    emd_ctx* c = b->job[i];
+    if (!c || b->remaining[i] <= 0) continue;
+    b->remaining[i] -= 1;
+    c->cur ^= 1;
+    if (b->remaining[i] == 0) {
+      if (finished) ++*finished;
+      b->dirty = true;  // its tiles leave the work list
+    }
+  }
+  return EMD_OK;
+}
+
+int emd_batch_sync(emd_batch* b) {
+  if (int rc = batch_check(b)) return rc;
+  DeviceGuard dg(b->device);
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+  CK(cudaStreamSynchronize(b->st));
+  if (h & emd::kErrTimeout) {
+    CK(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->st));
+    set_err("a bounded device-side wait gave up");
+    return EMD_ETIMEOUT;
+  }
+  return EMD_OK;
+}
+
+int emd_batch_config(emd_batch* b, int* clusters, int* order, int* max_clusters) {
+  if (int rc = batch_check(b)) return rc;
+  if (clusters) *clusters = b->cur.clusters;
+  if (order) *order = b->cur.order;
+  if (max_clusters) *max_clusters = b->max_clusters;
   return EMD_OK;
 }
 

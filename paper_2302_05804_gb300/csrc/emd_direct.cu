@@ -224,13 +224,14 @@ __device__ __forceinline__ double block_sum_f64(double v, double* red /* >= 8 */
 //   rows (t+1) ... and a final wait [B_{n-1}] before exit, so no CTA
 //   overwrites or releases shared memory its peer may still be reading.
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
-    fused_kernel(const Shape s, const FusedArgs a, const int mode, double* __restrict__ part) {
-  extern __shared__ __align__(128) float smem[];
-  __shared__ double red[kThreads / 32];
+// One 128 x 128 tile (rows i0.., cols j0..) handled by CTA q of a pair; the
+// caller owns the mbarrier, its phase, the timeout flag and the chi-square
+// accumulator so a persistent kernel can run many tiles per CTA pair.
+__device__ __forceinline__ void fused_tile(const Shape& s, const FusedArgs& a, const int mode,
+                                           const int i0, const int j0, const int q, float* smem,
+                                           uint64_t* mbar, uint32_t& phase, bool& timed_out,
+                                           double& chi) {
   cg::cluster_group cluster = cg::this_cluster();
-  const int q = (int)cluster.block_rank();
-  const int i0 = blockIdx.y * kTile, j0 = (blockIdx.x >> 1) * kTile;
   const int tid = threadIdx.x;
   const Geom& g = s.g;
   const int hc = s.hc, Kc = s.Kc, KP = s.KP;
@@ -241,15 +242,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   float* ws_base = xs_base + xs_floats;
   float* ksf = ws_base + ws_floats;
   float* ksa = ksf + Kc * KP;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(ksa + Kc * KP);
   const SPlane xs{xs_base, s.xpitch, 2};
   const SPlane ws{ws_base, s.wpitch, 1};
 
   for (int e = tid; e < ws_floats; e += kThreads) ws_base[e] = 0.f;
-  if (tid == 0) {
-    mbar_init(mbar, 1);
-    fence_mbar_init();
-  }
   __syncthreads();
 
   // forward microtile (4 x 16) of this thread in its CTA's half region
@@ -261,9 +257,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   const int amy = (wid & 3) * 8 + (lane & 7);
   const int amx = (wid >> 2) * 4 + (lane >> 3);
 
-  uint32_t phase = 0;
-  bool timed_out = false;
-  double chi = 0.0;
   const int ccols = 16 * s.MXf;
 
   for (int t = 0; t < s.n; ++t) {
@@ -414,14 +407,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     }
   }
   if (mode == 0) cluster_wait();  // [B_{n-1}]
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    fused_kernel(const Shape s, const FusedArgs a, const int mode, double* __restrict__ part) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ double red[kThreads / 32];
+  __shared__ uint64_t mbar_s;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int q = (int)cluster.block_rank();
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar_s, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  bool timed_out = false;
+  double chi = 0.0;
+  fused_tile(s, a, mode, blockIdx.y * kTile, (blockIdx.x >> 1) * kTile, q, smem, &mbar_s, phase,
+             timed_out, chi);
   if (mode == 2) {
     const double tot = block_sum_f64(chi, red);
-    if (tid == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = tot;
   }
   if (timed_out) {
     // give the staged copies a bounded chance to land before the CTA exits
-    mbar_wait_bounded(mbar, phase ^ 1u);
-    if (tid == 0) atomicOr(a.err, kErrTimeout);
+    mbar_wait_bounded(&mbar_s, phase ^ 1u);
+    if (threadIdx.x == 0) atomicOr(a.err, kErrTimeout);
   }
 }
 
@@ -440,6 +452,105 @@ cudaError_t launch_fused(const Shape& s, const FusedArgs& a, int mode, double* p
 }
 
 int fused_blocks(const Shape& s) { return 2 * s.gx * s.gy; }
+
+// ---------------------------------------------------------------------------
+// persistent multi-job kernel: one EM iteration for every active job of a
+// batch. CTA pairs claim (job, tile) items from a device counter until the
+// work list is exhausted; items of jobs with no iterations left are skipped.
+// ---------------------------------------------------------------------------
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    batch_kernel(const BatchJob* __restrict__ jobs, const int2* __restrict__ items,
+                 const int* __restrict__ n_items, int* __restrict__ counter, int* err) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ uint64_t mbar_s;
+  __shared__ int claim_s[2];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int q = (int)cluster.block_rank();
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar_s, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  bool timed_out = false;
+  double chi = 0.0;
+  const int total = *n_items;
+  volatile int* leader_claim = cluster.map_shared_rank(claim_s, 0);
+  for (int it = 0;; ++it) {
+    if (q == 0 && threadIdx.x == 0) claim_s[it & 1] = atomicAdd(counter, 1);
+    cluster_arrive();
+    cluster_wait();  // the claim is visible to both CTAs
+    const int item = leader_claim[it & 1];
+    cluster_arrive();
+    cluster_wait();  // both read it: the leader may move on (or exit)
+    if (item >= total) break;
+    const int2 w = items[item];
+    const BatchJob& J = jobs[w.x];
+    if (J.remaining <= 0) continue;
+    const int tx = w.y % J.s.gx, ty = w.y / J.s.gx;
+    fused_tile(J.s, J.a[J.cur], 0, ty * kTile, tx * kTile, q, smem, &mbar_s, phase, timed_out,
+               chi);
+  }
+  if (timed_out) {
+    mbar_wait_bounded(&mbar_s, phase ^ 1u);
+    if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
+  }
+}
+
+// after a batch step: every job that ran advances one iteration
+__global__ void batch_advance_kernel(BatchJob* __restrict__ jobs, int njobs) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < njobs && jobs[j].remaining > 0) {
+    jobs[j].remaining -= 1;
+    jobs[j].cur ^= 1;
+  }
+}
+
+size_t batch_smem_bytes() {
+  // the largest fused-kernel footprint of any accepted shape (hc <= EMD_MAX_HC)
+  size_t m = 0;
+  for (int r = 1; r <= 2; ++r)
+    for (int K = 1; K <= 2 * EMD_MAX_HC * r + 1; K += 2) {
+      Shape s;
+      const char* why;
+      if (make_shape(256, 256, 1, K, r, &s, &why) && s.smem_fused > m) m = s.smem_fused;
+    }
+  return m;
+}
+
+int batch_max_clusters(size_t smem) {
+  static int cached = -1;
+  if (cached >= 0) return cached;
+  if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return -1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, batch_kernel, &cfg) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return -1;
+  }
+  cached = n;
+  return n;
+}
+
+cudaError_t launch_batch(const BatchJob* jobs, int njobs, const int2* items, const int* n_items,
+                         int* counter, int* err, int clusters, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  batch_kernel<<<2 * clusters, kThreads, smem, st>>>(jobs, items, n_items, counter, err);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  batch_advance_kernel<<<(njobs + 127) / 128, 128, 0, st>>>(const_cast<BatchJob*>(jobs), njobs);
+  return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------------------
 // set-up: u = mask ? 1/v : 0 (in place over v), y sanitised, FP64 sums

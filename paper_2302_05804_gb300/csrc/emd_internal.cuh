@@ -80,6 +80,20 @@ struct SetupArgs {
   int* err;
 };
 
+// one job of a batch (device-side table entry)
+struct BatchJob {
+  Shape s;
+  FusedArgs a[2];  // arguments with x = buffer c, xn = buffer c^1, for c = cur
+  int cur;         // current x buffer
+  int remaining;   // iterations still to run (0: skipped)
+};
+
+size_t batch_smem_bytes();
+int batch_max_clusters(size_t smem);
+// memset(counter) + persistent kernel + advance, all on st (graph-capturable)
+cudaError_t launch_batch(const BatchJob* jobs, int njobs, const int2* items, const int* n_items,
+                         int* counter, int* err, int clusters, size_t smem, cudaStream_t st);
+
 // sets the thread-local message returned by emd_last_error (emd_api.cu)
 void set_error_message(const char* msg);
 
@@ -122,7 +136,7 @@ struct TcLaunch {
   uint16_t* xb;          // [2 ping-pong][2 hi/lo][R2] 16-bit planes
   const uint16_t* hank;  // Hankel blocks
   int pp;                // ping-pong slot of the current x
-  float zscale, wscale, dscale, xscale_next;
+  const float* scales;   // device {z, w, Den, x} scales (all 1 for BF16)
   int write_xb;
   int* err;
 };
@@ -133,7 +147,10 @@ int make_x_tensormap(const Shape& s, const TcShape& t, void* xb, CUtensorMap* ma
 cudaError_t launch_build_hankel(const Shape& s, const TcShape& t, const float* kf, const float* ka,
                                 uint16_t* hank, float gscale, cudaStream_t st);
 cudaError_t launch_split_x(const Shape& s, const TcShape& t, const float* x, uint16_t* xb, int pp,
-                           float xscale, cudaStream_t st);
+                           const float* scales, cudaStream_t st);
+cudaError_t launch_max_nonneg(const float* v, long long count, unsigned int* out, cudaStream_t st);
+cudaError_t launch_fp16_scales(const unsigned int* xmax_bits, float gscale, float umax, float fsum,
+                               float* scales, cudaStream_t st);
 cudaError_t launch_tc_iter(const Shape& s, const TcShape& t, const TcLaunch& L,
                            const CUtensorMap& map, cudaStream_t st);
 

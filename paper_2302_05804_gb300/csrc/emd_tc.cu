@@ -241,8 +241,9 @@ __global__ void build_hankel_kernel(const Shape s, const TcShape t, const float*
 // x (fp32 planes) -> 16-bit hi and lo planes at ping-pong slot pp:
 // xb[((pp * 2 + hl) * R2 + phi) * plane + offset]
 __global__ void split_x_kernel(const Shape s, int fp16, const float* __restrict__ x,
-                               uint16_t* __restrict__ xb, int pp, float xscale) {
+                               uint16_t* __restrict__ xb, int pp, const float* __restrict__ scales) {
   const Geom& g = s.g;
+  const float xscale = scales[3];
   const long long tot = (long long)s.R2 * g.plane;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
@@ -267,14 +268,12 @@ struct TcArgs {
   uint16_t* xb;          // [2][2][R2] 16-bit planes
   const uint16_t* hank;  // Hankel blocks
   int pp;                // ping-pong slot of the current x in xb
-  float zscale;          // forward accumulator -> z
-  float wscale;          // w -> adjoint operand
-  float dscale;          // adjoint accumulator -> Den
-  float xscale_next;     // x_next -> operand (fp16 modes: unused, split pass rescales)
-  int write_xb;          // epilogue writes the next x's 16-bit planes
+  const float* scales;   // device: {forward acc -> z, w -> operand, adjoint acc -> Den, x -> operand}
+  int write_xb;          // epilogue writes the next x's 16-bit planes (BF16 modes)
   int* err;
 };
 
+template <int NPROD>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_iter_kernel(const Shape s, const TcShape t, const TcArgs A,
                    const __grid_constant__ CUtensorMap xmap) {
@@ -328,7 +327,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
-  const int nprod = t.nprod;
+  constexpr int nprod = NPROD;
+  const float zscale = A.scales[0], wscale = A.scales[1], dscale = A.scales[2],
+              xscale = A.scales[3];
   const int KSf = t.Kf / 16, KSa = t.Ka / 16;
 
   if (warp == 0) {
@@ -402,15 +403,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               bar_wait(&b_full[stage], bf_phase, abort);
               tc_fence_after();
               const uint32_t bst = ring_a + stage * t.stage_bytes;
+              // descriptor bases; a k-step advances the start-address field
+              uint64_t ah = sdesc(xs_a + a * 16, x_lbo, 128);
+              uint64_t al = ah + (xplane_b >> 4);
+              uint64_t bh = sdesc(bst, 128, 128);
+              uint64_t bl = bh + ((uint32_t)(t.Sf * 128) >> 4);
+              const uint64_t astep = (2u * x_lbo) >> 4, bstep = 256u >> 4;
+#pragma unroll 2
               for (int kk = 0; kk < KSf; ++kk) {
-                for (int pr = 0; pr < nprod; ++pr) {
-                  const int xh = (pr == 2) ? 1 : 0;  // x_lo only in the third product
-                  const int gh = (pr == 1) ? 1 : 0;  // g_lo only in the second
-                  const uint64_t ad = sdesc(xs_a + xh * xplane_b + kk * 2 * x_lbo + a * 16, x_lbo, 128);
-                  const uint64_t bd = sdesc(bst + gh * t.Sf * 128 + kk * 2 * 128, 128, 128);
-                  mma(dacc, ad, bd, idesc_f, accum);
-                  accum = 1;
+                mma(dacc, ah, bh, idesc_f, accum);
+                accum = 1;
+                if (nprod == 3) {
+                  mma(dacc, ah, bl, idesc_f, 1u);
+                  mma(dacc, al, bh, idesc_f, 1u);
                 }
+                ah += astep;
+                al += astep;
+                bh += bstep;
+                bl += bstep;
               }
               mma_commit(&b_empty[stage]);
               if (++stage == kTcStages) { stage = 0; bf_phase ^= 1u; }
@@ -429,15 +439,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             bar_wait(&b_full[stage], bf_phase, abort);
             tc_fence_after();
             const uint32_t bst = ring_a + stage * t.stage_bytes;
+            uint64_t ah = sdesc(ws_a + a * 16, w_lbo, 128);
+            uint64_t al = ah + (wplane_b >> 4);
+            uint64_t bh = sdesc(bst, 128, 128);
+            uint64_t bl = bh + ((uint32_t)(t.Sa * 128) >> 4);
+            const uint64_t astep = (2u * w_lbo) >> 4, bstep = 256u >> 4;
+            uint32_t acc = (tt > 0 || a > 0) ? 1u : 0u;
+#pragma unroll 2
             for (int kk = 0; kk < KSa; ++kk) {
-              for (int pr = 0; pr < nprod; ++pr) {
-                const int wh = (pr == 2) ? 1 : 0;
-                const int gh = (pr == 1) ? 1 : 0;
-                const uint64_t ad = sdesc(ws_a + wh * wplane_b + kk * 2 * w_lbo + a * 16, w_lbo, 128);
-                const uint64_t bd = sdesc(bst + gh * t.Sa * 128 + kk * 2 * 128, 128, 128);
-                const uint32_t acc = (tt > 0 || a > 0 || kk > 0 || pr > 0) ? 1u : 0u;
-                mma(dden, ad, bd, idesc_a, acc);
+              mma(dden, ah, bh, idesc_a, acc);
+              acc = 1u;
+              if (nprod == 3) {
+                mma(dden, ah, bl, idesc_a, 1u);
+                mma(dden, al, bh, idesc_a, 1u);
               }
+              ah += astep;
+              al += astep;
+              bh += bstep;
+              bl += bstep;
             }
             mma_commit(&b_empty[stage]);
             if (++stage == kTcStages) { stage = 0; bf_phase ^= 1u; }
@@ -456,46 +475,67 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int tt = 0; tt < s.n; ++tt) {
       const float* ut = A.u + (long long)tt * g.plane;
       for (int mt = 0; mt < 2; ++mt) {
-        bar_wait(&acc_full[mt], af_phase[mt], abort);
-        af_phase[mt] ^= 1u;
-        tc_fence_after();
         const int rr = kTcRows * mt + m;  // region row (0 = coarse row i0 - hc)
         const bool valid = rr < kTcRows + 2 * hc;
+        const bool warp_valid = kTcRows * mt + 32 * quad < kTcRows + 2 * hc;
         const float* urow = ut + (long long)(i0 + hc + rr) * g.P + (j0 + hc);
-        for (int cb = 0; cb < t.Nf / 16; ++cb) {
-          float z[16];
-          tmem_ld16(tmem + lane_off + (uint32_t)(128 * mt + 16 * cb), z);
-          if (valid) {
-            // tensor-memory columns 16cb..16cb+15 hold region columns
-            // Nf-1-16cb down to Nf-16-16cb: pack them into two 8-column groups
-            const int c_hi = t.Nf - 16 * cb - 1;  // region column of z[0]
-            uint16_t hv[16], lv[16];
+        const int nch = t.Nf / 16;
+        if (warp_valid) {
+          // tensor-memory columns 16cb..16cb+15 hold region columns
+          // Nf-1-16cb down to Nf-16-16cb; u of the next chunk is loaded while
+          // the current one is converted
+          float un[16];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const int cc = c_hi - e;
-              const float w = urow[cc] * z[e] * A.zscale * A.wscale;
-              const uint16_t h = enc16(w, fp16);
-              hv[15 - e] = h;
-              lv[15 - e] = enc16(w - dec16(h, fp16), fp16);
+          for (int e = 0; e < 16; ++e) un[e] = valid ? urow[t.Nf - 1 - e] : 0.f;
+          for (int cb = 0; cb < nch; ++cb) {
+            float uc[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) uc[e] = un[e];
+            if (cb + 1 < nch) {
+#pragma unroll
+              for (int e = 0; e < 16; ++e) un[e] = valid ? urow[t.Nf - 17 - 16 * cb - e] : 0.f;
             }
-            const int c0 = c_hi - 15;  // lowest region column of the chunk (multiple of 8)
+            float z[16];
+            if (cb == 0) {
+              bar_wait(&acc_full[mt], af_phase[mt], abort);
+              tc_fence_after();
+            }
+            tmem_ld16(tmem + lane_off + (uint32_t)(128 * mt + 16 * cb), z);
+            if (valid) {
+              const int c_hi = t.Nf - 16 * cb - 1;  // region column of z[0]
+              uint16_t hv[16], lv[16];
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-              const int grp = (c0 >> 3) + half;
-              uint4 ph, pl;
-              ph.x = hv[8 * half + 0] | ((uint32_t)hv[8 * half + 1] << 16);
-              ph.y = hv[8 * half + 2] | ((uint32_t)hv[8 * half + 3] << 16);
-              ph.z = hv[8 * half + 4] | ((uint32_t)hv[8 * half + 5] << 16);
-              ph.w = hv[8 * half + 6] | ((uint32_t)hv[8 * half + 7] << 16);
-              pl.x = lv[8 * half + 0] | ((uint32_t)lv[8 * half + 1] << 16);
-              pl.y = lv[8 * half + 2] | ((uint32_t)lv[8 * half + 3] << 16);
-              pl.z = lv[8 * half + 4] | ((uint32_t)lv[8 * half + 5] << 16);
-              pl.w = lv[8 * half + 6] | ((uint32_t)lv[8 * half + 7] << 16);
-              *reinterpret_cast<uint4*>(ws + (size_t)grp * t.WRp * 16 + rr * 16) = ph;
-              *reinterpret_cast<uint4*>(ws + wplane_b + (size_t)grp * t.WRp * 16 + rr * 16) = pl;
+              for (int e = 0; e < 16; ++e) {
+                const float w = uc[e] * z[e] * zscale * wscale;
+                const uint16_t h = enc16(w, fp16);
+                hv[15 - e] = h;
+                lv[15 - e] = enc16(w - dec16(h, fp16), fp16);
+              }
+              const int c0 = c_hi - 15;  // lowest region column of the chunk (multiple of 8)
+#pragma unroll
+              for (int half = 0; half < 2; ++half) {
+                const int grp = (c0 >> 3) + half;
+                uint4 ph, pl;
+                ph.x = hv[8 * half + 0] | ((uint32_t)hv[8 * half + 1] << 16);
+                ph.y = hv[8 * half + 2] | ((uint32_t)hv[8 * half + 3] << 16);
+                ph.z = hv[8 * half + 4] | ((uint32_t)hv[8 * half + 5] << 16);
+                ph.w = hv[8 * half + 6] | ((uint32_t)hv[8 * half + 7] << 16);
+                *reinterpret_cast<uint4*>(ws + (size_t)grp * t.WRp * 16 + rr * 16) = ph;
+                if (nprod == 3) {
+                  pl.x = lv[8 * half + 0] | ((uint32_t)lv[8 * half + 1] << 16);
+                  pl.y = lv[8 * half + 2] | ((uint32_t)lv[8 * half + 3] << 16);
+                  pl.z = lv[8 * half + 4] | ((uint32_t)lv[8 * half + 5] << 16);
+                  pl.w = lv[8 * half + 6] | ((uint32_t)lv[8 * half + 7] << 16);
+                  *reinterpret_cast<uint4*>(ws + wplane_b + (size_t)grp * t.WRp * 16 + rr * 16) = pl;
+                }
+              }
             }
           }
+        } else {
+          bar_wait(&acc_full[mt], af_phase[mt], abort);
+          tc_fence_after();
         }
+        af_phase[mt] ^= 1u;
         tc_fence_before();
         bar_arrive(&acc_empty[mt]);
       }
@@ -517,7 +557,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const int j = j0 + jj;
           if (i < g.H && j < g.W && !*abort) {
             const long long off = pb + (long long)(g.B + i) * g.P + g.B + j;
-            const float d = dv[e] * A.dscale;
+            const float d = dv[e] * dscale;
             const float xo = A.x[off];
             float xv = xo;
             if (d > 0.f) {
@@ -529,7 +569,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             A.xn[off] = xv;
             if (A.write_xb) {
-              const float sv = xv * A.xscale_next;
+              const float sv = xv * xscale;
               const uint16_t h = enc16(sv, fp16);
               const long long plane_hi = ((long long)((A.pp ^ 1) * 2 + 0) * R2 + phi) * g.plane;
               const long long plane_lo = ((long long)((A.pp ^ 1) * 2 + 1) * R2 + phi) * g.plane;
@@ -558,7 +598,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 size_t tc_buffer_bytes(const Shape& s, const TcShape& t) {
   const size_t xb = 4ull * s.R2 * s.g.plane * sizeof(uint16_t);
   const size_t hk = (size_t)s.n * s.R2 * s.Kc * t.hank_block;
-  return ((xb + 255) & ~(size_t)255) + ((hk + 255) & ~(size_t)255);
+  return ((xb + 255) & ~(size_t)255) + ((hk + 255) & ~(size_t)255) + 512;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -595,17 +635,62 @@ cudaError_t launch_build_hankel(const Shape& s, const TcShape& t, const float* k
 }
 
 cudaError_t launch_split_x(const Shape& s, const TcShape& t, const float* x, uint16_t* xb, int pp,
-                           float xscale, cudaStream_t st) {
-  split_x_kernel<<<1024, 256, 0, st>>>(s, t.fp16, x, xb, pp, xscale);
+                           const float* scales, cudaStream_t st) {
+  split_x_kernel<<<1024, 256, 0, st>>>(s, t.fp16, x, xb, pp, scales);
+  return cudaGetLastError();
+}
+
+// max of non-negative values (the float bit patterns order like the integers)
+__global__ void max_nonneg_kernel(const float* __restrict__ v, long long count,
+                                  unsigned int* __restrict__ out) {
+  float m = 0.f;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, v[e]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
+}
+
+cudaError_t launch_max_nonneg(const float* v, long long count, unsigned int* out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  max_nonneg_kernel<<<1024, 256, 0, st>>>(v, count, out);
+  return cudaGetLastError();
+}
+
+// FP16 operand scales, all powers of two: x -> 2^ex x with max x scaled to
+// <= 2^14, PSF taps by gscale (fixed per frame set), w by a bound:
+// |w| <= max u * max x * fsum (fsum = largest sum of |taps| of a forward
+// model). scales = {1/(xs gs), ws, 1/(ws gs), xs}.
+__global__ void fp16_scales_kernel(const unsigned int* __restrict__ xmax_bits, float gscale,
+                                   float umax, float fsum, float* __restrict__ scales) {
+  const float xmax = fmaxf(__uint_as_float(*xmax_bits), 1e-30f);
+  const float xs = exp2f(floorf(log2f(16384.f / xmax)));
+  const float wb = fmaxf(umax * xmax * fsum, 1e-30f);
+  const float ws = exp2f(floorf(log2f(16384.f / wb)));
+  scales[0] = 1.f / (xs * gscale);
+  scales[1] = ws;
+  scales[2] = 1.f / (ws * gscale);
+  scales[3] = xs;
+}
+
+cudaError_t launch_fp16_scales(const unsigned int* xmax_bits, float gscale, float umax, float fsum,
+                               float* scales, cudaStream_t st) {
+  fp16_scales_kernel<<<1, 1, 0, st>>>(xmax_bits, gscale, umax, fsum, scales);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_iter(const Shape& s, const TcShape& t, const TcLaunch& L,
                            const CUtensorMap& map, cudaStream_t st) {
-  static size_t attr = 0;
+  static size_t attr1 = 0, attr3 = 0;
+  size_t& attr = (t.nprod == 3) ? attr3 : attr1;
   if (t.smem > attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_iter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)t.smem);
+    cudaError_t e = (t.nprod == 3)
+                        ? cudaFuncSetAttribute(tc_iter_kernel<3>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem)
+                        : cudaFuncSetAttribute(tc_iter_kernel<1>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
     if (e != cudaSuccess) return e;
     attr = t.smem;
   }
@@ -617,14 +702,14 @@ cudaError_t launch_tc_iter(const Shape& s, const TcShape& t, const TcLaunch& L,
   a.xb = L.xb;
   a.hank = L.hank;
   a.pp = L.pp;
-  a.zscale = L.zscale;
-  a.wscale = L.wscale;
-  a.dscale = L.dscale;
-  a.xscale_next = L.xscale_next;
+  a.scales = L.scales;
   a.write_xb = L.write_xb;
   a.err = L.err;
   dim3 grid(t.gxt, t.gyt);
-  tc_iter_kernel<<<grid, kTcThreads, t.smem, st>>>(s, t, a, map);
+  if (t.nprod == 3)
+    tc_iter_kernel<3><<<grid, kTcThreads, t.smem, st>>>(s, t, a, map);
+  else
+    tc_iter_kernel<1><<<grid, kTcThreads, t.smem, st>>>(s, t, a, map);
   return cudaGetLastError();
 }
 

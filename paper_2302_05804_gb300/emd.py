@@ -35,6 +35,8 @@ EXPORTS = [
     "emd_create", "emd_ctx_bytes", "emd_destroy", "emd_last_error", "emd_set_stream",
     "emd_set_frames", "emd_set_x", "emd_iterate", "emd_get_x", "emd_loglik",
     "emd_set_precision", "emd_get_numerator", "emd_get_weights", "emd_frame_stats_noalloc",
+    "emd_batch_create", "emd_batch_destroy", "emd_batch_add", "emd_batch_remove",
+    "emd_batch_step", "emd_batch_remaining", "emd_batch_sync", "emd_batch_config",
 ]
 
 
@@ -86,6 +88,20 @@ def load(build_if_missing: bool = False):
         lib.emd_get_weights.argtypes = [vp, vp]
         lib.emd_frame_stats_noalloc.argtypes = [vp, vp, vp, i, i, i, vp, vp]
         lib.emd_frame_stats_noalloc.restype = i
+        ip = C.POINTER(C.c_int)
+        lib.emd_batch_create.argtypes = [i]
+        lib.emd_batch_create.restype = vp
+        lib.emd_batch_destroy.argtypes = [vp]
+        lib.emd_batch_destroy.restype = None
+        lib.emd_batch_add.argtypes = [vp, vp, i]
+        lib.emd_batch_remove.argtypes = [vp, i]
+        lib.emd_batch_step.argtypes = [vp, ip]
+        lib.emd_batch_remaining.argtypes = [vp, i]
+        lib.emd_batch_sync.argtypes = [vp]
+        lib.emd_batch_config.argtypes = [vp, ip, ip, ip]
+        for name in ("emd_batch_add", "emd_batch_remove", "emd_batch_step",
+                     "emd_batch_remaining", "emd_batch_sync", "emd_batch_config"):
+            getattr(lib, name).restype = i
         for name in ("emd_set_stream", "emd_set_frames", "emd_set_x", "emd_iterate",
                      "emd_get_x", "emd_loglik", "emd_set_precision", "emd_get_numerator",
                      "emd_get_weights"):
@@ -194,6 +210,53 @@ def emd_frame_stats_noalloc(y, v, mask, H: int, W: int, n: int, out, stream=None
 
 def emd_set_precision(ctx, mode: int) -> None:
     _check(load().emd_set_precision(ctx, int(mode)))
+
+
+def emd_batch_create(max_jobs: int):
+    h = load().emd_batch_create(int(max_jobs))
+    if not h:
+        raise EMDError(EMD_EINVAL, load().emd_last_error().decode())
+    return h
+
+
+def emd_batch_destroy(b) -> None:
+    if b:
+        load().emd_batch_destroy(b)
+
+
+def emd_batch_add(b, ctx, iterations: int) -> int:
+    rc = load().emd_batch_add(b, ctx, int(iterations))
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
+def emd_batch_remove(b, slot: int) -> None:
+    _check(load().emd_batch_remove(b, int(slot)))
+
+
+def emd_batch_step(b) -> int:
+    """One iteration for every active job; returns how many finished."""
+    fin = C.c_int(0)
+    _check(load().emd_batch_step(b, C.byref(fin)))
+    return fin.value
+
+
+def emd_batch_remaining(b, slot: int) -> int:
+    rc = load().emd_batch_remaining(b, int(slot))
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
+def emd_batch_sync(b) -> None:
+    _check(load().emd_batch_sync(b))
+
+
+def emd_batch_config(b):
+    c, o, m = C.c_int(), C.c_int(), C.c_int()
+    _check(load().emd_batch_config(b, C.byref(c), C.byref(o), C.byref(m)))
+    return {"clusters": c.value, "order": o.value, "max_clusters": m.value}
 
 
 # -- convenience wrapper --------------------------------------------------------

@@ -1,0 +1,205 @@
+"""Continuous-batching server for EM deconvolution jobs.
+
+Jobs (sky patches of uneven size, exposure count and PSF size) arrive over
+time. Each admitted job owns a library context (its x, y, u and PSFs stay
+resident in device memory) and joins the running batch: every
+``emd_batch_step`` advances ALL admitted jobs by one EM iteration in a
+single persistent-kernel launch (replayed from a CUDA graph). New jobs are
+admitted between steps whenever a batch slot is free and their device
+footprint (``emd_ctx_bytes``) fits the HBM budget; their host-to-device
+uploads and set-up kernels run on their own streams while earlier jobs keep
+iterating. A finished job is read back, its context freed, and its slot and
+memory go to the next job in the queue (first come, first served).
+
+Latency of a job = time its result is on the host - its arrival time.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import emd
+
+
+@dataclass
+class JobSpec:
+    """One deconvolution request."""
+    jid: int
+    arrival: float          # seconds after the start of the run
+    H: int
+    W: int
+    n: int
+    K: int
+    r: int = 1
+    iters: int = 50
+
+
+@dataclass
+class JobData:
+    y: np.ndarray
+    v: np.ndarray
+    f: np.ndarray
+    mask: np.ndarray
+
+
+@dataclass
+class JobResult:
+    jid: int
+    arrival: float
+    admitted: float
+    finished: float
+    x: np.ndarray | None = None
+    loglik: float | None = None
+
+    @property
+    def latency(self):
+        return self.finished - self.arrival
+
+
+def poisson_trace(n_jobs: int, rate: float, seed: int = 4004, s_range=(128, 2048),
+                  n_range=(4, 40), k_range=(15, 43), iters: int = 50, r: int = 1):
+    """Poisson arrivals at `rate` jobs/s; side log-uniform in s_range, n
+    uniform in n_range, odd K uniform in k_range."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    ks = np.arange(k_range[0] | 1, k_range[1] + 1, 2)
+    for j in range(n_jobs):
+        t += g.exponential(1.0 / rate)
+        S = int(round(math.exp(g.uniform(math.log(s_range[0]), math.log(s_range[1])))))
+        n = int(g.integers(n_range[0], n_range[1] + 1))
+        K = int(g.choice(ks))
+        out.append(JobSpec(j, t, S, S, n, K, r, iters))
+    return out
+
+
+class DataPool:
+    """Job inputs cut from one resident synthetic frame set: a job of side S
+    with n exposures and K x K PSFs takes an S x S window of n exposures
+    (cycling through the pool's exposures) and the central K x K of their
+    PSFs, renormalised. Only the inputs are shared; every job is solved
+    independently."""
+
+    def __init__(self, problem):
+        self.p = problem
+
+    def make(self, spec: JobSpec) -> JobData:
+        p = self.p
+        g = np.random.Generator(np.random.PCG64(spec.jid))
+        H, W = spec.H, spec.W
+        i0 = int(g.integers(0, p.H - H + 1))
+        j0 = int(g.integers(0, p.W - W + 1))
+        ts = [(spec.jid + t) % p.n for t in range(spec.n)]
+        y = np.ascontiguousarray(p.y[ts, i0:i0 + H, j0:j0 + W])
+        v = np.ascontiguousarray(p.v[ts, i0:i0 + H, j0:j0 + W])
+        m = np.ascontiguousarray(p.mask[ts, i0:i0 + H, j0:j0 + W])
+        c, h = p.K // 2, spec.K // 2
+        f = p.f[ts, c - h:c + h + 1, c - h:c + h + 1].astype(np.float64)
+        f = (f / f.sum(axis=(1, 2), keepdims=True)).astype(np.float32)
+        return JobData(y, v, np.ascontiguousarray(f), m)
+
+
+class Server:
+    """Admission + continuous batching over the library's batch API."""
+
+    def __init__(self, hbm_budget: float = 80e9, max_slots: int = 64, keep_results: bool = False):
+        import torch
+        self.torch = torch
+        self.budget = hbm_budget
+        self.max_slots = max_slots
+        self.keep = keep_results
+        self.batch = emd.emd_batch_create(max_slots)
+        self.used = 0
+        self.queue: list[tuple[JobSpec, JobData]] = []
+        self.active: dict[int, dict] = {}  # slot -> record
+        self.results: list[JobResult] = []
+        self.steps = 0
+        self.t0 = time.perf_counter()
+
+    def now(self):
+        return time.perf_counter() - self.t0
+
+    def close(self):
+        for rec in self.active.values():
+            emd.emd_batch_remove(self.batch, rec["slot"])
+            emd.emd_destroy(rec["ctx"])
+        self.active.clear()
+        emd.emd_batch_destroy(self.batch)
+        self.batch = None
+
+    def submit(self, spec: JobSpec, data: JobData):
+        self.queue.append((spec, data))
+
+    def _admit(self):
+        admitted = 0
+        while self.queue and len(self.active) < self.max_slots:
+            spec, data = self.queue[0]
+            need = emd.emd_ctx_bytes(spec.H, spec.W, spec.n, spec.K, spec.r)
+            if self.used + need > self.budget and self.active:
+                break  # wait for memory (a job larger than the budget runs alone)
+            self.queue.pop(0)
+            stream = self.torch.cuda.Stream()
+            ctx = emd.emd_create(spec.H, spec.W, spec.n, spec.K, spec.r)
+            emd.emd_set_stream(ctx, stream)
+            emd.emd_set_frames(ctx, data.y, data.v, data.f, data.mask)
+            slot = emd.emd_batch_add(self.batch, ctx, spec.iters)
+            self.used += need
+            self.active[slot] = dict(spec=spec, ctx=ctx, slot=slot, bytes=need,
+                                     admitted=self.now(), stream=stream)
+            admitted += 1
+        return admitted
+
+    def _retire(self):
+        done = [s for s, rec in self.active.items()
+                if emd.emd_batch_remaining(self.batch, s) == 0]
+        if not done:
+            return 0
+        emd.emd_batch_sync(self.batch)
+        for s in done:
+            rec = self.active.pop(s)
+            spec = rec["spec"]
+            x = np.empty((spec.r * spec.H, spec.r * spec.W), np.float32)
+            emd.emd_get_x(rec["ctx"], x)
+            res = JobResult(spec.jid, spec.arrival, rec["admitted"], self.now(),
+                            x if self.keep else None)
+            emd.emd_batch_remove(self.batch, s)
+            emd.emd_destroy(rec["ctx"])
+            self.used -= rec["bytes"]
+            self.results.append(res)
+        return len(done)
+
+    def run(self, trace, data_of, time_limit: float | None = None, realtime: bool = True):
+        """Serve `trace` (JobSpecs sorted by arrival). data_of(spec) -> JobData.
+        With realtime=False every job is visible at t = 0 (saturation run)."""
+        pending = list(trace)
+        self.t0 = time.perf_counter()
+        total = len(pending)
+        while len(self.results) < total:
+            now = self.now()
+            while pending and (not realtime or pending[0].arrival <= now):
+                spec = pending.pop(0)
+                self.submit(spec, data_of(spec))
+            self._admit()
+            if self.active:
+                emd.emd_batch_step(self.batch)
+                self.steps += 1
+                self._retire()
+            elif pending:
+                time.sleep(max(0.0, min(0.05, pending[0].arrival - self.now())))
+            if time_limit and self.now() > time_limit:
+                break
+        emd.emd_batch_sync(self.batch)
+        return self.results
+
+    @staticmethod
+    def summary(results, trace_len=None):
+        if not results:
+            return {}
+        lat = np.array([r.latency for r in results])
+        span = max(r.finished for r in results) - min(r.arrival for r in results)
+        return {"jobs": len(results), "jobs_per_s": len(results) / span,
+                "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "mean_s": float(lat.mean()), "span_s": span}

@@ -1,0 +1,82 @@
+"""Batching: jobs of different shapes advancing together in one persistent
+kernel per step give bit-for-bit the iterates they give alone, including a
+job that joins while others are running (continuous batching)."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+JOBS = [
+    dict(H=200, W=150, n=3, K=15, r=1, mask_frac=0.05, n_points=60, n_gal=2),
+    dict(H=130, W=257, n=2, K=43, r=1, mask_frac=0.05, n_points=60, n_gal=2),
+    dict(H=96, W=80, n=2, K=15, r=2, fwhm=(3.0, 6.0), mask_frac=0.05, n_points=30, n_gal=2),
+    dict(H=64, W=64, n=4, K=7, r=1, mask_frac=0.0, n_points=20, n_gal=1),
+    dict(H=300, W=310, n=5, K=21, r=1, mask_frac=0.05, n_points=150, n_gal=3),
+]
+
+
+def make(i):
+    return synth.make_problem("hsc", seed_offset=i, **JOBS[i])
+
+
+def ctx_for(emd, p):
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    d.set_frames(p.y, p.v, p.f, p.mask)
+    d.set_x(np.full((p.r * p.H, p.r * p.W), 5.0, np.float32))
+    return d
+
+
+def test_batch_matches_solo_runs_bitwise():
+    from paper_2302_05804_gb300 import emd
+    iters = [6, 4, 7, 3, 5]
+    probs = [make(i) for i in range(len(JOBS))]
+    solo = []
+    for p, k in zip(probs, iters):
+        d = ctx_for(emd, p)
+        d.iterate(k)
+        solo.append(d.x())
+        d.close()
+    b = emd.emd_batch_create(8)
+    ds = [ctx_for(emd, p) for p in probs]
+    slots = {}
+    # four jobs start together; the fifth joins after two steps
+    for i in range(4):
+        slots[i] = emd.emd_batch_add(b, ds[i].ctx, iters[i])
+    done, step = 0, 0
+    while done < len(probs):
+        if step == 2:
+            slots[4] = emd.emd_batch_add(b, ds[4].ctx, iters[4])
+        done += emd.emd_batch_step(b)
+        step += 1
+        assert step < 50
+    emd.emd_batch_sync(b)
+    for i in range(len(probs)):
+        assert emd.emd_batch_remaining(b, slots[i]) == 0
+        np.testing.assert_array_equal(ds[i].x(), solo[i])
+    cfg = emd.emd_batch_config(b)
+    assert 1 <= cfg["clusters"] <= cfg["max_clusters"] and cfg["order"] in (0, 1)
+    for i in range(len(probs)):
+        emd.emd_batch_remove(b, slots[i])
+        ds[i].close()
+    emd.emd_batch_destroy(b)
+
+
+def test_batch_remove_midway_keeps_reached_iterate():
+    from paper_2302_05804_gb300 import emd
+    p = make(0)
+    d = ctx_for(emd, p)
+    b = emd.emd_batch_create(2)
+    s = emd.emd_batch_add(b, d.ctx, 10)
+    for _ in range(3):
+        emd.emd_batch_step(b)
+    emd.emd_batch_sync(b)
+    assert emd.emd_batch_remaining(b, s) == 7
+    emd.emd_batch_remove(b, s)
+    x3 = d.x()
+    e = ctx_for(emd, p)
+    e.iterate(3)
+    np.testing.assert_array_equal(x3, e.x())
+    d.close(); e.close()
+    emd.emd_batch_destroy(b)

@@ -10,6 +10,11 @@ memory):
   * split BF16 (x_hi f_hi + x_hi f_lo + x_lo f_hi): the dropped x_lo f_lo
     term and the residue rounding are ~2^-16 relative per product: relative
     L2 <= 1e-4 after one iteration (the bar the split form must meet).
+  * FP16, one product: 11 significant bits (unit roundoff 2^-11), operands
+    scaled by powers of two into range: relative L2 <= 3 * 2^-11 ~ 1.5e-3,
+    bar 2e-3.
+  * split FP16: ~2^-22 per product, below the FP32 accumulation error of the
+    Kc^2-term sums (~1e-6): bar 2e-5.
 """
 import numpy as np
 import pytest
@@ -19,8 +24,8 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-BF16, SPLIT_BF16 = 1, 3
-TOL1 = {BF16: 5e-3, SPLIT_BF16: 1e-4}
+BF16, FP16, SPLIT_BF16, SPLIT_FP16 = 1, 2, 3, 4
+TOL1 = {BF16: 5e-3, FP16: 2e-3, SPLIT_BF16: 1e-4, SPLIT_FP16: 2e-5}
 
 
 def rel_l2(a, b):
@@ -58,7 +63,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("mode", [BF16, SPLIT_BF16])
+@pytest.mark.parametrize("mode", [BF16, FP16, SPLIT_BF16, SPLIT_FP16])
 @pytest.mark.parametrize("recipe,kw", CASES)
 def test_tc_one_iteration(mode, recipe, kw):
     p = synth.make_problem(recipe, **kw)
@@ -78,10 +83,12 @@ def test_tc_split_ten_iterations_and_mode_switch():
     p = synth.make_problem("parity", mask_frac=0.05)
     x0 = start(p)
     u, y, N, _ = oracle.prepare(p)
-    x10 = run(p, x0, 10, SPLIT_BF16)
-    err = rel_l2(x10, oracle.em_run(x0, N, u, p.f, 10))
-    print(f"split bf16: rel L2 after 10 iterations = {err:.3e}")
-    assert err <= 1e-3
+    xo10 = oracle.em_run(x0, N, u, p.f, 10)
+    for mode in (SPLIT_BF16, SPLIT_FP16):
+        x10 = run(p, x0, 10, mode)
+        err = rel_l2(x10, xo10)
+        print(f"mode {mode}: rel L2 after 10 iterations = {err:.3e}")
+        assert err <= 1e-3
     # switching back to FP32 in the same context gives the FP32 result
     d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
     d.set_frames(p.y, p.v, p.f, p.mask)
