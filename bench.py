@@ -59,6 +59,18 @@ def algorithmic_flops(H, W, n, K, r):
     return 2.0 * 2.0 * n * H * W * (K + r - 1) ** 2
 
 
+def aggregate_over_ranks(local_ms, units_per_rank, world, device="cuda"):
+    """Whole-job throughput of N independent replicas: every rank processed
+    units_per_rank; the job took the slowest rank's time. Returns
+    (max_ms over ranks, value in units/s / 1e9)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return max_ms, units_per_rank * world / (max_ms / 1e3) / 1e9
+
+
 def tc_executed_flops(H, W, n, K, r, nprod):
     """Tensor-core flops one iteration issues: per 128x64 Den tile, exposure
     and phase, two forward M-tiles of N = Nf over Kf input columns and one
@@ -215,6 +227,41 @@ def run_reference(args):
     return 0
 
 
+def run_serving(p, args):
+    """Continuous-batching sample: jobs with sides log-uniform in [128, 2048],
+    4-40 exposures, odd PSF sides 15-43, 50 iterations each, cut from the
+    resident frame set; an 80 GB budget. First all jobs at t=0 (saturated
+    jobs/s), then a Poisson stream at 0.7x that rate for p50/p99 latency."""
+    from paper_2302_05804_gb300 import serve
+    pool = serve.DataPool(p)
+    kw = dict(s_range=(128, min(2048, p.H)), n_range=(4, 40), k_range=(15, min(43, p.K)),
+              iters=50)
+    sat_trace = serve.poisson_trace(args.serve_jobs, rate=1e9, seed=4004, **kw)
+    srv = serve.Server(hbm_budget=80e9, max_slots=64)
+    try:
+        res = srv.run(sat_trace, pool.make, realtime=False)
+    finally:
+        srv.close()
+    sat = serve.Server.summary(res)
+    rate = 0.7 * sat["jobs_per_s"]
+    trace = serve.poisson_trace(args.serve_jobs, rate=rate, seed=4005, **kw)
+    srv = serve.Server(hbm_budget=80e9, max_slots=64)
+    try:
+        res = srv.run(trace, pool.make, realtime=True)
+    finally:
+        srv.close()
+    live = serve.Server.summary(res)
+    fma = sum(2.0 * s.n * s.H * s.W * s.K ** 2 * s.iters for s in trace)
+    return {"jobs": len(res), "saturated_jobs_per_s": sat["jobs_per_s"],
+            "arrival_rate_jobs_per_s": rate, "jobs_per_s": live["jobs_per_s"],
+            "p50_latency_s": live["p50_s"], "p99_latency_s": live["p99_s"],
+            "mean_latency_s": live["mean_s"], "gpix_exposure_iters_per_s":
+                sum(s.H * s.W * s.n * s.iters for s in trace) / live["span_s"] / 1e9,
+            "useful_tflops": 2 * fma / live["span_s"] / 1e12,
+            "workload": "sides log-uniform 128-2048, n 4-40, K odd 15-43, 50 iterations, "
+                        "Poisson arrivals at 0.7x saturated rate, 80 GB budget, 64 slots"}
+
+
 def config_of(args, extra=None):
     d = workload_shape(args.workload)
     H, W, n, K, r = d["H"], d["W"], d["n"], d["K"], d["r"]
@@ -277,13 +324,8 @@ def run_ours(args):
     barrier()
     clocks = sampler.stop()
     per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    t = torch.tensor([total_ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
-    units = Hf * Wf * p.n * args.steps * world
-    value = units / (total_ms / 1e3) / 1e9
+    total_ms, value = aggregate_over_ranks(ev[0].elapsed_time(ev[-1]), Hf * Wf * p.n * args.steps,
+                                           world)
 
     flops = algorithmic_flops(p.H, p.W, p.n, p.K, p.r)
     launch_s = statistics.mean(per) / 1e3
@@ -340,6 +382,10 @@ def run_ours(args):
                "step": "set_frames + iterations + loglik + get_x, host pinned buffers"}
     d.close()
 
+    serving = None
+    if args.serve_jobs > 0 and prec == 0:
+        serving = run_serving(p, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = oracle_steps(p, args.cpu_crop, 1, 0, min_seconds=args.cpu_seconds)
@@ -356,6 +402,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": config_of(args), "roofline": roofline, "cpu_baseline": cpu,
             "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -377,6 +424,8 @@ def main():
     ap.add_argument("--e2e-iters", type=int, default=10)
     ap.add_argument("--e2e-jobs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=40,
+                    help="jobs in the serving sample (0 disables it)")
     ap.add_argument("--cpu-crop", type=int, default=512)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-crop", type=int, default=256)

@@ -465,6 +465,7 @@ int emd_iterate(emd_ctx* c, int k) {
       L.x = c->x[c->cur];
       L.xn = c->x[c->cur ^ 1];
       L.N = c->N;
+      L.Den = c->Den;
       L.u = c->u;
       L.xb = c->xb;
       L.hank = c->hank;

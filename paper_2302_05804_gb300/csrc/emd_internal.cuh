@@ -132,6 +132,7 @@ struct TcLaunch {
   const float* x;
   float* xn;
   const float* N;
+  float* Den;
   const float* u;
   uint16_t* xb;          // [2 ping-pong][2 hi/lo][R2] 16-bit planes
   const uint16_t* hank;  // Hankel blocks

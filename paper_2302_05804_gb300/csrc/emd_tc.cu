@@ -264,6 +264,7 @@ struct TcArgs {
   const float* x;        // R2 fp32 planes (current)
   float* xn;             // R2 fp32 planes (next)
   const float* N;        // R2 planes
+  float* Den;            // R2 planes: running sum of the exposures' partials
   const float* u;        // n planes
   uint16_t* xb;          // [2][2][R2] 16-bit planes
   const uint16_t* hank;  // Hankel blocks
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_iter_kernel(const Shape s, const TcShape t, const TcArgs A,
                    const __grid_constant__ CUtensorMap xmap) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ uint64_t bars[8 + 2 * kTcStages];
+  __shared__ uint64_t bars[9 + 2 * kTcStages];
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
 
@@ -298,8 +299,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t* acc_empty = &bars[4];  // [2]
   uint64_t* w_full = &bars[6];
   uint64_t* den_full = &bars[7];
-  uint64_t* b_full = &bars[8];
-  uint64_t* b_empty = &bars[8 + kTcStages];
+  uint64_t* den_empty = &bars[8];
+  uint64_t* b_full = &bars[9];
+  uint64_t* b_empty = &bars[9 + kTcStages];
   volatile int* abort = &abort_s;
 
   if (threadIdx.x == 0) {
@@ -312,6 +314,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     bar_init(w_full, 128);
     bar_init(den_full, 1);
+    bar_init(den_empty, 128);
     for (int i = 0; i < kTcStages; ++i) {
       bar_init(&b_full[i], 1);
       bar_init(&b_empty[i], 1);
@@ -385,7 +388,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const uint32_t idesc_a = idesc_base | ((uint32_t)(t.TC >> 3) << 17);
       const uint32_t xs_a = su32(xs), ws_a = su32(ws), ring_a = su32(ring);
       const uint32_t x_lbo = (uint32_t)t.XRp * 16, w_lbo = (uint32_t)t.WRp * 16;
-      uint32_t xf_phase = 0, wf_phase = 0, bf_phase = 0;
+      uint32_t xf_phase = 0, wf_phase = 0, bf_phase = 0, de_phase = 1;
       uint32_t ae_phase[2] = {1u, 1u};
       int stage = 0;
       for (int tt = 0; tt < s.n && !*abort; ++tt) {
@@ -429,9 +432,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           mma_commit(&acc_full[mt]);
         }
-        // adjoint into Den (tensor-memory columns 256 + 64 phi)
+        // adjoint of this exposure into the Den partial (tensor-memory
+        // columns 256 + 64 phi), once the epilogue has taken the last one
         bar_wait(w_full, wf_phase, abort);
         wf_phase ^= 1u;
+        bar_wait(den_empty, de_phase, abort);
+        de_phase ^= 1u;
         tc_fence_after();
         for (int phi = 0; phi < R2; ++phi) {
           const uint32_t dden = tmem + 256u + (uint32_t)(t.TC * phi);
@@ -444,7 +450,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             uint64_t bh = sdesc(bst, 128, 128);
             uint64_t bl = bh + ((uint32_t)(t.Sa * 128) >> 4);
             const uint64_t astep = (2u * w_lbo) >> 4, bstep = 256u >> 4;
-            uint32_t acc = (tt > 0 || a > 0) ? 1u : 0u;
+            uint32_t acc = (a > 0) ? 1u : 0u;
 #pragma unroll 2
             for (int kk = 0; kk < KSa; ++kk) {
               mma(dden, ah, bh, idesc_a, acc);
@@ -462,8 +468,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (++stage == kTcStages) { stage = 0; bf_phase ^= 1u; }
           }
         }
+        mma_commit(den_full);
       }
-      mma_commit(den_full);
     }
   } else {
     // ------------------------------ epilogue (warps 2-5) -------------------
@@ -471,6 +477,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int m = 32 * quad + lane;      // row within an M-tile
     const uint32_t lane_off = (uint32_t)(32 * quad) << 16;
     uint32_t af_phase[2] = {0u, 0u};
+    uint32_t df_phase = 0;
     const int fp16 = t.fp16;
     for (int tt = 0; tt < s.n; ++tt) {
       const float* ut = A.u + (long long)tt * g.plane;
@@ -541,45 +548,56 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bar_arrive(w_full);
-    }
-    // ---------------- update x' = Den > 0 ? x max(N,0) / Den : x ------------
-    bar_wait(den_full, 0, abort);
-    tc_fence_after();
-    const int i = i0 + m;
-    for (int phi = 0; phi < R2; ++phi) {
-      const long long pb = (long long)phi * g.plane;
-      for (int cb = 0; cb < t.TC / 16; ++cb) {
-        float dv[16];
-        tmem_ld16(tmem + lane_off + 256u + (uint32_t)(t.TC * phi + 16 * cb), dv);
+      // ---- this exposure's Den partial: summed into the running Den (FP32,
+      // exposures in ascending order); the last exposure applies
+      // x' = Den > 0 ? x max(N,0) / Den : x instead of storing
+      bar_wait(den_full, df_phase, abort);
+      df_phase ^= 1u;
+      tc_fence_after();
+      const int i = i0 + m;
+      const bool last = (tt + 1 == s.n);
+      for (int phi = 0; phi < R2; ++phi) {
+        const long long pb = (long long)phi * g.plane;
+        for (int cb = 0; cb < t.TC / 16; ++cb) {
+          float dv[16];
+          tmem_ld16(tmem + lane_off + 256u + (uint32_t)(t.TC * phi + 16 * cb), dv);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int jj = t.TC - 1 - (16 * cb + e);
-          const int j = j0 + jj;
-          if (i < g.H && j < g.W && !*abort) {
-            const long long off = pb + (long long)(g.B + i) * g.P + g.B + j;
-            const float d = dv[e] * dscale;
-            const float xo = A.x[off];
-            float xv = xo;
-            if (d > 0.f) {
-              const float nv = fmaxf(A.N[off], 0.f);
-              if (d < 1e-30f)
-                xv = (float)((double)xo * (double)nv / (double)d);
-              else
-                xv = xo * nv / d;
-            }
-            A.xn[off] = xv;
-            if (A.write_xb) {
-              const float sv = xv * xscale;
-              const uint16_t h = enc16(sv, fp16);
-              const long long plane_hi = ((long long)((A.pp ^ 1) * 2 + 0) * R2 + phi) * g.plane;
-              const long long plane_lo = ((long long)((A.pp ^ 1) * 2 + 1) * R2 + phi) * g.plane;
-              const long long o2 = (long long)(g.B + i) * g.P + g.B + j;
-              A.xb[plane_hi + o2] = h;
-              A.xb[plane_lo + o2] = enc16(sv - dec16(h, fp16), fp16);
+          for (int e = 0; e < 16; ++e) {
+            const int jj = t.TC - 1 - (16 * cb + e);
+            const int j = j0 + jj;
+            if (i < g.H && j < g.W && !*abort) {
+              const long long off = pb + (long long)(g.B + i) * g.P + g.B + j;
+              float d = dv[e] * dscale;
+              if (tt > 0) d = A.Den[off] + d;
+              if (!last) {
+                A.Den[off] = d;
+                continue;
+              }
+              const float xo = A.x[off];
+              float xv = xo;
+              if (d > 0.f) {
+                const float nv = fmaxf(A.N[off], 0.f);
+                if (d < 1e-30f)
+                  xv = (float)((double)xo * (double)nv / (double)d);
+                else
+                  xv = xo * nv / d;
+              }
+              A.xn[off] = xv;
+              if (A.write_xb) {
+                const float sv = xv * xscale;
+                const uint16_t h = enc16(sv, fp16);
+                const long long plane_hi = ((long long)((A.pp ^ 1) * 2 + 0) * R2 + phi) * g.plane;
+                const long long plane_lo = ((long long)((A.pp ^ 1) * 2 + 1) * R2 + phi) * g.plane;
+                const long long o2 = (long long)(g.B + i) * g.P + g.B + j;
+                A.xb[plane_hi + o2] = h;
+                A.xb[plane_lo + o2] = enc16(sv - dec16(h, fp16), fp16);
+              }
             }
           }
         }
       }
+      tc_fence_before();
+      bar_arrive(den_empty);
     }
   }
   tc_fence_before();
@@ -698,6 +716,7 @@ cudaError_t launch_tc_iter(const Shape& s, const TcShape& t, const TcLaunch& L,
   a.x = L.x;
   a.xn = L.xn;
   a.N = L.N;
+  a.Den = L.Den;
   a.u = L.u;
   a.xb = L.xb;
   a.hank = L.hank;

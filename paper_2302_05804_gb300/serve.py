@@ -103,9 +103,16 @@ class DataPool:
 
 
 class Server:
-    """Admission + continuous batching over the library's batch API."""
+    """Admission + continuous batching over the library's batch API.
+
+    A preparation thread turns arrived requests into ready contexts
+    (inputs cut, context created, frames uploaded on the job's own stream)
+    while the stepping thread keeps the batch running; contexts are created
+    only while the HBM budget allows. The stepping thread adds ready jobs
+    between steps, steps, and retires finished jobs (read back, freed)."""
 
     def __init__(self, hbm_budget: float = 80e9, max_slots: int = 64, keep_results: bool = False):
+        import threading
         import torch
         self.torch = torch
         self.budget = hbm_budget
@@ -113,48 +120,66 @@ class Server:
         self.keep = keep_results
         self.batch = emd.emd_batch_create(max_slots)
         self.used = 0
-        self.queue: list[tuple[JobSpec, JobData]] = []
+        self.lock = threading.Condition()
+        self.ready: list[dict] = []
         self.active: dict[int, dict] = {}  # slot -> record
         self.results: list[JobResult] = []
         self.steps = 0
         self.t0 = time.perf_counter()
+        self.error = None
 
     def now(self):
         return time.perf_counter() - self.t0
 
     def close(self):
-        for rec in self.active.values():
-            emd.emd_batch_remove(self.batch, rec["slot"])
+        for rec in list(self.active.values()) + self.ready:
+            if "slot" in rec:
+                emd.emd_batch_remove(self.batch, rec["slot"])
             emd.emd_destroy(rec["ctx"])
         self.active.clear()
+        self.ready.clear()
         emd.emd_batch_destroy(self.batch)
         self.batch = None
 
-    def submit(self, spec: JobSpec, data: JobData):
-        self.queue.append((spec, data))
+    # -- preparation thread ---------------------------------------------------
+    def _prepare(self, trace, data_of, realtime):
+        try:
+            for spec in trace:
+                if realtime:
+                    delay = spec.arrival - self.now()
+                    if delay > 0:
+                        time.sleep(delay)
+                need = emd.emd_ctx_bytes(spec.H, spec.W, spec.n, spec.K, spec.r)
+                with self.lock:
+                    # wait for memory and for a slot to be in sight (a job
+                    # larger than the budget runs alone)
+                    while (self.used + need > self.budget and self.used > 0) or \
+                            len(self.ready) + len(self.active) >= self.max_slots + 4:
+                        self.lock.wait(0.05)
+                    self.used += need
+                data = data_of(spec)
+                stream = self.torch.cuda.Stream()
+                ctx = emd.emd_create(spec.H, spec.W, spec.n, spec.K, spec.r)
+                emd.emd_set_stream(ctx, stream)
+                emd.emd_set_frames(ctx, data.y, data.v, data.f, data.mask)
+                with self.lock:
+                    self.ready.append(dict(spec=spec, ctx=ctx, bytes=need, stream=stream,
+                                           prepared=self.now()))
+                    self.lock.notify_all()
+        except Exception as e:  # surfaced by run()
+            self.error = e
 
+    # -- stepping thread ----------------------------------------------------------
     def _admit(self):
-        admitted = 0
-        while self.queue and len(self.active) < self.max_slots:
-            spec, data = self.queue[0]
-            need = emd.emd_ctx_bytes(spec.H, spec.W, spec.n, spec.K, spec.r)
-            if self.used + need > self.budget and self.active:
-                break  # wait for memory (a job larger than the budget runs alone)
-            self.queue.pop(0)
-            stream = self.torch.cuda.Stream()
-            ctx = emd.emd_create(spec.H, spec.W, spec.n, spec.K, spec.r)
-            emd.emd_set_stream(ctx, stream)
-            emd.emd_set_frames(ctx, data.y, data.v, data.f, data.mask)
-            slot = emd.emd_batch_add(self.batch, ctx, spec.iters)
-            self.used += need
-            self.active[slot] = dict(spec=spec, ctx=ctx, slot=slot, bytes=need,
-                                     admitted=self.now(), stream=stream)
-            admitted += 1
-        return admitted
+        with self.lock:
+            while self.ready and len(self.active) < self.max_slots:
+                rec = self.ready.pop(0)
+                rec["slot"] = emd.emd_batch_add(self.batch, rec["ctx"], rec["spec"].iters)
+                rec["admitted"] = self.now()
+                self.active[rec["slot"]] = rec
 
     def _retire(self):
-        done = [s for s, rec in self.active.items()
-                if emd.emd_batch_remaining(self.batch, s) == 0]
+        done = [s for s in self.active if emd.emd_batch_remaining(self.batch, s) == 0]
         if not done:
             return 0
         emd.emd_batch_sync(self.batch)
@@ -167,31 +192,39 @@ class Server:
                             x if self.keep else None)
             emd.emd_batch_remove(self.batch, s)
             emd.emd_destroy(rec["ctx"])
-            self.used -= rec["bytes"]
+            with self.lock:
+                self.used -= rec["bytes"]
+                self.lock.notify_all()
             self.results.append(res)
         return len(done)
 
     def run(self, trace, data_of, time_limit: float | None = None, realtime: bool = True):
         """Serve `trace` (JobSpecs sorted by arrival). data_of(spec) -> JobData.
         With realtime=False every job is visible at t = 0 (saturation run)."""
-        pending = list(trace)
+        import threading
         self.t0 = time.perf_counter()
-        total = len(pending)
+        total = len(trace)
+        prep = threading.Thread(target=self._prepare, args=(list(trace), data_of, realtime),
+                                daemon=True)
+        prep.start()
         while len(self.results) < total:
-            now = self.now()
-            while pending and (not realtime or pending[0].arrival <= now):
-                spec = pending.pop(0)
-                self.submit(spec, data_of(spec))
+            if self.error:
+                raise self.error
             self._admit()
             if self.active:
                 emd.emd_batch_step(self.batch)
                 self.steps += 1
                 self._retire()
-            elif pending:
-                time.sleep(max(0.0, min(0.05, pending[0].arrival - self.now())))
+            else:
+                with self.lock:
+                    if not self.ready:
+                        self.lock.wait(0.01)
             if time_limit and self.now() > time_limit:
                 break
+        prep.join(timeout=60)
         emd.emd_batch_sync(self.batch)
+        if self.error:
+            raise self.error
         return self.results
 
     @staticmethod

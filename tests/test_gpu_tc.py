@@ -13,8 +13,12 @@ memory):
   * FP16, one product: 11 significant bits (unit roundoff 2^-11), operands
     scaled by powers of two into range: relative L2 <= 3 * 2^-11 ~ 1.5e-3,
     bar 2e-3.
-  * split FP16: ~2^-22 per product, below the FP32 accumulation error of the
-    Kc^2-term sums (~1e-6): bar 2e-5.
+  * split FP16: ~2^-22 per product; then the FP32 accumulation inside the
+    tensor core dominates: each exposure's adjoint and each forward M-tile is
+    one accumulator fed by ~10^3 MMAs (Kc filter rows x k-steps x 3), and
+    that accumulation alone leaves ~2.5e-5 at K = 43 for either split form
+    (measured: split BF16 2.2e-5, split FP16 2.5e-5): bar 1e-4, the bar of
+    the split form.
 """
 import numpy as np
 import pytest
@@ -25,7 +29,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 BF16, FP16, SPLIT_BF16, SPLIT_FP16 = 1, 2, 3, 4
-TOL1 = {BF16: 5e-3, FP16: 2e-3, SPLIT_BF16: 1e-4, SPLIT_FP16: 2e-5}
+TOL1 = {BF16: 5e-3, FP16: 2e-3, SPLIT_BF16: 1e-4, SPLIT_FP16: 1e-4}
 
 
 def rel_l2(a, b):
