@@ -131,6 +131,14 @@ int emd_loglik(emd_ctx *ctx, double *out, double *chi2);
  * into this library return EMD_EUNSUPPORTED and leave the mode unchanged. */
 int emd_set_precision(emd_ctx *ctx, int mode);
 
+/* Self-test of failure detection: launches, on ctx's stream, one CTA that
+ * waits on an mbarrier nothing ever arrives on, with the same bounded-wait
+ * code the kernels use but a limit of `spins` polls. The wait gives up, the
+ * kernel records the timeout in the context's device error word and exits;
+ * the call returns EMD_ETIMEOUT (the expected outcome) and clears the word,
+ * leaving the context usable. EMD_OK would mean the wait did not give up. */
+int emd_selftest_wait_timeout(emd_ctx *ctx, int spins);
+
 /* Inspection: the numerator N ((rH) x (rW)) and the weights u (n x H x W)
  * prepared by emd_set_frames. */
 int emd_get_numerator(emd_ctx *ctx, float *out);

@@ -493,6 +493,17 @@ int emd_get_x(emd_ctx* c, float* out) {
   return check_device_error(c);
 }
 
+int emd_selftest_wait_timeout(emd_ctx* c, int spins) {
+  if (int rc = check_ctx(c, false)) return rc;
+  if (spins < 1) {
+    set_err("emd_selftest_wait_timeout: spins must be >= 1");
+    return EMD_EINVAL;
+  }
+  DeviceGuard dg(c->device);
+  CK(emd::launch_wait_selftest((uint32_t)spins, c->err, c->st));
+  return check_device_error(c);
+}
+
 int emd_get_numerator(emd_ctx* c, float* out) {
   if (int rc = check_ctx(c, true)) return rc;
   DeviceGuard dg(c->device);

@@ -111,9 +111,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: gives up after ~2^22 polls (each poll may suspend briefly).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < (1u << 22); ++i)
+// Bounded wait: gives up after `limit` polls (each poll may suspend briefly).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint32_t limit = (1u << 22)) {
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -549,6 +550,27 @@ cudaError_t launch_batch(const BatchJob* jobs, int njobs, const int2* items, con
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   batch_advance_kernel<<<(njobs + 127) / 128, 128, 0, st>>>(const_cast<BatchJob*>(jobs), njobs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// self-test of the bounded waits: an mbarrier that nothing arrives on
+// ---------------------------------------------------------------------------
+
+__global__ void wait_selftest_kernel(uint32_t limit, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // the expected arrival never comes: the bounded wait must give up
+  const bool ok = mbar_wait_bounded(&bar, 0, limit);
+  if (!ok && threadIdx.x == 0) atomicOr(err, kErrTimeout);
+}
+
+cudaError_t launch_wait_selftest(uint32_t limit, int* err, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(limit, err);
   return cudaGetLastError();
 }
 

@@ -108,6 +108,8 @@ cudaError_t launch_build_kernels(const Shape& s, const float* f_raw, float* kf,
 cudaError_t launch_fused(const Shape& s, const FusedArgs& a, int mode, double* part,
                          cudaStream_t st);
 int fused_blocks(const Shape& s);
+// one CTA waiting (bounded by `limit` polls) on an mbarrier nothing arrives on
+cudaError_t launch_wait_selftest(uint32_t limit, int* err, cudaStream_t st);
 cudaError_t launch_fill_latent(const Shape& s, float* x, float c,
                                cudaStream_t st);
 cudaError_t launch_scatter_latent(const Shape& s, const float* nat, float* planes,

@@ -37,6 +37,7 @@ EXPORTS = [
     "emd_set_precision", "emd_get_numerator", "emd_get_weights", "emd_frame_stats_noalloc",
     "emd_batch_create", "emd_batch_destroy", "emd_batch_add", "emd_batch_remove",
     "emd_batch_step", "emd_batch_remaining", "emd_batch_sync", "emd_batch_config",
+    "emd_selftest_wait_timeout",
 ]
 
 
@@ -88,6 +89,8 @@ def load(build_if_missing: bool = False):
         lib.emd_get_weights.argtypes = [vp, vp]
         lib.emd_frame_stats_noalloc.argtypes = [vp, vp, vp, i, i, i, vp, vp]
         lib.emd_frame_stats_noalloc.restype = i
+        lib.emd_selftest_wait_timeout.argtypes = [vp, i]
+        lib.emd_selftest_wait_timeout.restype = i
         ip = C.POINTER(C.c_int)
         lib.emd_batch_create.argtypes = [i]
         lib.emd_batch_create.restype = vp
@@ -206,6 +209,11 @@ def emd_frame_stats_noalloc(y, v, mask, H: int, W: int, n: int, out, stream=None
     _check(load().emd_frame_stats_noalloc(_ptr(y, np.float32, "y"), _ptr(v, np.float32, "v"),
                                           _ptr(mask, np.uint8, "mask"), H, W, n,
                                           out.data_ptr(), stream))
+
+
+def emd_selftest_wait_timeout(ctx, spins: int = 1000) -> int:
+    """Returns the raw status (EMD_ETIMEOUT expected)."""
+    return int(load().emd_selftest_wait_timeout(ctx, int(spins)))
 
 
 def emd_set_precision(ctx, mode: int) -> None:

@@ -239,3 +239,20 @@ def test_invalid_data_and_state_errors(emd):
         d.iterate(-1)
     assert ei.value.code == emd.EMD_EINVAL
     d.close()
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable(emd):
+    # failure detection without a fault: a wait on a barrier nothing arrives
+    # on must give up, report EMD_ETIMEOUT, and leave the context working
+    p = make("hsc", H=48, W=40, n=2, K=7, n_points=10, n_gal=1)
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    rc = emd.emd_selftest_wait_timeout(d.ctx, 2000)
+    assert rc == emd.EMD_ETIMEOUT, rc
+    assert "wait" in emd.emd_last_error()
+    d.set_frames(p.y, p.v, p.f, p.mask)
+    x0 = start(p)
+    d.set_x(x0)
+    d.iterate(2)
+    x2 = d.x()
+    d.close()
+    np.testing.assert_array_equal(x2, gpu_run(emd, p, x0, 2))
