@@ -116,6 +116,17 @@ int emd_set_x(emd_ctx *ctx, const float *x0);
  * asynchronous). EMD_ETIMEOUT if a bounded device wait gave up. */
 int emd_iterate(emd_ctx *ctx, int k);
 
+/* Streaming (frame-by-frame) EM, the order-dependent alternative the paper
+ * contrasts with its simultaneous update (Sec. 1 and the remarks after
+ * Eq. (2), after Harmeling et al.): each of k passes updates x once per
+ * exposure t, in the given order, with that exposure alone:
+ *   x <- x . max(F_t^T(u_t y_t), 0) / F_t^T(u_t F_t x)
+ * (x unchanged where the denominator is 0). order: a permutation of
+ * 0..n-1, or NULL for ascending. The per-exposure numerators are computed
+ * on the first call after emd_set_frames (n latent planes of device memory,
+ * allocated then). Runs on the FP32 kernel regardless of the precision. */
+int emd_iterate_streaming(emd_ctx *ctx, int k, const int *order);
+
 /* Copy the current iterate to out ((rH) x (rW) float32). */
 int emd_get_x(emd_ctx *ctx, float *out);
 

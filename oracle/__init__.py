@@ -72,6 +72,8 @@ def _load():
             lib.oracle_em_run.argtypes = [dp, dp, dp, dp, i, i, i, i, i, i]
             lib.oracle_em_step_literal.argtypes = [dp, dp, dp, C.c_void_p, dp,
                                                    i, i, i, i]
+            lib.oracle_em_pass_streaming.argtypes = [dp, dp, dp, dp, i, i, i, i, i,
+                                                     C.c_void_p]
             lib.oracle_chi2.argtypes = [dp, dp, dp, dp, i, i, i, i, i]
             lib.oracle_chi2.restype = C.c_double
             lib.oracle_logdet.argtypes = [dp, dp, C.c_long]
@@ -207,6 +209,19 @@ def em_step_literal(x, y, u, f, mask=None):
     _load().oracle_em_step_literal(_p(x), _p(y), _p(u),
                                    None if m is None else m.ctypes.data,
                                    _p(f), n, H, W, f.shape[1])
+    return x
+
+
+def em_streaming(x, y, u, f, k, r=1, order=None):
+    """k passes of the frame-by-frame (streaming) EM; y zero where u = 0."""
+    x, y, u, f = _d(x).copy(), _d(y), _d(u), _d(f)
+    n, H, W, K, r = _dims(u, f, r)
+    o = None
+    if order is not None:
+        o = np.ascontiguousarray(order, dtype=np.int32)
+    for _ in range(int(k)):
+        _load().oracle_em_pass_streaming(_p(x), _p(y), _p(u), _p(f), n, H, W, K, r,
+                                         None if o is None else o.ctypes.data)
     return x
 
 

@@ -287,6 +287,30 @@ void oracle_em_step_literal(double *x, const double *y, const double *u,
     free(tmp2);
 }
 
+/* Streaming (frame-by-frame) EM, the order-dependent scheme the paper
+ * contrasts with Eq. (2) (Sec. 1 and the remarks after Eq. (2)): one pass
+ * updates x once per exposure, in the given order, each time with that
+ * exposure alone: x' = Den_t > 0 ? x max(N_t, 0) / Den_t : x with
+ * N_t = F_t^T(u_t y_t), Den_t = F_t^T(u_t F_t x). y must be 0 where u = 0. */
+void oracle_em_pass_streaming(double *x, const double *y, const double *u,
+                              const double *f, int n, int H, int W, int K,
+                              int r, const int *order)
+{
+    const long np = (long)H * W, nf = (long)r * r * H * W;
+    double *Nt = (double *)malloc(sizeof(double) * nf);
+    double *Dt = (double *)malloc(sizeof(double) * nf);
+    for (int q = 0; q < n; q++) {
+        const int t = order ? order[q] : q;
+        oracle_numerator(y + t * np, u + t * np, f + (long)t * K * K, 1, H, W,
+                         K, r, Nt);
+        oracle_denominator(x, u + t * np, f + (long)t * K * K, 1, H, W, K, r,
+                           Dt);
+        oracle_apply_update(x, Nt, Dt, nf);
+    }
+    free(Nt);
+    free(Dt);
+}
+
 /* ----------------------------------------------------------------------- */
 /* Log-likelihood of Eq. (1) and the default initial guess                  */
 /* ----------------------------------------------------------------------- */

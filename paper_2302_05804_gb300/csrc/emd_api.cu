@@ -100,6 +100,9 @@ struct emd_ctx {
   float* scales = nullptr;       // device {z, w, Den, x} operand scales
   unsigned int* xmax = nullptr;  // device max of x (FP16 modes)
   float gscale = 1.f, umax = 0.f, fsum = 0.f;
+  // streaming EM: per-exposure numerators (allocated on first use)
+  float* Nt = nullptr;
+  bool nt_ready = false;
 };
 
 namespace {
@@ -161,6 +164,8 @@ emd::FusedArgs fused_args(emd_ctx* c) {
   a.Nw = c->N;
   a.Den = c->Den;
   a.err = c->err;
+  a.t0 = 0;
+  a.t1 = c->s.n;
   return a;
 }
 
@@ -271,6 +276,7 @@ void emd_destroy(emd_ctx* c) {
   else cudaDeviceSynchronize();
   cudaFree(c->arena);
   if (c->tc_arena) cudaFree(c->tc_arena);
+  if (c->Nt) cudaFree(c->Nt);
   delete c;
 }
 
@@ -341,6 +347,7 @@ int emd_set_frames(emd_ctx* c, const float* y, const float* v, const float* f,
   const Shape& s = c->s;
   c->frames = false;
   c->hank_ready = false;
+  c->nt_ready = false;
   const size_t npix = (size_t)s.n * s.H * s.W;
   if (int rc = put_planes(c, c->y, y, s.n)) return rc;
   if (int rc = put_planes(c, c->u, v, s.n)) return rc;  // v, converted in place below
@@ -482,6 +489,64 @@ int emd_iterate(emd_ctx* c, int k) {
     emd::FusedArgs a = fused_args(c);
     CK(emd::launch_fused(c->s, a, 0, c->part, c->st));
     c->cur ^= 1;
+  }
+  return EMD_OK;
+}
+
+int emd_iterate_streaming(emd_ctx* c, int k, const int* order) {
+  if (int rc = check_ctx(c, true)) return rc;
+  const Shape& s = c->s;
+  if (k < 0) {
+    set_err("emd_iterate_streaming: k must be >= 0");
+    return EMD_EINVAL;
+  }
+  std::vector<int> ord(s.n);
+  for (int t = 0; t < s.n; ++t) ord[t] = t;
+  if (order) {
+    std::vector<char> seen(s.n, 0);
+    for (int t = 0; t < s.n; ++t) {
+      const int e = order[t];
+      if (e < 0 || e >= s.n || seen[e]) {
+        set_err("emd_iterate_streaming: order must be a permutation of 0..n-1");
+        return EMD_EINVAL;
+      }
+      seen[e] = 1;
+      ord[t] = e;
+    }
+  }
+  DeviceGuard dg(c->device);
+  const size_t lat = (size_t)s.R2 * s.g.plane;
+  if (!c->Nt) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, (size_t)s.n * lat * sizeof(float));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_err("emd_iterate_streaming: cudaMalloc of the per-exposure numerators failed");
+      return EMD_ENOMEM;
+    }
+    CK(cudaMemset(p, 0, (size_t)s.n * lat * sizeof(float)));
+    c->Nt = static_cast<float*>(p);
+  }
+  if (!c->nt_ready) {
+    for (int t = 0; t < s.n; ++t) {
+      emd::FusedArgs a = fused_args(c);
+      a.Nw = c->Nt + (size_t)t * lat;
+      a.t0 = t;
+      a.t1 = t + 1;
+      CK(emd::launch_fused(s, a, 1, c->part, c->st));
+    }
+    c->nt_ready = true;
+  }
+  for (int it = 0; it < k; ++it) {
+    for (int q = 0; q < s.n; ++q) {
+      const int t = ord[q];
+      emd::FusedArgs a = fused_args(c);
+      a.N = c->Nt + (size_t)t * lat;
+      a.t0 = t;
+      a.t1 = t + 1;
+      CK(emd::launch_fused(s, a, 0, c->part, c->st));
+      c->cur ^= 1;
+    }
   }
   return EMD_OK;
 }

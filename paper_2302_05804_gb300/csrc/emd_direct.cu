@@ -260,7 +260,8 @@ __device__ __forceinline__ void fused_tile(const Shape& s, const FusedArgs& a, c
 
   const int ccols = 16 * s.MXf;
 
-  for (int t = 0; t < s.n; ++t) {
+  const int t0 = a.t0, t1 = a.t1;  // exposures of this launch, ascending
+  for (int t = t0; t < t1; ++t) {
     const long long tplane = (long long)t * g.plane;
     if (mode != 1) {
       // ---------------- forward: z = sum_phi kf_phi (x) x_phi -----------------
@@ -270,7 +271,7 @@ __device__ __forceinline__ void fused_tile(const Shape& s, const FusedArgs& a, c
 #pragma unroll
         for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
       for (int phi = 0; phi < s.R2; ++phi) {
-        const bool stage = (s.R2 > 1) || (t == 0);
+        const bool stage = (s.R2 > 1) || (t == t0);
         __syncthreads();  // earlier readers of xs / ksf are done
         if (stage && tid < 32) {
           const float* plane = a.x + (long long)phi * g.plane;
@@ -293,7 +294,7 @@ __device__ __forceinline__ void fused_tile(const Shape& s, const FusedArgs& a, c
         if (has_f && !timed_out) corr_tile<4, 16>(acc, xs, 4 * fmy, 16 * fmx, ksf, KP, Kc);
       }
       // ---------------- weight by u_t (mode 0) or chi-square (mode 2) ----------
-      if (mode == 0 && t > 0) cluster_wait();  // [B_{t-1}]: peer done reading our w
+      if (mode == 0 && t > t0) cluster_wait();  // [B_{t-1}]: peer done reading our w
       if (has_f) {
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
@@ -377,14 +378,14 @@ __device__ __forceinline__ void fused_tile(const Shape& s, const FusedArgs& a, c
       for (int p = 0; p < 2; ++p) {
         const int i = i0 + kHalf * q + 2 * amy + p;
         const long long grow = pbase + (long long)(g.B + i) * g.P + g.B + j0 + 16 * amx;
-        if (t > 0) {
+        if (t > t0) {
 #pragma unroll
           for (int c = 0; c < 16; ++c) acc2[p][c] = a.Den[grow + c] + acc2[p][c];
         }
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int j = j0 + 16 * amx + c;
-          if (t + 1 < s.n) {
+          if (t + 1 < t1) {
             a.Den[grow + c] = acc2[p][c];
           } else if (i < g.H && j < g.W) {
             if (mode == 1) {

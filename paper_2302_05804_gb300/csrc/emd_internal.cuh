@@ -70,6 +70,7 @@ struct FusedArgs {
   float* Nw;          // R2 planes (output of mode 1)
   float* Den;         // R2 planes (scratch between exposures)
   int* err;
+  int t0, t1;         // exposures [t0, t1) of this launch (all: 0, n)
 };
 
 struct SetupArgs {

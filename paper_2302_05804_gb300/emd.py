@@ -37,7 +37,7 @@ EXPORTS = [
     "emd_set_precision", "emd_get_numerator", "emd_get_weights", "emd_frame_stats_noalloc",
     "emd_batch_create", "emd_batch_destroy", "emd_batch_add", "emd_batch_remove",
     "emd_batch_step", "emd_batch_remaining", "emd_batch_sync", "emd_batch_config",
-    "emd_selftest_wait_timeout",
+    "emd_selftest_wait_timeout", "emd_iterate_streaming",
 ]
 
 
@@ -89,6 +89,8 @@ def load(build_if_missing: bool = False):
         lib.emd_get_weights.argtypes = [vp, vp]
         lib.emd_frame_stats_noalloc.argtypes = [vp, vp, vp, i, i, i, vp, vp]
         lib.emd_frame_stats_noalloc.restype = i
+        lib.emd_iterate_streaming.argtypes = [vp, i, vp]
+        lib.emd_iterate_streaming.restype = i
         lib.emd_selftest_wait_timeout.argtypes = [vp, i]
         lib.emd_selftest_wait_timeout.restype = i
         ip = C.POINTER(C.c_int)
@@ -178,6 +180,14 @@ def emd_set_x(ctx, x0) -> None:
 
 def emd_iterate(ctx, k: int) -> None:
     _check(load().emd_iterate(ctx, int(k)))
+
+
+def emd_iterate_streaming(ctx, k: int, order=None) -> None:
+    """k streaming passes (one update per exposure, in `order`)."""
+    arr = None
+    if order is not None:
+        arr = (C.c_int * len(order))(*[int(t) for t in order])
+    _check(load().emd_iterate_streaming(ctx, int(k), arr))
 
 
 def emd_get_x(ctx, out) -> None:
@@ -298,6 +308,9 @@ class Deconvolver:
 
     def iterate(self, k):
         emd_iterate(self.ctx, k)
+
+    def iterate_streaming(self, k, order=None):
+        emd_iterate_streaming(self.ctx, k, order)
 
     def set_precision(self, mode):
         emd_set_precision(self.ctx, mode)

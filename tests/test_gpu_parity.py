@@ -256,3 +256,24 @@ def test_bounded_wait_gives_up_and_context_stays_usable(emd):
     x2 = d.x()
     d.close()
     np.testing.assert_array_equal(x2, gpu_run(emd, p, x0, 2))
+
+
+@pytest.mark.parametrize("kw", [dict(H=96, W=130, n=3, K=15, r=1, mask_frac=0.05),
+                                dict(H=64, W=48, n=3, K=9, r=2, mask_frac=0.05)])
+def test_streaming_em_parity_and_order(emd, kw):
+    p = make("hsc", fwhm=(1.5 * kw["r"], 3.0 * kw["r"]), n_points=30, n_gal=2, **kw)
+    x0 = start(p)
+    u, y, _, _ = oracle.prepare(p)
+    for order, k in ((None, 1), ([2, 0, 1], 3)):
+        d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+        d.set_frames(p.y, p.v, p.f, p.mask)
+        d.set_x(x0)
+        d.iterate_streaming(k, order)
+        xg = d.x()
+        d.close()
+        xo = oracle.em_streaming(x0, y, u, p.f, k, r=p.r, order=order)
+        assert rel_l2(xg, xo) <= (1e-5 if k == 1 else 5e-5)
+    # order matters for the streaming scheme, on the GPU as in the oracle
+    a = oracle.em_streaming(x0, y, u, p.f, 3, r=p.r, order=[0, 1, 2])
+    assert rel_l2(xg, a) > 10 * rel_l2(xg, oracle.em_streaming(x0, y, u, p.f, 3, r=p.r,
+                                                                order=[2, 0, 1]))

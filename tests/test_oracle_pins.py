@@ -357,3 +357,50 @@ def test_em_step_at_matches_full_step(r, K):
     np.testing.assert_allclose(Do, den.ravel()[idx], rtol=1e-12)
     np.testing.assert_allclose(No, N.ravel()[idx], rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(xo, x1.ravel()[idx], rtol=1e-12)
+
+
+# -- streaming (frame-by-frame) EM, the order-dependent contrast of Sec. 2 --------
+
+def _stream_problem(seed=41, n=3, r=1):
+    x_true, y, v, f, mask = small_problem(seed=seed, H=24, W=20, n=n, K=5, r=r)
+    u, _ = oracle.weights(v, mask, y)
+    yy = np.where(mask != 0, y, 0.0)
+    return x_true, yy, v, f, mask, u
+
+
+def test_streaming_with_one_exposure_is_the_batch_update():
+    x_true, y, v, f, mask, u = _stream_problem(n=1)
+    x0 = np.abs(x_true) + 1.0
+    a = oracle.em_streaming(x0, y, u, f, 3)
+    b = oracle.em_run(x0, oracle.numerator(y, u, f), u, f, 3)
+    np.testing.assert_allclose(a, b, rtol=1e-14)
+
+
+def test_streaming_pass_is_a_sequence_of_single_frame_updates():
+    x_true, y, v, f, mask, u = _stream_problem(n=3)
+    x0 = np.abs(x_true) + 1.0
+    order = [2, 0, 1]
+    x = x0.copy()
+    for t in order:
+        x = oracle.em_step(x, oracle.numerator(y[t:t + 1], u[t:t + 1], f[t:t + 1]),
+                           u[t:t + 1], f[t:t + 1])
+    np.testing.assert_allclose(oracle.em_streaming(x0, y, u, f, 1, order=order), x, rtol=1e-14)
+
+
+def test_streaming_depends_on_frame_order_unlike_eq2():
+    x_true, y, v, f, mask, u = _stream_problem(n=3)
+    x0 = np.abs(x_true) + 1.0
+    a = oracle.em_streaming(x0, y, u, f, 2, order=[0, 1, 2])
+    b = oracle.em_streaming(x0, y, u, f, 2, order=[2, 1, 0])
+    assert np.linalg.norm(a - b) > 1e-6 * np.linalg.norm(a)
+
+
+@pytest.mark.parametrize("r", [1, 2])
+def test_streaming_keeps_the_noise_free_truth(r):
+    g = rng(8)
+    n, H, W, K = 3, 10, 12, 5
+    x_true = g.uniform(0.2, 3.0, (r * H, r * W))
+    f = np.stack([rand_psf(K, g) for _ in range(n)])
+    y = np.stack([synth.block_sum(ss.convolve2d(x_true, f[t], mode="same"), r) for t in range(n)])
+    u = g.uniform(0.3, 1.0, (n, H, W))
+    np.testing.assert_allclose(oracle.em_streaming(x_true, y, u, f, 2, r=r), x_true, rtol=1e-12)
