@@ -74,6 +74,12 @@ def _load():
                                                    i, i, i, i]
             lib.oracle_em_pass_streaming.argtypes = [dp, dp, dp, dp, i, i, i, i, i,
                                                      C.c_void_p]
+            lib.oracle_psf_model.argtypes = [dp, i, dp, i, i, i, dp]
+            lib.oracle_psf_model_adjoint.argtypes = [dp, i, dp, i, i, i, dp]
+            lib.oracle_psf_loss.argtypes = [dp, i, dp, i, dp, i, i, C.c_double, C.c_void_p]
+            lib.oracle_psf_loss.restype = C.c_double
+            d_ = C.c_double
+            lib.oracle_psf_fit.argtypes = [dp, i, dp, i, dp, i, i, d_, d_, d_, d_, d_, i]
             lib.oracle_chi2.argtypes = [dp, dp, dp, dp, i, i, i, i, i]
             lib.oracle_chi2.restype = C.c_double
             lib.oracle_logdet.argtypes = [dp, dp, C.c_long]
@@ -223,6 +229,43 @@ def em_streaming(x, y, u, f, k, r=1, order=None):
         _load().oracle_em_pass_streaming(_p(x), _p(y), _p(u), _p(f), n, H, W, K, r,
                                          None if o is None else o.ctypes.data)
     return x
+
+
+# -- PSF super-resolution fit, Eq. (4) ------------------------------------------
+
+def psf_fine_side(K, r):
+    return r * (K - 1) + 1
+
+
+def psf_model(h, g, r, K):
+    """D^r(h * g) on the K x K coarse grid."""
+    h, g = _d(h), _d(g)
+    m = np.empty((K, K))
+    _load().oracle_psf_model(_p(h), h.shape[0], _p(g), g.shape[0], r, K, _p(m))
+    return m
+
+
+def psf_model_adjoint(w, g, r, Kh):
+    w, g = _d(w), _d(g)
+    out = np.empty((Kh, Kh))
+    _load().oracle_psf_model_adjoint(_p(w), w.shape[0], _p(g), g.shape[0], r, Kh, _p(out))
+    return out
+
+
+def psf_loss(h, f, g, r, lam, grad=False):
+    h, f, g = _d(h), _d(f), _d(g)
+    gr = np.empty_like(h) if grad else None
+    L = _load().oracle_psf_loss(_p(h), h.shape[0], _p(f), f.shape[0], _p(g), g.shape[0], r,
+                                float(lam), None if gr is None else gr.ctypes.data)
+    return (L, gr) if grad else L
+
+
+def psf_fit(f, g, r, lam, iters, lr, h0, b1=0.9, b2=0.999, eps=1e-8):
+    """iters projected Adam steps on Eq. (4) from h0."""
+    h, f, g = _d(h0).copy(), _d(f), _d(g)
+    _load().oracle_psf_fit(_p(h), h.shape[0], _p(f), f.shape[0], _p(g), g.shape[0], r,
+                           float(lam), float(lr), float(b1), float(b2), float(eps), int(iters))
+    return h
 
 
 def chi2(x, y, u, f, r=1):

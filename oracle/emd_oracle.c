@@ -443,3 +443,118 @@ void oracle_em_step_at(const double *x, const double *y, const double *u,
     free(memo);
     free(have);
 }
+
+/* ----------------------------------------------------------------------- */
+/* PSF super-resolution fit, Eq. (4)                                        */
+/* ----------------------------------------------------------------------- */
+/*
+ * h = argmin_{h >= 0}  sum_ij ([D^r(h * g)]_ij - f_ij)^2 + lambda sum_ij (grad h)_ij^2
+ * Readings (Sec. 2 gives only the objective and "Adam"):
+ *   - f is K x K (coarse); h lives on the fine grid of Kh = r (K-1) + 1
+ *     pixels per side (odd, centre fine pixel r (K-1)/2 inside the centre
+ *     coarse pixel's block, fine pixel P belonging to coarse pixel P div r);
+ *   - h * g is the zero-padded 'same' convolution on the Kh x Kh grid,
+ *     zero-extended to rK x rK before the r x r block sum D^r;
+ *   - (grad h)^2 = (h[i+1][j]-h[i][j])^2 + (h[i][j+1]-h[i][j])^2 for the
+ *     differences inside the grid;
+ *   - g is a normalised Gaussian given by the caller;
+ *   - Adam (Kingma & Ba) with bias correction; h >= 0 by projection after
+ *     each step.
+ */
+
+/* m = D^r(pad(h * g)), m is K x K. */
+void oracle_psf_model(const double *h, int Kh, const double *g, int Kg, int r,
+                      int K, double *m)
+{
+    double *q = (double *)malloc(sizeof(double) * Kh * Kh);
+    oracle_conv_same(h, Kh, Kh, g, Kg, q);
+    for (int i = 0; i < K; i++)
+        for (int j = 0; j < K; j++) {
+            double s = 0.0;
+            for (int a = 0; a < r; a++)
+                for (int b = 0; b < r; b++) {
+                    int P = r * i + a, Q = r * j + b;
+                    if (P < Kh && Q < Kh) s += q[P * Kh + Q];
+                }
+            m[i * K + j] = s;
+        }
+    free(q);
+}
+
+/* transpose of oracle_psf_model: out (Kh x Kh) = g-correlation of the
+ * replicated K x K array w, cropped to Kh x Kh. */
+void oracle_psf_model_adjoint(const double *w, int K, const double *g, int Kg,
+                              int r, int Kh, double *out)
+{
+    double *q = (double *)malloc(sizeof(double) * Kh * Kh);
+    for (int P = 0; P < Kh; P++)
+        for (int Q = 0; Q < Kh; Q++) q[P * Kh + Q] = w[(P / r) * K + Q / r];
+    oracle_corr_same(q, Kh, Kh, g, Kg, out);
+    free(q);
+}
+
+/* loss of Eq. (4) at h; the gradient goes to grad when it is not NULL */
+double oracle_psf_loss(const double *h, int Kh, const double *f, int K,
+                       const double *g, int Kg, int r, double lambda,
+                       double *grad)
+{
+    double *m = (double *)malloc(sizeof(double) * K * K);
+    oracle_psf_model(h, Kh, g, Kg, r, K, m);
+    double loss = 0.0;
+    for (int e = 0; e < K * K; e++) {
+        m[e] -= f[e];
+        loss += m[e] * m[e];
+    }
+    if (grad) {
+        oracle_psf_model_adjoint(m, K, g, Kg, r, Kh, grad);
+        for (int e = 0; e < Kh * Kh; e++) grad[e] *= 2.0;
+    }
+    for (int i = 0; i < Kh; i++)
+        for (int j = 0; j < Kh; j++) {
+            const double c = h[i * Kh + j];
+            if (i + 1 < Kh) {
+                const double d = h[(i + 1) * Kh + j] - c;
+                loss += lambda * d * d;
+                if (grad) {
+                    grad[(i + 1) * Kh + j] += 2.0 * lambda * d;
+                    grad[i * Kh + j] -= 2.0 * lambda * d;
+                }
+            }
+            if (j + 1 < Kh) {
+                const double d = h[i * Kh + j + 1] - c;
+                loss += lambda * d * d;
+                if (grad) {
+                    grad[i * Kh + j + 1] += 2.0 * lambda * d;
+                    grad[i * Kh + j] -= 2.0 * lambda * d;
+                }
+            }
+        }
+    free(m);
+    return loss;
+}
+
+/* iters Adam steps from h (in place), projected onto h >= 0 after each. */
+void oracle_psf_fit(double *h, int Kh, const double *f, int K, const double *g,
+                    int Kg, int r, double lambda, double lr, double b1,
+                    double b2, double eps, int iters)
+{
+    const int nh = Kh * Kh;
+    double *mo = (double *)calloc(nh, sizeof(double));
+    double *vo = (double *)calloc(nh, sizeof(double));
+    double *gr = (double *)malloc(sizeof(double) * nh);
+    double p1 = 1.0, p2 = 1.0;
+    for (int k = 1; k <= iters; k++) {
+        oracle_psf_loss(h, Kh, f, K, g, Kg, r, lambda, gr);
+        p1 *= b1;
+        p2 *= b2;
+        for (int e = 0; e < nh; e++) {
+            mo[e] = b1 * mo[e] + (1.0 - b1) * gr[e];
+            vo[e] = b2 * vo[e] + (1.0 - b2) * gr[e] * gr[e];
+            const double mh = mo[e] / (1.0 - p1), vh = vo[e] / (1.0 - p2);
+            h[e] = fmax(h[e] - lr * mh / (sqrt(vh) + eps), 0.0);
+        }
+    }
+    free(mo);
+    free(vo);
+    free(gr);
+}

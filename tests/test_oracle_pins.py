@@ -404,3 +404,77 @@ def test_streaming_keeps_the_noise_free_truth(r):
     y = np.stack([synth.block_sum(ss.convolve2d(x_true, f[t], mode="same"), r) for t in range(n)])
     u = g.uniform(0.3, 1.0, (n, H, W))
     np.testing.assert_allclose(oracle.em_streaming(x_true, y, u, f, 2, r=r), x_true, rtol=1e-12)
+
+
+# -- PSF super-resolution fit, Eq. (4) ------------------------------------------------
+
+def gauss_kernel(r):
+    """Normalised Gaussian with FWHM r fine pixels (the width of Eq. (4)'s g)."""
+    sig = r / (2.0 * np.sqrt(2.0 * np.log(2.0)))
+    k = int(np.ceil(3 * sig))
+    yy, xx = np.mgrid[-k:k + 1, -k:k + 1]
+    g = np.exp(-(xx ** 2 + yy ** 2) / (2 * sig * sig))
+    return g / g.sum()
+
+
+def psf_model_numpy(h, g, r, K):
+    q = ss.convolve2d(h, g, mode="same")
+    Kh = h.shape[0]
+    full = np.zeros((r * K, r * K))
+    full[:Kh, :Kh] = q
+    return full.reshape(K, r, K, r).sum(axis=(1, 3))
+
+
+def psf_loss_numpy(h, f, g, r, lam):
+    K = f.shape[0]
+    res = psf_model_numpy(h, g, r, K) - f
+    return (res ** 2).sum() + lam * ((np.diff(h, axis=0) ** 2).sum() + (np.diff(h, axis=1) ** 2).sum())
+
+
+@pytest.mark.parametrize("K,r", [(7, 2), (9, 3), (5, 1)])
+def test_psf_model_library_and_adjoint(K, r):
+    g_ = rng(K + r)
+    Kh = oracle.psf_fine_side(K, r)
+    h = g_.uniform(0, 1, (Kh, Kh))
+    g = gauss_kernel(r)
+    np.testing.assert_allclose(oracle.psf_model(h, g, r, K), psf_model_numpy(h, g, r, K),
+                               rtol=1e-13, atol=1e-14)
+    w = g_.standard_normal((K, K))
+    lhs = float(np.vdot(oracle.psf_model(h, g, r, K), w))
+    rhs = float(np.vdot(h, oracle.psf_model_adjoint(w, g, r, Kh)))
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+
+
+def test_psf_loss_and_gradient():
+    g_ = rng(3)
+    K, r, lam = 9, 2, 0.3
+    Kh = oracle.psf_fine_side(K, r)
+    g = gauss_kernel(r)
+    f = synth.moffat_psf(K, 2.5, 3.0)
+    h = g_.uniform(0, 0.02, (Kh, Kh))
+    L, gr = oracle.psf_loss(h, f, g, r, lam, grad=True)
+    assert abs(L - psf_loss_numpy(h, f, g, r, lam)) <= 1e-12 * L
+    for idx in [(0, 0), (Kh // 2, Kh // 2), (3, Kh - 1), (Kh - 1, 5)]:
+        e = np.zeros_like(h)
+        e[idx] = 1e-6
+        fd = (psf_loss_numpy(h + e, f, g, r, lam) - psf_loss_numpy(h - e, f, g, r, lam)) / 2e-6
+        assert abs(fd - gr[idx]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_psf_fit_reaches_the_constrained_minimiser():
+    from scipy.optimize import minimize
+    K, r, lam = 9, 2, 1e-3
+    Kh = oracle.psf_fine_side(K, r)
+    g = gauss_kernel(r)
+    f = synth.moffat_psf(K, 2.2, 3.0, ellip=0.1, angle=0.4)
+    h0 = np.kron(f, np.ones((r, r)))[:Kh, :Kh] / r ** 2
+    h = oracle.psf_fit(f, g, r, lam, 20000, 1e-4, h0)
+    res = minimize(lambda z: psf_loss_numpy(z.reshape(Kh, Kh), f, g, r, lam),
+                   h0.ravel(), method="L-BFGS-B", bounds=[(0, None)] * (Kh * Kh),
+                   jac=lambda z: oracle.psf_loss(z.reshape(Kh, Kh), f, g, r, lam, grad=True)[1].ravel(),
+                   options=dict(maxiter=20000, ftol=1e-16, gtol=1e-12))
+    hs = res.x.reshape(Kh, Kh)
+    Lh, Ls = psf_loss_numpy(h, f, g, r, lam), psf_loss_numpy(hs, f, g, r, lam)
+    assert Lh <= Ls * (1 + 1e-6)
+    assert np.linalg.norm(h - hs) <= 1e-4 * np.linalg.norm(hs)
+    assert (h >= 0).all()
