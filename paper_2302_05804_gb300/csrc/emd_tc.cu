@@ -343,16 +343,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       uint32_t be_phase = 1;
       const long long hb = t.hank_block;
       for (int tt = 0; tt < s.n && !*abort; ++tt) {
-        for (int mt = 0; mt < 2; ++mt) {
+        // split products: one pass per forward M-tile with its hi and lo x
+        // bands; one product: a single pass with both M-tiles' bands resident
+        // (the lo slot holds the second band), so consecutive MMAs share B
+        for (int pass = 0; pass < (nprod == 1 ? 1 : 2); ++pass) {
           for (int phi = 0; phi < R2; ++phi) {
             bar_wait(x_empty, xe_phase, abort);
             xe_phase ^= 1u;
-            const int nplanes = (nprod > 1) ? 2 : 1;  // x_lo only feeds the split products
-            bar_expect_tx(x_full, nplanes * xplane_b);
-            for (int hl = 0; hl < nplanes; ++hl) {
+            bar_expect_tx(x_full, 2 * xplane_b);
+            for (int slot = 0; slot < 2; ++slot) {
+              const int hl = (nprod == 1) ? 0 : slot;
+              const int mt = (nprod == 1) ? slot : pass;
               const int plane = (A.pp * 2 + hl) * R2 + phi;
               for (int c = 0; c < t.Kf / 8; ++c)
-                tma_3d(xs + hl * xplane_b + c * t.XRp * 16, &xmap, j0 + 8 * c, i0 + kTcRows * mt,
+                tma_3d(xs + slot * xplane_b + c * t.XRp * 16, &xmap, j0 + 8 * c, i0 + kTcRows * mt,
                        plane, x_full);
             }
             for (int a = 0; a < Kc; ++a) {
@@ -392,11 +396,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       uint32_t ae_phase[2] = {1u, 1u};
       int stage = 0;
       for (int tt = 0; tt < s.n && !*abort; ++tt) {
-        for (int mt = 0; mt < 2; ++mt) {
-          bar_wait(&acc_empty[mt], ae_phase[mt], abort);
-          ae_phase[mt] ^= 1u;
+        for (int pass = 0; pass < (nprod == 1 ? 1 : 2); ++pass) {
+          const int mt0 = (nprod == 1) ? 0 : pass;
+          const int mt1 = (nprod == 1) ? 1 : pass;
+          for (int mt = mt0; mt <= mt1; ++mt) {
+            bar_wait(&acc_empty[mt], ae_phase[mt], abort);
+            ae_phase[mt] ^= 1u;
+          }
           tc_fence_after();
-          const uint32_t dacc = tmem + (uint32_t)(128 * mt);
+          const uint32_t dacc = tmem + (uint32_t)(128 * mt0);
           uint32_t accum = 0;
           for (int phi = 0; phi < R2; ++phi) {
             bar_wait(x_full, xf_phase, abort);
@@ -406,7 +414,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               bar_wait(&b_full[stage], bf_phase, abort);
               tc_fence_after();
               const uint32_t bst = ring_a + stage * t.stage_bytes;
-              // descriptor bases; a k-step advances the start-address field
+              // descriptor bases; a k-step advances the start-address field.
+              // Split: ah/al = x_hi/x_lo of this M-tile. One product: ah/al =
+              // x of M-tile 0 / M-tile 1.
               uint64_t ah = sdesc(xs_a + a * 16, x_lbo, 128);
               uint64_t al = ah + (xplane_b >> 4);
               uint64_t bh = sdesc(bst, 128, 128);
@@ -414,12 +424,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               const uint64_t astep = (2u * x_lbo) >> 4, bstep = 256u >> 4;
 #pragma unroll 2
               for (int kk = 0; kk < KSf; ++kk) {
-                mma(dacc, ah, bh, idesc_f, accum);
-                accum = 1;
                 if (nprod == 3) {
+                  mma(dacc, ah, bh, idesc_f, accum);
                   mma(dacc, ah, bl, idesc_f, 1u);
                   mma(dacc, al, bh, idesc_f, 1u);
+                } else {
+                  mma(dacc, ah, bh, idesc_f, accum);
+                  mma(dacc + 128u, al, bh, idesc_f, accum);
                 }
+                accum = 1;
                 ah += astep;
                 al += astep;
                 bh += bstep;
@@ -430,7 +443,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             mma_commit(x_empty);
           }
-          mma_commit(&acc_full[mt]);
+          for (int mt = mt0; mt <= mt1; ++mt) mma_commit(&acc_full[mt]);
         }
         // adjoint of this exposure into the Den partial (tensor-memory
         // columns 256 + 64 phi), once the epilogue has taken the last one
