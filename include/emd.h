@@ -235,6 +235,40 @@ int emd_batch_config(emd_batch *b, int *clusters, int *order, int *max_clusters)
 int emd_frame_stats_noalloc(const float *y, const float *v, const uint8_t *mask,
                             int H, int W, int n, double *out, void *stream);
 
+/*
+ * emd_fit_psf -- super-resolved PSFs of Eq. (4) (Sec. 2): for each of the n
+ * coarse PSFs f_t (K x K, odd K) find the fine PSF
+ *   h_t = argmin_{h >= 0} sum_ij ([D^r(h * g)]_ij - f_t,ij)^2
+ *                         + lambda sum_ij (grad h)_ij^2
+ * by `iters` steps of projected Adam (bias-corrected, beta1 0.9, beta2
+ * 0.999, epsilon 1e-8, step `lr`; h is clipped to >= 0 after every step).
+ * h_t has Kh = r (K-1) + 1 fine pixels per side (odd), fine pixel P lying
+ * in coarse pixel P div r, so it is directly the K = Kh PSF of an r x r
+ * super-resolution context (emd_create(..., Kh, r)). h * g is the
+ * zero-padded 'same' convolution on the Kh x Kh grid, zero-extended to
+ * rK x rK before the block sum D^r; (grad h)^2 is the sum of squared
+ * forward differences inside the grid.
+ *
+ * f: n x K x K float32, row-major; g: Kg x Kg float32 (odd Kg, the
+ * broadening kernel of Eq. (4), e.g. a Gaussian whose FWHM is one coarse
+ * pixel); h0: n x Kh x Kh start, or NULL for the coarse PSF spread evenly
+ * over each block (h0[P][Q] = f[P div r][Q div r] / r^2); h_out: n x Kh x Kh;
+ * loss_out: n floats (the Eq. (4) loss at the returned h, FP32) or NULL.
+ * Every buffer may be host or device memory (caller-owned; host buffers are
+ * staged through a temporary device allocation). One CTA fits one PSF with
+ * all of its state resident on chip; the call runs on the legacy default
+ * stream and returns when the fit is done. EMD_EINVAL for NULL f/g/h_out,
+ * even K or Kg, r outside 1..8, K or Kg above EMD_PSF_MAX_COARSE,
+ * iters < 0, lambda < 0 or lr <= 0; EMD_EUNSUPPORTED when Kh is too large
+ * for one CTA's shared memory (2 Kh^2 + 2 K^2 + Kg^2 floats above 200 KB;
+ * Kh up to about 140 fits, e.g. K = 43 with r = 2 or 3);
+ * EMD_ENOMEM / EMD_ECUDA on device failures.
+ */
+#define EMD_PSF_MAX_COARSE 127
+int emd_fit_psf(const float *f, int n, int K, int r, const float *g, int Kg,
+                const float *h0, float lambda, float lr, int iters, float *h_out,
+                float *loss_out);
+
 #ifdef __cplusplus
 }
 #endif

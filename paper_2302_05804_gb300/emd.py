@@ -37,7 +37,7 @@ EXPORTS = [
     "emd_set_precision", "emd_get_numerator", "emd_get_weights", "emd_frame_stats_noalloc",
     "emd_batch_create", "emd_batch_destroy", "emd_batch_add", "emd_batch_remove",
     "emd_batch_step", "emd_batch_remaining", "emd_batch_sync", "emd_batch_config",
-    "emd_selftest_wait_timeout", "emd_iterate_streaming",
+    "emd_selftest_wait_timeout", "emd_iterate_streaming", "emd_fit_psf",
 ]
 
 
@@ -104,6 +104,8 @@ def load(build_if_missing: bool = False):
         lib.emd_batch_remaining.argtypes = [vp, i]
         lib.emd_batch_sync.argtypes = [vp]
         lib.emd_batch_config.argtypes = [vp, ip, ip, ip]
+        lib.emd_fit_psf.argtypes = [vp, i, i, i, vp, i, vp, C.c_float, C.c_float, i, vp, vp]
+        lib.emd_fit_psf.restype = i
         for name in ("emd_batch_add", "emd_batch_remove", "emd_batch_step",
                      "emd_batch_remaining", "emd_batch_sync", "emd_batch_config"):
             getattr(lib, name).restype = i
@@ -219,6 +221,30 @@ def emd_frame_stats_noalloc(y, v, mask, H: int, W: int, n: int, out, stream=None
     _check(load().emd_frame_stats_noalloc(_ptr(y, np.float32, "y"), _ptr(v, np.float32, "v"),
                                           _ptr(mask, np.uint8, "mask"), H, W, n,
                                           out.data_ptr(), stream))
+
+
+def emd_fit_psf(f, g, r: int, lam: float, lr: float, iters: int, h0=None, h_out=None,
+                loss_out=None):
+    """Eq. (4) fit of n super-resolved PSFs: f is n x K x K (or K x K), g is
+    Kg x Kg, both float32 (numpy or torch, host or device). Returns (h, loss):
+    h is n x Kh x Kh with Kh = r (K-1) + 1 (h_out when given), loss the n
+    final Eq. (4) losses (loss_out when given; host array otherwise)."""
+    single = len(f.shape) == 2
+    n = 1 if single else int(f.shape[0])
+    K, Kg = int(f.shape[-1]), int(g.shape[-1])
+    Kh = r * (K - 1) + 1
+    own_h, own_l = h_out is None, loss_out is None
+    if own_h:
+        h_out = np.empty((n, Kh, Kh), np.float32)
+    if own_l:
+        loss_out = np.empty(n, np.float32)
+    _check(load().emd_fit_psf(_ptr(f, np.float32, "f"), n, K, int(r), _ptr(g, np.float32, "g"), Kg,
+                              _ptr(h0, np.float32, "h0"), float(lam), float(lr), int(iters),
+                              _ptr(h_out, np.float32, "h_out"),
+                              _ptr(loss_out, np.float32, "loss_out")))
+    if single:
+        return (h_out[0] if own_h else h_out), (float(loss_out[0]) if own_l else loss_out)
+    return h_out, loss_out
 
 
 def emd_selftest_wait_timeout(ctx, spins: int = 1000) -> int:

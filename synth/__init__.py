@@ -39,6 +39,17 @@ __all__ = [
 # PSFs and sources
 # ---------------------------------------------------------------------------
 
+def gaussian_kernel(fwhm: float) -> np.ndarray:
+    """Normalised circular Gaussian with the given FWHM in pixels, sampled at
+    pixel centres out to 3 sigma (odd side): the broadening kernel g of the
+    Eq. (4) PSF fit, whose FWHM is one coarse pixel (r fine pixels)."""
+    sig = fwhm / (2.0 * np.sqrt(2.0 * np.log(2.0)))
+    k = int(np.ceil(3 * sig))
+    yy, xx = np.mgrid[-k:k + 1, -k:k + 1]
+    g = np.exp(-(xx ** 2 + yy ** 2) / (2 * sig * sig))
+    return g / g.sum()
+
+
 def moffat_psf(K: int, fwhm: float, beta: float, ellip: float = 0.0,
                angle: float = 0.0) -> np.ndarray:
     """K x K Moffat profile (1 + R^2/alpha^2)^-beta sampled at pixel centres.

@@ -69,3 +69,17 @@ def test_null_context_is_an_error(lib):
     with pytest.raises(emd.EMDError) as ei:
         emd.emd_iterate(None, 1)
     assert ei.value.code == emd.EMD_EINVAL
+
+
+def test_fit_psf_rejects_bad_arguments_before_touching_the_gpu(lib):
+    import numpy as np
+    from paper_2302_05804_gb300 import emd
+    g = np.ones((3, 3), np.float32) / 9
+    for f, r, lam, lr, it in [(np.ones((1, 8, 8), np.float32), 2, 0.0, 1e-4, 1),   # even K
+                              (np.ones((1, 9, 9), np.float32), 0, 0.0, 1e-4, 1),   # r = 0
+                              (np.ones((1, 9, 9), np.float32), 2, -1.0, 1e-4, 1),  # lambda < 0
+                              (np.ones((1, 9, 9), np.float32), 2, 0.0, 0.0, 1),    # lr = 0
+                              (np.ones((1, 9, 9), np.float32), 2, 0.0, 1e-4, -1)]:  # iters < 0
+        with pytest.raises(emd.EMDError) as e:
+            emd.emd_fit_psf(f, g, r, lam, lr, it)
+        assert e.value.code == emd.EMD_EINVAL

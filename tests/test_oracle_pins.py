@@ -410,11 +410,7 @@ def test_streaming_keeps_the_noise_free_truth(r):
 
 def gauss_kernel(r):
     """Normalised Gaussian with FWHM r fine pixels (the width of Eq. (4)'s g)."""
-    sig = r / (2.0 * np.sqrt(2.0 * np.log(2.0)))
-    k = int(np.ceil(3 * sig))
-    yy, xx = np.mgrid[-k:k + 1, -k:k + 1]
-    g = np.exp(-(xx ** 2 + yy ** 2) / (2 * sig * sig))
-    return g / g.sum()
+    return synth.gaussian_kernel(r)
 
 
 def psf_model_numpy(h, g, r, K):
