@@ -80,6 +80,7 @@ def _load():
             lib.oracle_psf_loss.restype = C.c_double
             d_ = C.c_double
             lib.oracle_psf_fit.argtypes = [dp, i, dp, i, dp, i, i, d_, d_, d_, d_, d_, i]
+            lib.oracle_psf_fit.restype = d_
             lib.oracle_chi2.argtypes = [dp, dp, dp, dp, i, i, i, i, i]
             lib.oracle_chi2.restype = C.c_double
             lib.oracle_logdet.argtypes = [dp, dp, C.c_long]
@@ -260,12 +261,13 @@ def psf_loss(h, f, g, r, lam, grad=False):
     return (L, gr) if grad else L
 
 
-def psf_fit(f, g, r, lam, iters, lr, h0, b1=0.9, b2=0.999, eps=1e-8):
-    """iters projected Adam steps on Eq. (4) from h0."""
+def psf_fit(f, g, r, lam, iters, lr, h0, b1=0.9, b2=0.999, eps=1e-8, with_loss=False):
+    """iters projected Adam steps on Eq. (4) from h0; the iterate of lowest
+    loss among h0 .. h_iters (and that loss when with_loss)."""
     h, f, g = _d(h0).copy(), _d(f), _d(g)
-    _load().oracle_psf_fit(_p(h), h.shape[0], _p(f), f.shape[0], _p(g), g.shape[0], r,
-                           float(lam), float(lr), float(b1), float(b2), float(eps), int(iters))
-    return h
+    L = _load().oracle_psf_fit(_p(h), h.shape[0], _p(f), f.shape[0], _p(g), g.shape[0], r,
+                               float(lam), float(lr), float(b1), float(b2), float(eps), int(iters))
+    return (h, L) if with_loss else h
 
 
 def chi2(x, y, u, f, r=1):

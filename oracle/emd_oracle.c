@@ -533,18 +533,27 @@ double oracle_psf_loss(const double *h, int Kh, const double *f, int K,
     return loss;
 }
 
-/* iters Adam steps from h (in place), projected onto h >= 0 after each. */
-void oracle_psf_fit(double *h, int Kh, const double *f, int K, const double *g,
-                    int Kg, int r, double lambda, double lr, double b1,
-                    double b2, double eps, int iters)
+/* iters Adam steps from h, projected onto h >= 0 after each. Adam at a
+ * fixed step does not descend monotonically (once its second moments have
+ * decayed it makes intermittent excursions), so the estimate of the argmin
+ * of Eq. (4) is the iterate of lowest loss among h_0 .. h_iters (the first
+ * such on ties); it is written back to h and its loss returned. */
+double oracle_psf_fit(double *h, int Kh, const double *f, int K, const double *g,
+                      int Kg, int r, double lambda, double lr, double b1,
+                      double b2, double eps, int iters)
 {
     const int nh = Kh * Kh;
     double *mo = (double *)calloc(nh, sizeof(double));
     double *vo = (double *)calloc(nh, sizeof(double));
     double *gr = (double *)malloc(sizeof(double) * nh);
-    double p1 = 1.0, p2 = 1.0;
+    double *best = (double *)malloc(sizeof(double) * nh);
+    double p1 = 1.0, p2 = 1.0, lbest = 0.0;
     for (int k = 1; k <= iters; k++) {
-        oracle_psf_loss(h, Kh, f, K, g, Kg, r, lambda, gr);
+        const double L = oracle_psf_loss(h, Kh, f, K, g, Kg, r, lambda, gr);
+        if (k == 1 || L < lbest) {
+            lbest = L;
+            memcpy(best, h, sizeof(double) * nh);
+        }
         p1 *= b1;
         p2 *= b2;
         for (int e = 0; e < nh; e++) {
@@ -554,7 +563,15 @@ void oracle_psf_fit(double *h, int Kh, const double *f, int K, const double *g,
             h[e] = fmax(h[e] - lr * mh / (sqrt(vh) + eps), 0.0);
         }
     }
+    const double L = oracle_psf_loss(h, Kh, f, K, g, Kg, r, lambda, NULL);
+    if (iters >= 1 && !(L < lbest)) {
+        memcpy(h, best, sizeof(double) * nh);
+    } else {
+        lbest = L;
+    }
     free(mo);
     free(vo);
     free(gr);
+    free(best);
+    return lbest;
 }

@@ -474,3 +474,46 @@ def test_psf_fit_reaches_the_constrained_minimiser():
     assert Lh <= Ls * (1 + 1e-6)
     assert np.linalg.norm(h - hs) <= 1e-4 * np.linalg.norm(hs)
     assert (h >= 0).all()
+
+
+def adam_iterates_numpy(f, g, r, lam, lr, iters, h0):
+    """Every iterate h_0 .. h_iters of projected Adam on Eq. (4) (Kingma & Ba
+    with bias correction), gradients by the chain rule through the library
+    model psf_model_numpy."""
+    K = f.shape[0]
+    Kh = h0.shape[0]
+    h, m, v = h0.copy(), np.zeros_like(h0), np.zeros_like(h0)
+    out = [h.copy()]
+    for k in range(1, iters + 1):
+        res = psf_model_numpy(h, g, r, K) - f
+        rep = np.kron(res, np.ones((r, r)))[:Kh, :Kh]
+        gr = 2 * ss.correlate2d(rep, g, mode="same")
+        gr[1:] += 2 * lam * np.diff(h, axis=0)
+        gr[:-1] -= 2 * lam * np.diff(h, axis=0)
+        gr[:, 1:] += 2 * lam * np.diff(h, axis=1)
+        gr[:, :-1] -= 2 * lam * np.diff(h, axis=1)
+        m = 0.9 * m + 0.1 * gr
+        v = 0.999 * v + 0.001 * gr * gr
+        h = np.maximum(h - lr * (m / (1 - 0.9 ** k)) / (np.sqrt(v / (1 - 0.999 ** k)) + 1e-8), 0)
+        out.append(h.copy())
+    return out
+
+
+@pytest.mark.parametrize("iters,lr", [(0, 1e-3), (1, 1e-3), (40, 1e-3), (300, 1e-2)])
+def test_psf_fit_returns_the_lowest_loss_iterate(iters, lr):
+    """Adam at a fixed step is not monotone: with a large step the loss
+    rises again late in the run, and the fit must return the best iterate
+    (the first on ties) with its loss."""
+    K, r, lam = 5, 2, 1e-2
+    g = gauss_kernel(r)
+    f = synth.moffat_psf(K, 1.6, 3.0)
+    Kh = oracle.psf_fine_side(K, r)
+    h0 = np.kron(f, np.ones((r, r)))[:Kh, :Kh] / r ** 2
+    hs = adam_iterates_numpy(f, g, r, lam, lr, iters, h0)
+    Ls = [psf_loss_numpy(h, f, g, r, lam) for h in hs]
+    kbest = int(np.argmin(Ls))
+    h, L = oracle.psf_fit(f, g, r, lam, iters, lr, h0, with_loss=True)
+    np.testing.assert_allclose(h, hs[kbest], rtol=1e-9, atol=1e-15)
+    assert abs(L - Ls[kbest]) <= 1e-12 * Ls[kbest]
+    if iters == 300:
+        assert 0 < kbest < iters   # the case exercises a late rise
