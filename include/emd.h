@@ -242,6 +242,9 @@ int emd_frame_stats_noalloc(const float *y, const float *v, const uint8_t *mask,
  *                         + lambda sum_ij (grad h)_ij^2
  * by `iters` steps of projected Adam (bias-corrected, beta1 0.9, beta2
  * 0.999, epsilon 1e-8, step `lr`; h is clipped to >= 0 after every step).
+ * Adam at a fixed step is not monotone, so the result is the iterate of
+ * lowest Eq. (4) loss among h_0 .. h_iters (the first on ties), with the
+ * loss evaluated in FP32 on the device.
  * h_t has Kh = r (K-1) + 1 fine pixels per side (odd), fine pixel P lying
  * in coarse pixel P div r, so it is directly the K = Kh PSF of an r x r
  * super-resolution context (emd_create(..., Kh, r)). h * g is the
@@ -254,17 +257,21 @@ int emd_frame_stats_noalloc(const float *y, const float *v, const uint8_t *mask,
  * pixel); h0: n x Kh x Kh start, or NULL for the coarse PSF spread evenly
  * over each block (h0[P][Q] = f[P div r][Q div r] / r^2); h_out: n x Kh x Kh;
  * loss_out: n floats (the Eq. (4) loss at the returned h, FP32) or NULL.
+ * h_out also serves as the store of the best iterate during the fit.
  * Every buffer may be host or device memory (caller-owned; host buffers are
- * staged through a temporary device allocation). One CTA fits one PSF with
- * all of its state resident on chip; the call runs on the legacy default
- * stream and returns when the fit is done. EMD_EINVAL for NULL f/g/h_out,
- * even K or Kg, r outside 1..8, K or Kg above EMD_PSF_MAX_COARSE,
- * iters < 0, lambda < 0 or lr <= 0; EMD_EUNSUPPORTED when Kh is too large
- * for one CTA's shared memory (2 Kh^2 + 2 K^2 + Kg^2 floats above 200 KB;
- * Kh up to about 140 fits, e.g. K = 43 with r = 2 or 3);
- * EMD_ENOMEM / EMD_ECUDA on device failures.
+ * staged through a temporary device allocation, which also holds the Adam
+ * moments). One CTA fits one PSF, with h, the residual, f and g resident in
+ * its shared memory for all iterations; the call runs on the legacy default
+ * stream and returns when the fit is done.
+ * Errors: EMD_EINVAL for NULL f/g/h_out, even K or Kg, r outside 1..8, K
+ * above EMD_PSF_MAX_COARSE, Kg above EMD_PSF_MAX_KG, iters < 0, lambda < 0
+ * or lr <= 0; EMD_EUNSUPPORTED when Kh is too large for one CTA's shared
+ * memory (two zero-haloed planes of (Kh + Kg - 1)^2 floats plus 2 K^2 +
+ * 2 Kg^2 floats above 220 KB; Kh up to about 160 fits, e.g. K = 43 with
+ * r = 2 or 3); EMD_ENOMEM / EMD_ECUDA on device failures.
  */
 #define EMD_PSF_MAX_COARSE 127
+#define EMD_PSF_MAX_KG 15
 int emd_fit_psf(const float *f, int n, int K, int r, const float *g, int Kg,
                 const float *h0, float lambda, float lr, int iters, float *h_out,
                 float *loss_out);

@@ -158,3 +158,19 @@ def test_bad_arguments_raise(emd):
         emd.emd_fit_psf(f, g, 2, -1.0, 1e-4, 10)
     with pytest.raises(emd.EMDError):   # fine side 2 (128 - 1) + 1 = 255: too large
         emd.emd_fit_psf(np.ones((1, 127, 127), np.float32), g, 2, 0.0, 1e-4, 1)
+
+
+@pytest.mark.parametrize("n", [1, 19, 80, 160])
+def test_cluster_split_matches_oracle(emd, n):
+    """The library splits each PSF over a cluster of up to 8 CTAs, fewer as
+    the number of PSFs grows (one CTA each from 76 PSFs on); every split
+    must give the oracle's fit."""
+    K, r, lam = 11, 3, 1e-2
+    f = coarse_psfs(n, K, 100 + n)
+    g = synth.gaussian_kernel(r).astype(np.float32)
+    h, loss = emd.emd_fit_psf(f, g, r, lam, 1e-4, 60)
+    for t in sorted({0, n // 2, n - 1}):
+        h0 = default_h0(f[t], r)
+        ho = oracle.psf_fit(f[t], g, r, lam, 60, 1e-4, h0)
+        check_against_oracle(h[t], ho, h0, f[t], g, r, lam)
+        check_reported_loss(loss[t], h[t], f[t], g, r, lam)
