@@ -89,7 +89,9 @@ void emd_destroy(emd_ctx *ctx);
 const char *emd_last_error(void);
 
 /* Order all later work of ctx on `stream` (a cudaStream_t; NULL = legacy
- * default stream). The library never synchronises the device, only this
+ * default stream). Work already queued on the previous stream completes
+ * before anything later queued on the new one (an event hand-off; the call
+ * does not block). The library never synchronises the device, only this
  * stream. */
 int emd_set_stream(emd_ctx *ctx, void *stream);
 

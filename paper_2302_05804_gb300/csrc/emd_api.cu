@@ -79,6 +79,7 @@ struct emd_ctx {
   Layout L;
   int device = 0;
   cudaStream_t st = nullptr;
+  cudaEvent_t handoff = nullptr;  // orders work across emd_set_stream
   char* arena = nullptr;
   float* x[2] = {nullptr, nullptr};
   int cur = 0;
@@ -246,7 +247,11 @@ emd_ctx* emd_create(int H, int W, int n, int psf_k, int r) {
     return nullptr;
   }
   c->arena = static_cast<char*>(p);
-  e = cudaMemset(c->arena, 0, c->L.total);
+  // Zero the arena and wait for it here: a plain cudaMemset would be queued
+  // on the legacy stream, which does not order against the non-blocking
+  // stream the caller may set next, so later uploads could be overwritten.
+  e = cudaMemsetAsync(c->arena, 0, c->L.total, cudaStreamPerThread);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamPerThread);
   if (e != cudaSuccess) {
     set_err("emd_create: cudaMemset failed: %s", cudaGetErrorString(e));
     cudaFree(p);
@@ -272,9 +277,9 @@ emd_ctx* emd_create(int H, int W, int n, int psf_k, int r) {
 void emd_destroy(emd_ctx* c) {
   if (!c) return;
   DeviceGuard dg(c->device);
-  if (c->st) cudaStreamSynchronize(c->st);
-  else cudaDeviceSynchronize();
+  cudaStreamSynchronize(c->st);  // NULL: the legacy default stream
   cudaFree(c->arena);
+  if (c->handoff) cudaEventDestroy(c->handoff);
   if (c->tc_arena) cudaFree(c->tc_arena);
   if (c->Nt) cudaFree(c->Nt);
   delete c;
@@ -282,7 +287,15 @@ void emd_destroy(emd_ctx* c) {
 
 int emd_set_stream(emd_ctx* c, void* stream) {
   if (int rc = check_ctx(c, false)) return rc;
-  c->st = static_cast<cudaStream_t>(stream);
+  cudaStream_t ns = static_cast<cudaStream_t>(stream);
+  if (ns != c->st) {
+    // everything queued on the previous stream precedes what comes next
+    DeviceGuard dg(c->device);
+    if (!c->handoff) CK(cudaEventCreateWithFlags(&c->handoff, cudaEventDisableTiming));
+    CK(cudaEventRecord(c->handoff, c->st));
+    CK(cudaStreamWaitEvent(ns, c->handoff, 0));
+  }
+  c->st = ns;
   return EMD_OK;
 }
 
@@ -317,7 +330,7 @@ int emd_set_precision(emd_ctx* c, int mode) {
       set_err("emd_set_precision: cudaMalloc(%zu) failed: %s", need, cudaGetErrorString(e));
       return EMD_ENOMEM;
     }
-    CK(cudaMemset(p, 0, need));
+    CK(cudaMemsetAsync(p, 0, need, c->st));  // ordered before its first use on c->st
     c->tc_arena = static_cast<char*>(p);
     c->tc_bytes = need;
   }
@@ -524,7 +537,7 @@ int emd_iterate_streaming(emd_ctx* c, int k, const int* order) {
       set_err("emd_iterate_streaming: cudaMalloc of the per-exposure numerators failed");
       return EMD_ENOMEM;
     }
-    CK(cudaMemset(p, 0, (size_t)s.n * lat * sizeof(float)));
+    CK(cudaMemsetAsync(p, 0, (size_t)s.n * lat * sizeof(float), c->st));
     c->Nt = static_cast<float*>(p);
   }
   if (!c->nt_ready) {
@@ -771,7 +784,6 @@ emd_batch* emd_batch_create(int max_jobs) {
     return nullptr;
   }
   b->arena = static_cast<char*>(p);
-  cudaMemset(b->arena, 0, jb + ib + 1024);
   b->d_jobs = reinterpret_cast<emd::BatchJob*>(b->arena);
   b->d_items = reinterpret_cast<int2*>(b->arena + jb);
   b->d_nitems = reinterpret_cast<int*>(b->arena + jb + ib);
@@ -793,6 +805,15 @@ emd_batch* emd_batch_create(int max_jobs) {
     return nullptr;
   }
   b->own_stream = true;
+  // zeroed on the batch's own stream, ahead of every table upload and step
+  if (cudaMemsetAsync(b->arena, 0, jb + ib + 1024, b->st) != cudaSuccess) {
+    cudaGetLastError();
+    set_err("emd_batch_create: memset failed");
+    cudaStreamDestroy(b->st);
+    cudaFree(b->arena);
+    delete b;
+    return nullptr;
+  }
   cudaEventCreate(&b->e0);
   cudaEventCreate(&b->e1);
   return b;

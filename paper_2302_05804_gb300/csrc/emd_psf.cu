@@ -470,7 +470,7 @@ extern "C" int emd_fit_psf(const float* f, int n, int K, int r, const float* g, 
     }
 #undef EMD_FIT_CASE
   }
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (e == cudaSuccess && !hd) e = cudaMemcpy(h_out, dh, hb, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && !ld) e = cudaMemcpy(loss_out, dl, lb, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) rc = psf_fail(EMD_ECUDA, cudaGetErrorString(e));

@@ -277,3 +277,37 @@ def test_streaming_em_parity_and_order(emd, kw):
     a = oracle.em_streaming(x0, y, u, p.f, 3, r=p.r, order=[0, 1, 2])
     assert rel_l2(xg, a) > 10 * rel_l2(xg, oracle.em_streaming(x0, y, u, p.f, 3, r=p.r,
                                                                 order=[2, 0, 1]))
+
+
+def test_contexts_order_against_a_busy_legacy_stream(emd):
+    """A context created while the legacy default stream is busy and then
+    moved to a non-blocking stream must not have its zero-fill land after
+    its uploads, and work queued before emd_set_stream must precede work
+    queued after it: results equal those of an idle device, bit for bit."""
+    torch = pytest.importorskip("torch")
+    p = make(H=128, W=96, n=3, K=9)
+    x0 = start(p, 3)
+
+    def run(busy):
+        side = torch.cuda.Stream()  # created non-blocking by torch
+        if busy:  # ~0.1-0.5 s of work queued on the legacy default stream
+            a = torch.randn(4096, 4096, device="cuda")
+            for _ in range(40):
+                a = a @ a
+                a = a / a.norm()
+        d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+        emd.emd_set_stream(d.ctx, side.cuda_stream)
+        d.set_frames(p.y, p.v, p.f, p.mask)
+        d.set_x(x0)
+        d.iterate(2)
+        other = torch.cuda.Stream()
+        emd.emd_set_stream(d.ctx, other.cuda_stream)   # hand-off with work in flight
+        d.iterate(1)
+        x = d.x()
+        torch.cuda.synchronize()
+        d.close()
+        return x
+
+    ref = run(False)
+    got = run(True)
+    assert np.array_equal(ref, got)
