@@ -81,6 +81,11 @@ def _load():
             d_ = C.c_double
             lib.oracle_psf_fit.argtypes = [dp, i, dp, i, dp, i, i, d_, d_, d_, d_, d_, i]
             lib.oracle_psf_fit.restype = d_
+            lib.oracle_student_weights.argtypes = [dp, dp, dp, C.c_long, d_, dp]
+            lib.oracle_em_step_student.argtypes = [dp, dp, dp, dp, i, i, i, i, i, d_,
+                                                   C.c_void_p, C.c_void_p]
+            lib.oracle_student_loglik.argtypes = [dp, dp, dp, dp, dp, i, i, i, i, i, d_]
+            lib.oracle_student_loglik.restype = d_
             lib.oracle_chi2.argtypes = [dp, dp, dp, dp, i, i, i, i, i]
             lib.oracle_chi2.restype = C.c_double
             lib.oracle_logdet.argtypes = [dp, dp, C.c_long]
@@ -268,6 +273,34 @@ def psf_fit(f, g, r, lam, iters, lr, h0, b1=0.9, b2=0.999, eps=1e-8, with_loss=F
     L = _load().oracle_psf_fit(_p(h), h.shape[0], _p(f), f.shape[0], _p(g), g.shape[0], r,
                                float(lam), float(lr), float(b1), float(b2), float(eps), int(iters))
     return (h, L) if with_loss else h
+
+
+def student_weights(y, u, z, nu):
+    """u' = u (nu+1) / (nu + u (y-z)^2) where u != 0 (heavy-tailed E-step)."""
+    y, u, z = _d(y), _d(u), _d(z)
+    w = np.empty_like(u)
+    _load().oracle_student_weights(_p(y), _p(u), _p(z), u.size, float(nu), _p(w))
+    return w
+
+
+def em_step_student(x, y, u, f, nu, r=1):
+    """One heavy-tailed (Student-t, nu degrees of freedom) EM step.
+    Returns (x', N', Den')."""
+    x, y, u, f = _d(x).copy(), _d(y), _d(u), _d(f)
+    n, H, W, K, r = _dims(u, f, r)
+    num = np.empty_like(x)
+    den = np.empty_like(x)
+    _load().oracle_em_step_student(_p(x), _p(y), _p(u), _p(f), n, H, W, K, r, float(nu),
+                                   num.ctypes.data, den.ctypes.data)
+    return x, num, den
+
+
+def student_loglik(x, y, v, u, f, nu, r=1):
+    """Student-t log-likelihood of x over the valid pixels."""
+    x, y, v, u, f = _d(x), _d(y), _d(v), _d(u), _d(f)
+    n, H, W, K, r = _dims(u, f, r)
+    return _load().oracle_student_loglik(_p(x), _p(y), _p(v), _p(u), _p(f), n, H, W, K, r,
+                                         float(nu))
 
 
 def chi2(x, y, u, f, r=1):

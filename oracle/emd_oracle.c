@@ -312,6 +312,99 @@ void oracle_em_pass_streaming(double *x, const double *y, const double *u,
 }
 
 /* ----------------------------------------------------------------------- */
+/* Heavy-tailed noise (the outlook of Sec. 3: heavier-tailed noise terms)   */
+/* ----------------------------------------------------------------------- */
+/*
+ * Reading: y_t = D^r(f_t * x) + sqrt(v_t) e, e Student-t with nu degrees of
+ * freedom, written as a Gaussian scale mixture (e | s ~ N(0, 1/s),
+ * s ~ Gamma(nu/2, rate nu/2)). The E-step gives each valid pixel the
+ * expected precision scale E[s | y, x] = (nu + 1) / (nu + u (y - z)^2); the
+ * weighted least-squares problem with weights u' = u E[s] is then majorised
+ * exactly as in Eq. (2), so one step is
+ *   N' = sum_t F_t^T(u'_t y_t), Den' = sum_t F_t^T(u'_t z_t),
+ *   x' = Den' > 0 ? x max(N', 0) / Den' : x,
+ * a generalised EM step: it does not decrease the Student-t likelihood. As
+ * nu -> infinity, u' -> u and the step becomes Eq. (2).
+ */
+
+/* u' = u (nu + 1) / (nu + u (y - z)^2) where u != 0, else 0. */
+void oracle_student_weights(const double *y, const double *u, const double *z,
+                            long np, double nu, double *w)
+{
+    for (long i = 0; i < np; i++) {
+        if (u[i] != 0.0) {
+            const double d = y[i] - z[i];
+            w[i] = u[i] * (nu + 1.0) / (nu + u[i] * d * d);
+        } else {
+            w[i] = 0.0;
+        }
+    }
+}
+
+/* One heavy-tailed EM step in place on x; N' and Den' are returned in
+ * num_out / den_out when they are not NULL. y must be finite where u != 0. */
+void oracle_em_step_student(double *x, const double *y, const double *u,
+                            const double *f, int n, int H, int W, int K, int r,
+                            double nu, double *num_out, double *den_out)
+{
+    const long np = (long)H * W, nf = (long)r * r * H * W;
+    double *Num = num_out ? num_out : (double *)malloc(sizeof(double) * nf);
+    double *Den = den_out ? den_out : (double *)malloc(sizeof(double) * nf);
+    double *z = (double *)malloc(sizeof(double) * np);
+    double *w = (double *)malloc(sizeof(double) * np);
+    double *b = (double *)malloc(sizeof(double) * np);
+    double *a = (double *)malloc(sizeof(double) * nf);
+    memset(Num, 0, sizeof(double) * nf);
+    memset(Den, 0, sizeof(double) * nf);
+    for (int t = 0; t < n; t++) {
+        const double *ft = f + (long)t * K * K;
+        const double *yt = y + t * np, *ut = u + t * np;
+        oracle_forward(x, H, W, r, ft, K, z);
+        oracle_student_weights(yt, ut, z, np, nu, w);
+        for (long i = 0; i < np; i++) b[i] = (w[i] != 0.0) ? w[i] * yt[i] : 0.0;
+        oracle_adjoint(b, H, W, r, ft, K, a);
+        for (long i = 0; i < nf; i++) Num[i] += a[i];
+        for (long i = 0; i < np; i++) b[i] = w[i] * z[i];
+        oracle_adjoint(b, H, W, r, ft, K, a);
+        for (long i = 0; i < nf; i++) Den[i] += a[i];
+    }
+    oracle_apply_update(x, Num, Den, nf);
+    if (!num_out) free(Num);
+    if (!den_out) free(Den);
+    free(z);
+    free(w);
+    free(b);
+    free(a);
+}
+
+/* Student-t log-likelihood over the valid pixels:
+ *   sum [lgamma((nu+1)/2) - lgamma(nu/2) - 1/2 log(nu pi v)
+ *        - (nu+1)/2 log(1 + u (y - z)^2 / nu)]. */
+double oracle_student_loglik(const double *x, const double *y, const double *v,
+                             const double *u, const double *f, int n, int H,
+                             int W, int K, int r, double nu)
+{
+    const double pi = 3.14159265358979323846264338327950;
+    const long np = (long)H * W;
+    const double c = lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu);
+    double *z = (double *)malloc(sizeof(double) * np);
+    double s = 0.0;
+    for (int t = 0; t < n; t++) {
+        oracle_forward(x, H, W, r, f + (long)t * K * K, K, z);
+        for (long i = 0; i < np; i++) {
+            const double ui = u[t * np + i];
+            if (ui != 0.0) {
+                const double d = y[t * np + i] - z[i];
+                s += c - 0.5 * log(nu * pi * v[t * np + i]) -
+                     0.5 * (nu + 1.0) * log1p(ui * d * d / nu);
+            }
+        }
+    }
+    free(z);
+    return s;
+}
+
+/* ----------------------------------------------------------------------- */
 /* Log-likelihood of Eq. (1) and the default initial guess                  */
 /* ----------------------------------------------------------------------- */
 

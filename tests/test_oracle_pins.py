@@ -517,3 +517,117 @@ def test_psf_fit_returns_the_lowest_loss_iterate(iters, lr):
     assert abs(L - Ls[kbest]) <= 1e-12 * Ls[kbest]
     if iters == 300:
         assert 0 < kbest < iters   # the case exercises a late rise
+
+
+# -- heavy-tailed (Student-t) noise ------------------------------------------------
+
+def forward_numpy(x, f, r):
+    return np.stack([synth.block_sum(ss.convolve2d(x, f[t], mode="same"), r)
+                     for t in range(f.shape[0])])
+
+
+@pytest.mark.parametrize("K,r", [(3, 1), (5, 1), (3, 2)])
+def test_student_step_matches_dense_brute_force(K, r):
+    g = rng(70 + K + 10 * r)
+    H = W = 8 // r
+    n, nu = 3, 3.0
+    f = np.stack([rand_psf(K, g) for _ in range(n)])
+    x = g.uniform(0.5, 2.0, (r * H, r * W))
+    y = g.normal(2.0, 1.5, (n, H, W))
+    v = g.uniform(0.5, 2.0, (n, H, W))
+    mask = (g.uniform(size=(n, H, W)) > 0.2).astype(np.uint8)
+    u, _ = oracle.weights(v, mask)
+    yy = np.where(mask != 0, y, 0.0)
+    N = np.zeros(r * r * H * W)
+    Den = np.zeros(r * r * H * W)
+    for t in range(n):
+        A = dense_operator(H, W, f[t], r)
+        z = A @ x.ravel()
+        ut = u[t].ravel()
+        s = np.where(ut > 0, (nu + 1) / (nu + ut * (yy[t].ravel() - z) ** 2), 0.0)
+        N += A.T @ (ut * s * yy[t].ravel())
+        Den += A.T @ (ut * s * z)
+    x_ref = np.where(Den > 0, x.ravel() * np.maximum(N, 0) / np.where(Den > 0, Den, 1), x.ravel())
+    x1, num, den = oracle.em_step_student(x, yy, u, f, nu, r)
+    np.testing.assert_allclose(num.ravel(), N, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(den.ravel(), Den, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(x1.ravel(), x_ref, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("r", [1, 2])
+def test_student_reduces_to_eq2_as_nu_grows(r):
+    x_true, y, v, f, mask = small_problem(seed=80 + r, r=r, H=24, W=20, K=5)
+    u, _ = oracle.weights(v, mask, y)
+    yy = np.where(mask != 0, y, 0.0)
+    N = oracle.numerator(yy, u, f, r)
+    x0 = np.full((r * 24, r * 20), 2.0)
+    xg = oracle.em_step(x0, N, u, f, r)
+    xs, num, _ = oracle.em_step_student(x0, yy, u, f, 1e13, r)
+    np.testing.assert_allclose(num, N, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(xs, xg, rtol=1e-9, atol=1e-12)
+
+
+def test_student_loglik_matches_scipy_t_logpdf():
+    from scipy.stats import t as student_t
+    for r, nu in [(1, 2.5), (2, 7.0)]:
+        x_true, y, v, f, mask = small_problem(seed=90 + r, r=r, H=16, W=14, K=5)
+        u, _ = oracle.weights(v, mask, y)
+        yy = np.where(mask != 0, y, 0.0)
+        x = x_true * 0.9 + 0.5
+        z = forward_numpy(x, f, r)
+        ok = mask != 0
+        ref = student_t.logpdf(yy[ok], df=nu, loc=z[ok], scale=np.sqrt(v[ok])).sum()
+        got = oracle.student_loglik(x, yy, v, u, f, nu, r)
+        assert abs(got - ref) <= 1e-10 * abs(ref)
+
+
+def test_student_weights_closed_form():
+    g = rng(95)
+    y, z = g.normal(0, 3, 50), g.normal(0, 3, 50)
+    u = g.uniform(0.1, 2, 50)
+    u[::7] = 0.0
+    w = oracle.student_weights(y, u, z, 4.0)
+    np.testing.assert_allclose(w[u > 0], (u * 5.0 / (4.0 + u * (y - z) ** 2))[u > 0], rtol=1e-15)
+    assert (w[u == 0] == 0).all()
+
+
+@pytest.mark.parametrize("r", [1, 2])
+def test_student_em_is_monotone_and_keeps_the_truth(r):
+    """A generalised EM step never lowers the Student-t likelihood (with
+    outliers, masks and negative data), and noise-free data leave the truth
+    fixed."""
+    x_true, y, v, f, mask = small_problem(seed=100 + r, r=r, H=24, W=22, K=5)
+    g = rng(7)
+    y[0, 5, :] += 400.0                      # a satellite trail in one exposure
+    y[1, g.integers(0, 24, 12), g.integers(0, 22, 12)] += 300.0
+    u, _ = oracle.weights(v, mask, y)
+    yy = np.where(mask != 0, y, 0.0)
+    nu = 3.0
+    x = np.full((r * 24, r * 22), oracle.default_x0(yy, u, r))
+    ll = oracle.student_loglik(x, yy, v, u, f, nu, r)
+    for _ in range(60 if r == 1 else 30):
+        x = oracle.em_step_student(x, yy, u, f, nu, r)[0]
+        assert (x >= 0).all()
+        ll1 = oracle.student_loglik(x, yy, v, u, f, nu, r)
+        assert ll1 >= ll - 1e-12 * abs(ll)
+        ll = ll1
+    y0 = forward_numpy(x_true, f, r)
+    x1 = oracle.em_step_student(x_true, y0, u, f, nu, r)[0]
+    np.testing.assert_allclose(x1, x_true, rtol=1e-12)
+
+
+def test_student_em_resists_outliers_better_than_eq2():
+    x_true, y, v, f, mask = small_problem(seed=120, H=32, W=30, n=4, K=5, mask_frac=0.0)
+    y[0, 10, :] += 2000.0                    # satellite trails the mask missed
+    y[2, :, 7] += 2000.0
+    u, _ = oracle.weights(v, mask, y)
+    yy = np.where(mask != 0, y, 0.0)
+    x0 = np.full((32, 30), oracle.default_x0(yy, u))
+    N = oracle.numerator(yy, u, f)
+    xg, xs = x0.copy(), x0.copy()
+    for _ in range(150):
+        xg = oracle.em_step(xg, N, u, f)
+        xs = oracle.em_step_student(xs, yy, u, f, 3.0)[0]
+    eg = np.linalg.norm(forward_numpy(xg, f, 1) - forward_numpy(x_true, f, 1))
+    es = np.linalg.norm(forward_numpy(xs, f, 1) - forward_numpy(x_true, f, 1))
+    assert es < 0.5 * eg
