@@ -322,6 +322,7 @@ def config_of(args, extra=None):
                      f"{K}x{K} PSFs, r={r}, latent {r * H}x{r * W}",
          "H": H, "W": W, "n": n, "K": K, "r": r,
          "precision": args.precision,
+         "noise": (f"student-t nu={args.nu:g}" if getattr(args, "nu", 0) > 0 else "gaussian"),
          "l2": ("no flush: each step streams the u planes "
                 f"({n * H * W * 4 / 1e9:.1f} GB), far above the 129 MB L2"),
          "parallelism": "replicas"}
@@ -350,6 +351,8 @@ def run_ours(args):
     d.set_frames(p.y, p.v, p.f, p.mask)
     if prec:
         d.set_precision(prec)
+    if args.nu > 0:
+        d.set_noise(emd.EMD_NOISE_STUDENT_T, args.nu)
 
     def barrier():
         if world > 1:
@@ -378,7 +381,8 @@ def run_ours(args):
     total_ms, value = aggregate_over_ranks(ev[0].elapsed_time(ev[-1]), Hf * Wf * p.n * args.steps,
                                            world)
 
-    flops = algorithmic_flops(p.H, p.W, p.n, p.K, p.r)
+    # the heavy-tailed step runs the forward model and the adjoint twice
+    flops = algorithmic_flops(p.H, p.W, p.n, p.K, p.r) * (2 if args.nu > 0 else 1)
     launch_s = statistics.mean(per) / 1e3
     achieved = flops / launch_s / 1e12
     if prec == 0:
@@ -466,7 +470,8 @@ def run_ours(args):
                       "fp16": "f16", "split_fp16": "f16x3"}[args.precision],
             "data": "synthetic",
             "config": config_of(args), "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": e2e, "gpu_launches": args.steps * LAUNCHES_PER_STEP[args.precision],
+            "e2e": e2e,
+            "gpu_launches": args.steps * LAUNCHES_PER_STEP[args.precision] * (2 if args.nu > 0 else 1),
             "clocks": clocks,
             "serving": serving, "psf_fit": psf_fit,
         }
@@ -492,6 +497,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=40,
                     help="jobs in the serving sample (0 disables it)")
+    ap.add_argument("--nu", type=float, default=0.0,
+                    help="Student-t degrees of freedom of the heavy-tailed noise model "
+                         "(0: Gaussian, Eq. (1))")
     ap.add_argument("--psf-iters", type=int, default=20000,
                     help="Adam iterations of the Eq. (4) PSF fit sample (0 disables it)")
     ap.add_argument("--cpu-crop", type=int, default=512)

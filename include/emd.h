@@ -144,6 +144,32 @@ int emd_loglik(emd_ctx *ctx, double *out, double *chi2);
  * into this library return EMD_EUNSUPPORTED and leave the mode unchanged. */
 int emd_set_precision(emd_ctx *ctx, int mode);
 
+/*
+ * Noise model of the likelihood (Sec. 3's outlook: heavier-tailed noise
+ * terms for robustness to outliers such as satellite trails).
+ * EMD_NOISE_GAUSSIAN (default): Eq. (1), update Eq. (2).
+ * EMD_NOISE_STUDENT_T: y_t - D^r(f_t * x) = sqrt(v_t) e, e Student-t with nu
+ * degrees of freedom. Each emd_iterate step is then a generalised EM step:
+ * with z_t = D^r(f_t * x) and weights u' = u (nu+1) / (nu + u (y - z)^2)
+ * (the expected precision scale of the Gaussian scale mixture),
+ *   x <- x . max(sum_t F_t^T(u'_t y_t), 0) / sum_t F_t^T(u'_t z_t)
+ * (x unchanged where the denominator is 0); it never lowers the Student-t
+ * likelihood, and tends to Eq. (2) as nu grows. It costs two forward and
+ * two adjoint passes per iteration (Eq. (2): one each). emd_loglik then
+ * returns the Student-t log-likelihood
+ *   sum_valid [lgamma((nu+1)/2) - lgamma(nu/2) - 1/2 log(nu pi v)
+ *              - (nu+1)/2 log(1 + u (y - z)^2 / nu)]
+ * and *chi2 = sum_valid (nu+1) log(1 + u (y - z)^2 / nu).
+ * nu: finite, in (0, 1e30] (ignored for the Gaussian model). The heavy-tailed
+ * model runs on the FP32 kernel only: EMD_EUNSUPPORTED with a tensor-core
+ * precision, in emd_iterate_streaming and in emd_batch_add.
+ */
+enum emd_noise {
+    EMD_NOISE_GAUSSIAN = 0,
+    EMD_NOISE_STUDENT_T = 1
+};
+int emd_set_noise(emd_ctx *ctx, int model, double nu);
+
 /* Self-test of failure detection: launches, on ctx's stream, one CTA that
  * waits on an mbarrier nothing ever arrives on, with the same bounded-wait
  * code the kernels use but a limit of `spins` polls. The wait gives up, the

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <string>
 #include <vector>
@@ -39,7 +40,7 @@ Layout make_layout(const Shape& s) {
   const size_t lat = (size_t)s.R2 * s.g.plane * sizeof(float);
   const size_t exp = (size_t)s.n * s.g.plane * sizeof(float);
   const size_t ker = (size_t)s.n * s.R2 * s.Kc * s.KP * sizeof(float);
-  size_t parts = (size_t)emd::kRedBlocks * 3;
+  size_t parts = (size_t)emd::kRedBlocks * 4;
   if ((size_t)emd::fused_blocks(s) > parts) parts = emd::fused_blocks(s);
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
@@ -87,7 +88,11 @@ struct emd_ctx {
   float *kf = nullptr, *ka = nullptr, *fraw = nullptr;
   double *part = nullptr, *sums = nullptr;
   int* err = nullptr;
-  double logdet = 0.0, suy = 0.0, su = 0.0;
+  double logdet = 0.0, suy = 0.0, su = 0.0, nvalid = 0.0;
+  // noise model: Gaussian (Eq. (1)) or Student-t with nu degrees of freedom
+  int noise = EMD_NOISE_GAUSSIAN;
+  double nu = 0.0;
+  float* Ns = nullptr;  // heavy-tailed numerator (latent planes), allocated on first use
   bool frames = false;
   int prec = EMD_PREC_FP32;
   // tensor-core path (allocated when a tensor-core mode is first selected)
@@ -167,6 +172,7 @@ emd::FusedArgs fused_args(emd_ctx* c) {
   a.err = c->err;
   a.t0 = 0;
   a.t1 = c->s.n;
+  a.nu = c->noise == EMD_NOISE_STUDENT_T ? (float)c->nu : 0.f;
   return a;
 }
 
@@ -282,6 +288,7 @@ void emd_destroy(emd_ctx* c) {
   if (c->handoff) cudaEventDestroy(c->handoff);
   if (c->tc_arena) cudaFree(c->tc_arena);
   if (c->Nt) cudaFree(c->Nt);
+  if (c->Ns) cudaFree(c->Ns);
   delete c;
 }
 
@@ -308,6 +315,10 @@ int emd_set_precision(emd_ctx* c, int mode) {
   if (mode < 0 || mode > EMD_PREC_SPLIT_FP16) {
     set_err("unknown precision mode %d", mode);
     return EMD_EINVAL;
+  }
+  if (c->noise != EMD_NOISE_GAUSSIAN) {
+    set_err("emd_set_precision: the heavy-tailed update runs on the FP32 kernel only");
+    return EMD_EUNSUPPORTED;
   }
   DeviceGuard dg(c->device);
   emd::TcShape t;
@@ -381,11 +392,11 @@ int emd_set_frames(emd_ctx* c, const float* y, const float* v, const float* f,
   emd::SetupArgs sa{dmask, c->u, c->y, c->part, c->err};
   CK(emd::launch_setup(s, sa, c->st));
   if (tmp) CK(cudaFreeAsync(tmp, c->st));
-  CK(emd::launch_reduce_final(c->part, emd::kRedBlocks, 3, c->sums, c->st));
+  CK(emd::launch_reduce_final(c->part, emd::kRedBlocks, 4, c->sums, c->st));
   CK(emd::launch_build_kernels(s, c->fraw, c->kf, c->ka, c->st));
-  double h[3];
+  double h[4];
   int herr = 0;
-  CK(cudaMemcpyAsync(h, c->sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(h, c->sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CK(cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   if (herr & emd::kErrData) {
@@ -396,6 +407,7 @@ int emd_set_frames(emd_ctx* c, const float* y, const float* v, const float* f,
   c->logdet = h[0];
   c->suy = h[1];
   c->su = h[2];
+  c->nvalid = h[3];
   // numerator N = sum_t F_t^T (u_t y_t)
   emd::FusedArgs a = fused_args(c);
   CK(emd::launch_fused(s, a, 1, c->part, c->st));
@@ -498,6 +510,20 @@ int emd_iterate(emd_ctx* c, int k) {
     }
     return EMD_OK;
   }
+  if (c->noise == EMD_NOISE_STUDENT_T) {
+    // heavy-tailed EM: the numerator depends on x through the weights, so
+    // each iteration runs the forward model twice: N' (mode 3), then Den'
+    // and the update (mode 0), both with the weights u' of the current x
+    for (int it = 0; it < k; ++it) {
+      emd::FusedArgs a = fused_args(c);
+      a.Nw = c->Ns;
+      CK(emd::launch_fused(c->s, a, 3, c->part, c->st));
+      a.N = c->Ns;
+      CK(emd::launch_fused(c->s, a, 0, c->part, c->st));
+      c->cur ^= 1;
+    }
+    return EMD_OK;
+  }
   for (int it = 0; it < k; ++it) {
     emd::FusedArgs a = fused_args(c);
     CK(emd::launch_fused(c->s, a, 0, c->part, c->st));
@@ -506,9 +532,49 @@ int emd_iterate(emd_ctx* c, int k) {
   return EMD_OK;
 }
 
+int emd_set_noise(emd_ctx* c, int model, double nu) {
+  if (int rc = check_ctx(c, false)) return rc;
+  if (model == EMD_NOISE_GAUSSIAN) {
+    c->noise = model;
+    c->nu = 0.0;
+    return EMD_OK;
+  }
+  if (model != EMD_NOISE_STUDENT_T) {
+    set_err("emd_set_noise: unknown noise model %d", model);
+    return EMD_EINVAL;
+  }
+  if (!(nu > 0.0) || !std::isfinite(nu) || nu > 1e30) {
+    set_err("emd_set_noise: nu must be finite and in (0, 1e30]");
+    return EMD_EINVAL;
+  }
+  if (c->prec != EMD_PREC_FP32) {
+    set_err("emd_set_noise: the heavy-tailed update runs on the FP32 kernel (set precision FP32)");
+    return EMD_EUNSUPPORTED;
+  }
+  if (!c->Ns) {
+    DeviceGuard dg(c->device);
+    void* p = nullptr;
+    const size_t bytes = (size_t)c->s.R2 * c->s.g.plane * sizeof(float);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_err("emd_set_noise: cudaMalloc of the numerator planes failed");
+      return EMD_ENOMEM;
+    }
+    CK(cudaMemsetAsync(p, 0, bytes, c->st));
+    c->Ns = static_cast<float*>(p);
+  }
+  c->noise = model;
+  c->nu = nu;
+  return EMD_OK;
+}
+
 int emd_iterate_streaming(emd_ctx* c, int k, const int* order) {
   if (int rc = check_ctx(c, true)) return rc;
   const Shape& s = c->s;
+  if (c->noise != EMD_NOISE_GAUSSIAN) {
+    set_err("emd_iterate_streaming: Gaussian noise only");
+    return EMD_EUNSUPPORTED;
+  }
   if (k < 0) {
     set_err("emd_iterate_streaming: k must be >= 0");
     return EMD_EINVAL;
@@ -609,11 +675,21 @@ int emd_loglik(emd_ctx* c, double* out, double* chi2) {
   DeviceGuard dg(c->device);
   emd::FusedArgs a = fused_args(c);
   CK(emd::launch_fused(c->s, a, 2, c->part, c->st));
-  CK(emd::launch_reduce_final(c->part, emd::fused_blocks(c->s), 1, c->sums + 3, c->st));
+  CK(emd::launch_reduce_final(c->part, emd::fused_blocks(c->s), 1, c->sums + 4, c->st));
   double h = 0.0;
-  CK(cudaMemcpyAsync(&h, c->sums + 3, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(&h, c->sums + 4, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   if (int rc = check_device_error(c)) return rc;
-  *out = -0.5 * (h + c->logdet);
+  if (c->noise == EMD_NOISE_STUDENT_T) {
+    // sum over valid pixels of lgamma((nu+1)/2) - lgamma(nu/2) - 1/2 log(nu pi v)
+    // - (nu+1)/2 log(1 + u r^2 / nu); h holds the last term's sum times 2
+    const double nu = c->nu, kPi = 3.14159265358979323846, k2Pi = 6.28318530717958647692;
+    const double sum_log_v = c->logdet - c->nvalid * std::log(k2Pi);
+    *out = c->nvalid * (std::lgamma(0.5 * (nu + 1.0)) - std::lgamma(0.5 * nu) -
+                        0.5 * std::log(nu * kPi)) -
+           0.5 * sum_log_v - 0.5 * h;
+  } else {
+    *out = -0.5 * (h + c->logdet);
+  }
   if (chi2) *chi2 = h;
   return EMD_OK;
 }
@@ -838,8 +914,8 @@ int emd_batch_add(emd_batch* b, emd_ctx* c, int iterations) {
     set_err("emd_batch_add: iterations must be >= 0");
     return EMD_EINVAL;
   }
-  if (c->prec != EMD_PREC_FP32) {
-    set_err("emd_batch_add: batched jobs run the FP32 kernel (set precision FP32)");
+  if (c->prec != EMD_PREC_FP32 || c->noise != EMD_NOISE_GAUSSIAN) {
+    set_err("emd_batch_add: batched jobs run the FP32 Gaussian-noise kernel");
     return EMD_EUNSUPPORTED;
   }
   if (c->device != b->device) {

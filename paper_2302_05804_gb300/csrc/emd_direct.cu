@@ -218,6 +218,10 @@ __device__ __forceinline__ double block_sum_f64(double v, double* red /* >= 8 */
 // mode 0: one EM iteration x -> xn (Eq. (2)).
 // mode 1: N = sum_t F_t^T (u_t y_t) into a.N.
 // mode 2: chi2 = sum_t sum_i u (y - F_t x)^2 of the tile into part[block].
+// mode 3: N' = sum_t F_t^T (u'_t y_t) into a.Nw (heavy-tailed numerator).
+// With a.nu > 0 (Student-t noise, nu degrees of freedom) the weights of
+// modes 0 and 3 are u' = u (nu+1) / (nu + u (y - z)^2), z = F_t x, and mode 2
+// sums (nu+1) log(1 + u (y - z)^2 / nu) instead of u (y - z)^2.
 //
 // Cluster barrier protocol of mode 0 (every thread of both CTAs, in order):
 //   write own w rows (t) -> arrive+wait [A_t] -> copy peer halo rows ->
@@ -261,6 +265,7 @@ __device__ __forceinline__ void fused_tile(const Shape& s, const FusedArgs& a, c
   const int ccols = 16 * s.MXf;
 
   const int t0 = a.t0, t1 = a.t1;  // exposures of this launch, ascending
+  const bool xchg = (mode == 0 || mode == 3);  // forward, weights, halo swap, adjoint
   for (int t = t0; t < t1; ++t) {
     const long long tplane = (long long)t * g.plane;
     if (mode != 1) {
@@ -293,19 +298,31 @@ __device__ __forceinline__ void fused_tile(const Shape& s, const FusedArgs& a, c
         __syncthreads();
         if (has_f && !timed_out) corr_tile<4, 16>(acc, xs, 4 * fmy, 16 * fmx, ksf, KP, Kc);
       }
-      // ---------------- weight by u_t (mode 0) or chi-square (mode 2) ----------
-      if (mode == 0 && t > t0) cluster_wait();  // [B_{t-1}]: peer done reading our w
+      // ---------------- weights (modes 0, 3) or chi-square (mode 2) -------------
+      if (xchg && t > t0) cluster_wait();  // [B_{t-1}]: peer done reading our w
       if (has_f) {
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           const int rr = q * s.Rh + 4 * fmy + p;  // region row
           const long long grow = tplane + (long long)(i0 + hc + rr) * g.P + j0 + hc;
-          if (mode == 0) {
+          if (xchg) {
             float* wrow = srow(ws, rr - kHalf * q);
+            if (a.nu > 0.f) {
+              const float nu1 = a.nu + 1.f;
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              const int cc = 16 * fmx + c;
-              wrow[cc] = a.u[grow + cc] * acc[p][c];
+              for (int c = 0; c < 16; ++c) {
+                const int cc = 16 * fmx + c;
+                const float uv = a.u[grow + cc], yv = a.y[grow + cc];
+                const float d = yv - acc[p][c];
+                const float us = uv > 0.f ? uv * nu1 / fmaf(uv * d, d, a.nu) : 0.f;
+                wrow[cc] = us * (mode == 3 ? yv : acc[p][c]);
+              }
+            } else {
+#pragma unroll
+              for (int c = 0; c < 16; ++c) {
+                const int cc = 16 * fmx + c;
+                wrow[cc] = a.u[grow + cc] * acc[p][c];
+              }
             }
           } else {
 #pragma unroll
@@ -316,7 +333,10 @@ __device__ __forceinline__ void fused_tile(const Shape& s, const FusedArgs& a, c
               if (rr >= hc && rr < hc + kTile && cc >= hc && cc < hc + kTile && i < g.H &&
                   j < g.W && uv != 0.f) {
                 const double d = (double)a.y[grow + cc] - (double)acc[p][c];
-                chi += (double)uv * d * d;
+                if (a.nu > 0.f)
+                  chi += ((double)a.nu + 1.0) * log1p((double)uv * d * d / (double)a.nu);
+                else
+                  chi += (double)uv * d * d;
               }
             }
           }
@@ -388,7 +408,7 @@ __device__ __forceinline__ void fused_tile(const Shape& s, const FusedArgs& a, c
           if (t + 1 < t1) {
             a.Den[grow + c] = acc2[p][c];
           } else if (i < g.H && j < g.W) {
-            if (mode == 1) {
+            if (mode == 1 || mode == 3) {
               a.Nw[grow + c] = acc2[p][c];
             } else {
               const float d = acc2[p][c];
@@ -408,7 +428,7 @@ __device__ __forceinline__ void fused_tile(const Shape& s, const FusedArgs& a, c
       }
     }
   }
-  if (mode == 0) cluster_wait();  // [B_{n-1}]
+  if (xchg) cluster_wait();  // [B_{n-1}]
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
@@ -583,7 +603,7 @@ __global__ void __launch_bounds__(256) setup_kernel(const Shape s, const SetupAr
   __shared__ double red[8];
   const Geom& g = s.g;
   const long long hw = (long long)g.H * g.W, total = hw * s.n;
-  double ld = 0.0, suy = 0.0, su = 0.0;
+  double ld = 0.0, suy = 0.0, su = 0.0, cnt = 0.0;
   int bad = 0;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -603,6 +623,7 @@ __global__ void __launch_bounds__(256) setup_kernel(const Shape s, const SetupAr
         ld += log(6.283185307179586 * (double)v);
         suy += (double)uo * (double)yv;
         su += (double)uo;
+        cnt += 1.0;
       }
     }
     a.u[off] = uo;
@@ -612,10 +633,12 @@ __global__ void __launch_bounds__(256) setup_kernel(const Shape s, const SetupAr
   const double s0 = block_sum_f64(ld, red);
   const double s1 = block_sum_f64(suy, red);
   const double s2 = block_sum_f64(su, red);
+  const double s3 = block_sum_f64(cnt, red);
   if (threadIdx.x == 0) {
-    a.part[3 * blockIdx.x + 0] = s0;
-    a.part[3 * blockIdx.x + 1] = s1;
-    a.part[3 * blockIdx.x + 2] = s2;
+    a.part[4 * blockIdx.x + 0] = s0;
+    a.part[4 * blockIdx.x + 1] = s1;
+    a.part[4 * blockIdx.x + 2] = s2;
+    a.part[4 * blockIdx.x + 3] = s3;
   }
 }
 

@@ -71,13 +71,14 @@ struct FusedArgs {
   float* Den;         // R2 planes (scratch between exposures)
   int* err;
   int t0, t1;         // exposures [t0, t1) of this launch (all: 0, n)
+  float nu;           // Student-t degrees of freedom; 0 = Gaussian noise
 };
 
 struct SetupArgs {
   const uint8_t* mask;  // n x H x W uint8 (natural layout, device), or null
   float* u;             // in: v (copied into the u planes); out: u
   float* y;             // in/out: y; masked pixels become 0
-  double* part;         // kRedBlocks x 3 partial sums
+  double* part;         // kRedBlocks x 4 partial sums
   int* err;
 };
 

@@ -30,6 +30,8 @@ EMD_PREC_BF16 = 1
 EMD_PREC_FP16 = 2
 EMD_PREC_SPLIT_BF16 = 3
 EMD_PREC_SPLIT_FP16 = 4
+EMD_NOISE_GAUSSIAN = 0
+EMD_NOISE_STUDENT_T = 1
 
 EXPORTS = [
     "emd_create", "emd_ctx_bytes", "emd_destroy", "emd_last_error", "emd_set_stream",
@@ -37,7 +39,7 @@ EXPORTS = [
     "emd_set_precision", "emd_get_numerator", "emd_get_weights", "emd_frame_stats_noalloc",
     "emd_batch_create", "emd_batch_destroy", "emd_batch_add", "emd_batch_remove",
     "emd_batch_step", "emd_batch_remaining", "emd_batch_sync", "emd_batch_config",
-    "emd_selftest_wait_timeout", "emd_iterate_streaming", "emd_fit_psf",
+    "emd_selftest_wait_timeout", "emd_iterate_streaming", "emd_fit_psf", "emd_set_noise",
 ]
 
 
@@ -106,6 +108,8 @@ def load(build_if_missing: bool = False):
         lib.emd_batch_config.argtypes = [vp, ip, ip, ip]
         lib.emd_fit_psf.argtypes = [vp, i, i, i, vp, i, vp, C.c_float, C.c_float, i, vp, vp]
         lib.emd_fit_psf.restype = i
+        lib.emd_set_noise.argtypes = [vp, i, C.c_double]
+        lib.emd_set_noise.restype = i
         for name in ("emd_batch_add", "emd_batch_remove", "emd_batch_step",
                      "emd_batch_remaining", "emd_batch_sync", "emd_batch_config"):
             getattr(lib, name).restype = i
@@ -252,6 +256,11 @@ def emd_selftest_wait_timeout(ctx, spins: int = 1000) -> int:
     return int(load().emd_selftest_wait_timeout(ctx, int(spins)))
 
 
+def emd_set_noise(ctx, model: int, nu: float = 0.0) -> None:
+    """EMD_NOISE_GAUSSIAN or EMD_NOISE_STUDENT_T with nu degrees of freedom."""
+    _check(load().emd_set_noise(ctx, int(model), float(nu)))
+
+
 def emd_set_precision(ctx, mode: int) -> None:
     _check(load().emd_set_precision(ctx, int(mode)))
 
@@ -340,6 +349,9 @@ class Deconvolver:
 
     def set_precision(self, mode):
         emd_set_precision(self.ctx, mode)
+
+    def set_noise(self, model, nu=0.0):
+        emd_set_noise(self.ctx, model, nu)
 
     def x(self, out=None):
         if out is None:
