@@ -41,7 +41,8 @@ SM_MAX_MHZ = 2070.0
 # kernels one emd_iterate(ctx, 1) call launches: the fused kernel (FP32); the
 # x split + tensor-core kernel (BF16 modes); the x maximum, the power-of-two
 # scales, the split and the tensor-core kernel (FP16 modes)
-LAUNCHES_PER_STEP = {"fp32": 1, "bf16": 2, "split_bf16": 2, "fp16": 4, "split_fp16": 4}
+LAUNCHES_PER_STEP = {"fp32": 1, "bf16": 2, "split_bf16": 2, "fp16": 4, "split_fp16": 4,
+                     "fft": 2}
 KERNEL_SOURCES = ["paper_2302_05804_gb300/csrc/emd_direct.cu",
                   "paper_2302_05804_gb300/csrc/emd_internal.cuh"]
 
@@ -344,7 +345,8 @@ def run_ours(args):
     over = {"H": args.size, "W": args.size} if args.size else {}
     p = synth.make_problem(args.workload, **over)
     Hf, Wf = p.r * p.H, p.r * p.W
-    prec = {"fp32": 0, "bf16": 1, "fp16": 2, "split_bf16": 3, "split_fp16": 4}[args.precision]
+    prec = {"fp32": 0, "bf16": 1, "fp16": 2, "split_bf16": 3, "split_fp16": 4,
+            "fft": 5}[args.precision]
 
     stream = torch.cuda.Stream()
     d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r, stream=stream)
@@ -385,7 +387,23 @@ def run_ours(args):
     flops = algorithmic_flops(p.H, p.W, p.n, p.K, p.r) * (2 if args.nu > 0 else 1)
     launch_s = statistics.mean(per) / 1e3
     achieved = flops / launch_s / 1e12
-    if prec == 0:
+    if prec == 5:
+        # FFT form: flops of the transforms it runs (a real 128^2 transform
+        # = 2.5 N log2 N, N = 128^2) and of the spectrum products, against
+        # the FP32 peak; the direct-form flops it replaces are reported beside
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        B = 128 - (p.K - 1)
+        tiles = -(-p.H // B) * -(-p.W // B)
+        ffts = tiles * (2 * p.n + 2)
+        fl = ffts * 2.5 * 16384 * 14 + tiles * 2 * p.n * 6 * 128 * 65
+        ex = fl / launch_s / 1e12
+        roofline = {"bound": "alu", "achieved": ex, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ex / peak, "traffic": None,
+                    "kernel": "fft_forward_kernel + fft_adjoint_kernel (FP32 FFT)",
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                    "direct_equivalent_tflops": achieved,
+                    "fft_tflop_per_iteration": fl / 1e12}
+    elif prec == 0:
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
         traffic = committed_traffic(args.workload)
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -467,7 +485,7 @@ def run_ours(args):
             "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16": "bf16", "split_bf16": "bf16x3",
-                      "fp16": "f16", "split_fp16": "f16x3"}[args.precision],
+                      "fp16": "f16", "split_fp16": "f16x3", "fft": "f32"}[args.precision],
             "data": "synthetic",
             "config": config_of(args), "roofline": roofline, "cpu_baseline": cpu,
             "e2e": e2e,
@@ -491,7 +509,7 @@ def main():
     ap.add_argument("--size", type=int, default=0,
                     help="override the exposure side (profiling of small cases)")
     ap.add_argument("--precision", default="fp32",
-                    choices=["fp32", "bf16", "fp16", "split_bf16", "split_fp16"])
+                    choices=["fp32", "bf16", "fp16", "split_bf16", "split_fp16", "fft"])
     ap.add_argument("--e2e-iters", type=int, default=10)
     ap.add_argument("--e2e-jobs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -62,7 +62,8 @@ enum emd_precision {
     EMD_PREC_BF16 = 1,        /* tensor cores, BF16 operands, FP32 accumulate */
     EMD_PREC_FP16 = 2,        /* tensor cores, FP16 operands, FP32 accumulate */
     EMD_PREC_SPLIT_BF16 = 3,  /* tensor cores, hi+lo BF16 split, 3 products   */
-    EMD_PREC_SPLIT_FP16 = 4   /* tensor cores, hi+lo FP16 split, 3 products   */
+    EMD_PREC_SPLIT_FP16 = 4,  /* tensor cores, hi+lo FP16 split, 3 products   */
+    EMD_PREC_FFT_FP32 = 5     /* FP32 FFTs, overlap-save on 128 x 128 tiles   */
 };
 
 /* Largest PSF footprint the direct kernels accept: with
@@ -141,7 +142,14 @@ int emd_get_x(emd_ctx *ctx, float *out);
 int emd_loglik(emd_ctx *ctx, double *out, double *chi2);
 
 /* Select the convolution arithmetic (enum emd_precision). Modes not built
- * into this library return EMD_EUNSUPPORTED and leave the mode unchanged. */
+ * into this library return EMD_EUNSUPPORTED and leave the mode unchanged.
+ * EMD_PREC_FFT_FP32 computes the forward model and the adjoint of each
+ * iteration by FP32 FFTs (overlap-save: output tiles of 128 - 2h pixels,
+ * h = (K-1)/2, transformed as 128 x 128 real tiles); it needs r = 1
+ * (EMD_EUNSUPPORTED otherwise) and n extra exposure planes of device memory
+ * for the weighted model images u_t z_t, allocated on first selection.
+ * emd_loglik and emd_iterate_streaming use the direct FP32 kernel in every
+ * mode. */
 int emd_set_precision(emd_ctx *ctx, int mode);
 
 /*

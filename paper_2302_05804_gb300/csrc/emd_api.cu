@@ -93,6 +93,11 @@ struct emd_ctx {
   int noise = EMD_NOISE_GAUSSIAN;
   double nu = 0.0;
   float* Ns = nullptr;  // heavy-tailed numerator (latent planes), allocated on first use
+  // FFT path (allocated when EMD_PREC_FFT_FP32 is first selected)
+  char* fft_arena = nullptr;
+  float2* fft_spec = nullptr;
+  float* fft_w = nullptr;
+  bool fft_ready = false;
   bool frames = false;
   int prec = EMD_PREC_FP32;
   // tensor-core path (allocated when a tensor-core mode is first selected)
@@ -289,6 +294,7 @@ void emd_destroy(emd_ctx* c) {
   if (c->tc_arena) cudaFree(c->tc_arena);
   if (c->Nt) cudaFree(c->Nt);
   if (c->Ns) cudaFree(c->Ns);
+  if (c->fft_arena) cudaFree(c->fft_arena);
   delete c;
 }
 
@@ -312,7 +318,7 @@ int emd_set_precision(emd_ctx* c, int mode) {
     c->prec = mode;
     return EMD_OK;
   }
-  if (mode < 0 || mode > EMD_PREC_SPLIT_FP16) {
+  if (mode < 0 || mode > EMD_PREC_FFT_FP32) {
     set_err("unknown precision mode %d", mode);
     return EMD_EINVAL;
   }
@@ -321,6 +327,29 @@ int emd_set_precision(emd_ctx* c, int mode) {
     return EMD_EUNSUPPORTED;
   }
   DeviceGuard dg(c->device);
+  if (mode == EMD_PREC_FFT_FP32) {
+    if (c->s.r != 1) {
+      set_err("emd_set_precision: the FFT path supports r = 1 only");
+      return EMD_EUNSUPPORTED;
+    }
+    if (!c->fft_arena) {
+      const size_t need = emd::fft_buffer_bytes(c->s);
+      void* p = nullptr;
+      if (cudaMalloc(&p, need) != cudaSuccess) {
+        cudaGetLastError();
+        set_err("emd_set_precision: cudaMalloc(%zu) for the FFT path failed", need);
+        return EMD_ENOMEM;
+      }
+      CK(cudaMemsetAsync(p, 0, need, c->st));
+      c->fft_arena = static_cast<char*>(p);
+      const size_t spec = ((size_t)c->s.n * 128 * 65 * sizeof(float2) + 255) & ~(size_t)255;
+      c->fft_spec = reinterpret_cast<float2*>(c->fft_arena);
+      c->fft_w = reinterpret_cast<float*>(c->fft_arena + spec);
+      c->fft_ready = false;
+    }
+    c->prec = mode;
+    return EMD_OK;
+  }
   emd::TcShape t;
   const char* why = nullptr;
   if (!emd::make_tc_shape(c->s, mode, &t, &why)) {
@@ -371,6 +400,7 @@ int emd_set_frames(emd_ctx* c, const float* y, const float* v, const float* f,
   const Shape& s = c->s;
   c->frames = false;
   c->hank_ready = false;
+  c->fft_ready = false;
   c->nt_ready = false;
   const size_t npix = (size_t)s.n * s.H * s.W;
   if (int rc = put_planes(c, c->y, y, s.n)) return rc;
@@ -448,6 +478,24 @@ int emd_iterate(emd_ctx* c, int k) {
     return EMD_EINVAL;
   }
   DeviceGuard dg(c->device);
+  if (c->prec == EMD_PREC_FFT_FP32 && k > 0) {
+    if (!c->fft_ready) {
+      CK(emd::launch_fft_spectra(c->s, c->fraw, c->fft_spec, c->st));
+      c->fft_ready = true;
+    }
+    for (int it = 0; it < k; ++it) {
+      emd::FftLaunch L{};
+      L.x = c->x[c->cur];
+      L.xn = c->x[c->cur ^ 1];
+      L.N = c->N;
+      L.u = c->u;
+      L.w = c->fft_w;
+      L.spec = c->fft_spec;
+      CK(emd::launch_fft_iter(c->s, L, c->st));
+      c->cur ^= 1;
+    }
+    return EMD_OK;
+  }
   if (c->prec != EMD_PREC_FP32 && k > 0) {
     // tensor-core path: 16-bit operands of the PSFs (once per frame set) and
     // of the current x, then one kernel launch per iteration

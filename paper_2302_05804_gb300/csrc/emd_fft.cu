@@ -1,0 +1,356 @@
+// emd_fft.cu -- the forward model and the adjoint of Eq. (2) by FFT
+// (overlap-save on 128 x 128 tiles), an alternative to the direct FP32
+// kernel for r = 1. Same arithmetic type (FP32), different rounding.
+//
+// For an output tile with origin (i0, j0) and side B = 128 - 2 hc (hc =
+// (K-1)/2), the input region is rows/cols [i0 - hc, i0 - hc + 128) of the
+// image, zero outside it. With k the K x K PSF at the top-left of a zero
+// 128 x 128 array, the circular convolution of the region with k holds
+// z(i0 + p, j0 + q) at circular index (p + 2hc, q + 2hc), and the circular
+// correlation of the w region with k holds Den(i0 + p, j0 + q) at (p, q),
+// for p, q < B: no wrapped term reaches those indices. In Fourier space the
+// convolution multiplies by k^ and the correlation by conj(k^) (k is real).
+//
+// 2D real transforms in shared memory, radix-2, in place:
+//   forward (R2C): two real rows packed as one complex row; 64 row FFTs by
+//     decimation in frequency (natural in, bit-reversed out); the packed
+//     spectra split into the half spectra (65 bins) of the two rows; 65
+//     column FFTs, again by decimation in frequency. Result: row frequency
+//     bit-reversed, column frequency 0..64 natural. The PSF spectra are made
+//     by the same code, so products never need a reordering.
+//   inverse (C2R): 65 column FFTs by decimation in time with conjugate
+//     twiddles (bit-reversed in, natural out); the half spectra of row pairs
+//     merged into one packed full spectrum (Hermitian symmetry), written in
+//     bit-reversed order; 64 row FFTs by decimation in time; real part = even
+//     row, imaginary part = odd row; scaled by 1/128^2 (exact).
+// A half-spectrum buffer is 128 rows x kFP complex; the packed row pair k
+// occupies the 2 kFP slots from 2k kFP, so splitting and merging stay in
+// place (each pair is one warp's, with a warp barrier between its reads and
+// its writes).
+//
+// Per iteration: fft_forward_kernel (per tile: x^ once, then for each
+// exposure z = IFFT(x^ k_t^), w_t = u_t z written to a plane) and
+// fft_adjoint_kernel (per tile: sum_t FFT(w_t) conj(k_t^), one inverse
+// transform, the update of Eq. (2)).
+#include <math.h>
+
+#include "emd_internal.cuh"
+
+namespace emd {
+namespace {
+
+constexpr int kFT = 128;                 // tile side
+constexpr int kFP = 66;                  // half-spectrum row pitch (complex)
+constexpr int kFBins = 65;               // half-spectrum columns
+constexpr int kFBuf = kFT * kFP;         // float2 per transform buffer
+constexpr int kFThreads = 512;
+constexpr float kFScale = 1.0f / (kFT * kFT);
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ int rev7(int m) { return (int)(__brev((unsigned)m) >> 25); }
+
+// tw[k] = exp(-2 pi i k / 128), k < 64
+__device__ __forceinline__ void init_twiddles(float2* tw) {
+  for (int k = threadIdx.x; k < 64; k += blockDim.x) {
+    float sn, cs;
+    sincospif((float)k / 64.f, &sn, &cs);
+    tw[k] = make_float2(cs, -sn);
+  }
+}
+
+// 64 packed rows (at 2k kFP, contiguous): decimation in frequency
+__device__ void rows_dif(float2* buf, const float2* tw) {
+  for (int st = 0; st < 7; ++st) {
+    const int ls = 6 - st, s = 1 << ls;
+    for (int b = threadIdx.x; b < 64 * 64; b += blockDim.x) {
+      const int k = b >> 6, j = b & 63, jm = j & (s - 1);
+      const int i = ((j >> ls) << (ls + 1)) + jm;
+      float2* r = buf + 2 * k * kFP;
+      const float2 a = r[i], c = r[i + s];
+      r[i] = cadd(a, c);
+      r[i + s] = cmul(csub(a, c), tw[jm << st]);
+    }
+    __syncthreads();
+  }
+}
+
+// 64 packed rows: decimation in time (bit-reversed in), conjugate twiddles
+__device__ void rows_dit_inv(float2* buf, const float2* tw) {
+  for (int st = 0; st < 7; ++st) {
+    const int s = 1 << st;
+    for (int b = threadIdx.x; b < 64 * 64; b += blockDim.x) {
+      const int k = b >> 6, j = b & 63, jm = j & (s - 1);
+      const int i = ((j >> st) << (st + 1)) + jm;
+      float2* r = buf + 2 * k * kFP;
+      const float2 a = r[i], c = cmul(r[i + s], conjf2(tw[jm << (6 - st)]));
+      r[i] = cadd(a, c);
+      r[i + s] = csub(a, c);
+    }
+    __syncthreads();
+  }
+}
+
+// 65 columns (stride kFP): decimation in frequency
+__device__ void cols_dif(float2* buf, const float2* tw) {
+  for (int st = 0; st < 7; ++st) {
+    const int ls = 6 - st, s = 1 << ls;
+    for (int b = threadIdx.x; b < kFBins * 64; b += blockDim.x) {
+      const int j = b / kFBins, m = b - j * kFBins, jm = j & (s - 1);
+      const int i = ((j >> ls) << (ls + 1)) + jm;
+      float2* p = buf + m;
+      const float2 a = p[i * kFP], c = p[(i + s) * kFP];
+      p[i * kFP] = cadd(a, c);
+      p[(i + s) * kFP] = cmul(csub(a, c), tw[jm << st]);
+    }
+    __syncthreads();
+  }
+}
+
+// 65 columns: decimation in time, conjugate twiddles
+__device__ void cols_dit_inv(float2* buf, const float2* tw) {
+  for (int st = 0; st < 7; ++st) {
+    const int s = 1 << st;
+    for (int b = threadIdx.x; b < kFBins * 64; b += blockDim.x) {
+      const int j = b / kFBins, m = b - j * kFBins, jm = j & (s - 1);
+      const int i = ((j >> st) << (st + 1)) + jm;
+      float2* p = buf + m;
+      const float2 a = p[i * kFP], c = cmul(p[(i + s) * kFP], conjf2(tw[jm << (6 - st)]));
+      p[i * kFP] = cadd(a, c);
+      p[(i + s) * kFP] = csub(a, c);
+    }
+    __syncthreads();
+  }
+}
+
+// packed row spectra (bit-reversed) -> half spectra of the even and odd rows
+__device__ void split_rows(float2* buf) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = warp; k < 64; k += nw) {
+    float2* r = buf + 2 * k * kFP;
+    float2 e[3], o[3];
+    int ms[3] = {lane, lane + 32, 64};
+    const int cnt = lane == 0 ? 3 : 2;
+    for (int q = 0; q < cnt; ++q) {
+      const int m = ms[q];
+      const float2 cm = r[rev7(m)], cn = conjf2(r[rev7((128 - m) & 127)]);
+      e[q] = make_float2(0.5f * (cm.x + cn.x), 0.5f * (cm.y + cn.y));
+      const float2 d = csub(cm, cn);  // (cm - conj(c_-m)) / (2i) = -i d / 2
+      o[q] = make_float2(0.5f * d.y, -0.5f * d.x);
+    }
+    __syncwarp();
+    for (int q = 0; q < cnt; ++q) {
+      r[ms[q]] = e[q];
+      r[kFP + ms[q]] = o[q];
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+}
+
+// half spectra of row pairs -> packed full spectra in bit-reversed order
+__device__ void merge_rows(float2* buf) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = warp; k < 64; k += nw) {
+    float2* r = buf + 2 * k * kFP;
+    float2 d[4];
+    for (int q = 0; q < 4; ++q) {
+      const int m = lane + 32 * q;
+      if (m <= 64) {
+        const float2 e = r[m], o = r[kFP + m];
+        d[q] = make_float2(e.x - o.y, e.y + o.x);  // e + i o
+      } else {
+        const float2 e = conjf2(r[128 - m]), o = conjf2(r[kFP + 128 - m]);
+        d[q] = make_float2(e.x - o.y, e.y + o.x);
+      }
+    }
+    __syncwarp();
+    for (int q = 0; q < 4; ++q) r[rev7(lane + 32 * q)] = d[q];
+    __syncwarp();
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void r2c_2d(float2* buf, const float2* tw) {
+  rows_dif(buf, tw);
+  split_rows(buf);
+  cols_dif(buf, tw);
+}
+
+__device__ __forceinline__ void c2r_2d(float2* buf, const float2* tw) {
+  cols_dit_inv(buf, tw);
+  merge_rows(buf);
+  rows_dit_inv(buf, tw);
+}
+
+// value of tile pixel (P, Q) after c2r_2d (unscaled)
+__device__ __forceinline__ float tile_at(const float2* buf, int P, int Q) {
+  const float2 v = buf[(P >> 1) * 2 * kFP + Q];
+  return (P & 1) ? v.y : v.x;
+}
+
+// the 128 x 128 region with origin (r0, c0) of a padded plane, zero outside
+// the H x W image, packed into buf
+__device__ void load_region(float2* buf, const float* plane, const Geom& g, int r0, int c0) {
+  for (int e = threadIdx.x; e < 64 * kFT; e += blockDim.x) {
+    const int k = e >> 7, j = e & (kFT - 1);
+    const int i = r0 + 2 * k, jj = c0 + j;
+    float a = 0.f, b = 0.f;
+    if (jj >= 0 && jj < g.W) {
+      if (i >= 0 && i < g.H) a = plane[(long long)(g.B + i) * g.P + g.B + jj];
+      if (i + 1 >= 0 && i + 1 < g.H) b = plane[(long long)(g.B + i + 1) * g.P + g.B + jj];
+    }
+    buf[2 * k * kFP + j] = make_float2(a, b);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kFThreads, 1)
+    fft_spectra_kernel(const float* __restrict__ f, int K, float2* __restrict__ spec) {
+  extern __shared__ float2 fsm[];
+  __shared__ float2 tw[64];
+  float2* buf = fsm;
+  init_twiddles(tw);
+  const float* ft = f + (long long)blockIdx.x * K * K;
+  for (int e = threadIdx.x; e < 64 * kFT; e += blockDim.x) {
+    const int k = e >> 7, j = e & (kFT - 1);
+    const int i = 2 * k;
+    const float a = (i < K && j < K) ? ft[i * K + j] : 0.f;
+    const float b = (i + 1 < K && j < K) ? ft[(i + 1) * K + j] : 0.f;
+    buf[2 * k * kFP + j] = make_float2(a, b);
+  }
+  __syncthreads();
+  r2c_2d(buf, tw);
+  float2* out = spec + (long long)blockIdx.x * kFT * kFBins;
+  for (int e = threadIdx.x; e < kFT * kFBins; e += blockDim.x) {
+    const int rr = e / kFBins, m = e - rr * kFBins;
+    out[e] = buf[rr * kFP + m];
+  }
+}
+
+__global__ void __launch_bounds__(kFThreads, 1)
+    fft_forward_kernel(const Shape s, const FftLaunch a) {
+  extern __shared__ float2 fsm[];
+  __shared__ float2 tw[64];
+  float2* xh = fsm;
+  float2* wk = fsm + kFBuf;
+  const Geom& g = s.g;
+  const int hc = s.hc, B = kFT - 2 * hc;
+  const int i0 = blockIdx.y * B, j0 = blockIdx.x * B;
+  init_twiddles(tw);
+  load_region(xh, a.x, g, i0 - hc, j0 - hc);
+  r2c_2d(xh, tw);
+  for (int t = 0; t < s.n; ++t) {
+    const float2* kt = a.spec + (long long)t * kFT * kFBins;
+    for (int e = threadIdx.x; e < kFT * kFBins; e += blockDim.x) {
+      const int rr = e / kFBins, m = e - rr * kFBins;
+      wk[rr * kFP + m] = cmul(xh[rr * kFP + m], kt[e]);
+    }
+    __syncthreads();
+    c2r_2d(wk, tw);
+    const long long tplane = (long long)t * g.plane;
+    for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+      const int p = e / B, q = e - p * B;
+      const int i = i0 + p, j = j0 + q;
+      if (i < g.H && j < g.W) {
+        const long long gi = tplane + (long long)(g.B + i) * g.P + g.B + j;
+        a.w[gi] = a.u[gi] * (tile_at(wk, p + 2 * hc, q + 2 * hc) * kFScale);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kFThreads, 1)
+    fft_adjoint_kernel(const Shape s, const FftLaunch a) {
+  extern __shared__ float2 fsm[];
+  __shared__ float2 tw[64];
+  float2* sh = fsm;
+  float2* wk = fsm + kFBuf;
+  const Geom& g = s.g;
+  const int hc = s.hc, B = kFT - 2 * hc;
+  const int i0 = blockIdx.y * B, j0 = blockIdx.x * B;
+  init_twiddles(tw);
+  for (int e = threadIdx.x; e < kFBuf; e += blockDim.x) sh[e] = make_float2(0.f, 0.f);
+  for (int t = 0; t < s.n; ++t) {
+    load_region(wk, a.w + (long long)t * g.plane, g, i0 - hc, j0 - hc);
+    r2c_2d(wk, tw);
+    const float2* kt = a.spec + (long long)t * kFT * kFBins;
+    for (int e = threadIdx.x; e < kFT * kFBins; e += blockDim.x) {
+      const int rr = e / kFBins, m = e - rr * kFBins;
+      const int o = rr * kFP + m;
+      sh[o] = cadd(sh[o], cmulc(wk[o], kt[e]));
+    }
+    __syncthreads();
+  }
+  c2r_2d(sh, tw);
+  for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+    const int p = e / B, q = e - p * B;
+    const int i = i0 + p, j = j0 + q;
+    if (i < g.H && j < g.W) {
+      const long long gi = (long long)(g.B + i) * g.P + g.B + j;
+      const float d = tile_at(sh, p, q) * kFScale;
+      const float xo = a.x[gi], nraw = a.N[gi];
+      float xv = xo;
+      // The transform leaves a rounding floor (~1e-7 of the tile's weighted
+      // model) where the exact denominator is 0; N, from the direct kernel,
+      // is exactly 0 when no valid pixel lies in the footprint, which is
+      // then the sign of a zero denominator (x unchanged, as for Den = 0).
+      if (d > 0.f && nraw != 0.f) {
+        const float nv = fmaxf(nraw, 0.f);
+        if (d < 1e-30f)  // denominator near zero: guarded ratio in FP64
+          xv = (float)((double)xo * (double)nv / (double)d);
+        else
+          xv = xo * nv / d;
+      }
+      a.xn[gi] = xv;
+    }
+  }
+}
+
+}  // namespace
+
+size_t fft_buffer_bytes(const Shape& s) {
+  const size_t spec = (size_t)s.n * kFT * kFBins * sizeof(float2);
+  const size_t wpl = (size_t)s.n * s.g.plane * sizeof(float);
+  return ((spec + 255) & ~(size_t)255) + wpl;
+}
+
+size_t fft_smem_bytes() { return 2 * (size_t)kFBuf * sizeof(float2); }
+
+int fft_tile_side(const Shape& s) { return kFT - 2 * s.hc; }
+
+cudaError_t launch_fft_spectra(const Shape& s, const float* f, float2* spec, cudaStream_t st) {
+  const size_t smem = (size_t)kFBuf * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(fft_spectra_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fft_spectra_kernel<<<s.n, kFThreads, smem, st>>>(f, s.K, spec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_iter(const Shape& s, const FftLaunch& a, cudaStream_t st) {
+  const size_t smem = fft_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(fft_forward_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fft_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+  if (e != cudaSuccess) return e;
+  const int B = fft_tile_side(s);
+  const dim3 grid((s.g.W + B - 1) / B, (s.g.H + B - 1) / B);
+  fft_forward_kernel<<<grid, kFThreads, smem, st>>>(s, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  fft_adjoint_kernel<<<grid, kFThreads, smem, st>>>(s, a);
+  return cudaGetLastError();
+}
+
+}  // namespace emd

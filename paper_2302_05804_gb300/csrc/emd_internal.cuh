@@ -120,6 +120,21 @@ cudaError_t launch_gather_latent(const Shape& s, const float* planes, float* nat
                                  cudaStream_t st);
 
 // ---- tensor-core path (emd_tc.cu) ----
+// FFT path (r = 1): overlap-save on 128 x 128 tiles
+struct FftLaunch {
+  const float* x;       // current iterate (padded plane)
+  float* xn;            // next iterate
+  const float* N;       // numerator
+  const float* u;       // n weight planes
+  float* w;             // n planes of u_t z_t (written by the forward pass)
+  const float2* spec;   // n half spectra of the PSFs, 128 x 65 each
+};
+size_t fft_buffer_bytes(const Shape& s);
+size_t fft_smem_bytes();
+int fft_tile_side(const Shape& s);
+cudaError_t launch_fft_spectra(const Shape& s, const float* f, float2* spec, cudaStream_t st);
+cudaError_t launch_fft_iter(const Shape& s, const FftLaunch& a, cudaStream_t st);
+
 struct TcShape {
   int mode, fp16, nprod;
   int TC;           // Den columns per CTA (64); Den rows per CTA = 128 (MMA M)

@@ -30,6 +30,7 @@ EMD_PREC_BF16 = 1
 EMD_PREC_FP16 = 2
 EMD_PREC_SPLIT_BF16 = 3
 EMD_PREC_SPLIT_FP16 = 4
+EMD_PREC_FFT_FP32 = 5
 EMD_NOISE_GAUSSIAN = 0
 EMD_NOISE_STUDENT_T = 1
 
