@@ -11,7 +11,9 @@
 // for p, q < B: no wrapped term reaches those indices. In Fourier space the
 // convolution multiplies by k^ and the correlation by conj(k^) (k is real).
 //
-// 2D real transforms in shared memory, radix-2, in place:
+// 2D real transforms in shared memory, in place, each 128-point FFT done by
+// one warp in registers (radix-2 butterflies; four values per lane, shuffles
+// across lanes):
 //   forward (R2C): two real rows packed as one complex row; 64 row FFTs by
 //     decimation in frequency (natural in, bit-reversed out); the packed
 //     spectra split into the half spectra (65 bins) of the two rows; 65
@@ -40,7 +42,8 @@ namespace emd {
 namespace {
 
 constexpr int kFT = 128;                 // tile side
-constexpr int kFP = 66;                  // half-spectrum row pitch (complex)
+constexpr int kFP = 67;                  // half-spectrum row pitch (complex, odd:
+                                         // a warp's column loads hit distinct banks)
 constexpr int kFBins = 65;               // half-spectrum columns
 constexpr int kFBuf = kFT * kFP;         // float2 per transform buffer
 constexpr int kFThreads = 512;
@@ -66,128 +69,163 @@ __device__ __forceinline__ void init_twiddles(float2* tw) {
   }
 }
 
-// 64 packed rows (at 2k kFP, contiguous): decimation in frequency
-__device__ void rows_dif(float2* buf, const float2* tw) {
-  for (int st = 0; st < 7; ++st) {
-    const int ls = 6 - st, s = 1 << ls;
-    for (int b = threadIdx.x; b < 64 * 64; b += blockDim.x) {
-      const int k = b >> 6, j = b & 63, jm = j & (s - 1);
-      const int i = ((j >> ls) << (ls + 1)) + jm;
-      float2* r = buf + 2 * k * kFP;
-      const float2 a = r[i], c = r[i + s];
-      r[i] = cadd(a, c);
-      r[i + s] = cmul(csub(a, c), tw[jm << st]);
-    }
-    __syncthreads();
+// One 128-point FFT per warp, in registers: lane l holds v[q] = x[32 q + l].
+// Decimation in frequency (natural in, bit-reversed out): the spans 64 and
+// 32 pair the four values a lane holds; spans 16 .. 1 pair lanes l and
+// l ^ s through shuffles.
+__device__ __forceinline__ void warp_fft_dif(float2 (&v)[4], const float2* tw, int lane) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const float2 a = v[q], b = v[q + 2];
+    v[q] = cadd(a, b);
+    v[q + 2] = cmul(csub(a, b), tw[32 * q + lane]);
   }
-}
-
-// 64 packed rows: decimation in time (bit-reversed in), conjugate twiddles
-__device__ void rows_dit_inv(float2* buf, const float2* tw) {
-  for (int st = 0; st < 7; ++st) {
-    const int s = 1 << st;
-    for (int b = threadIdx.x; b < 64 * 64; b += blockDim.x) {
-      const int k = b >> 6, j = b & 63, jm = j & (s - 1);
-      const int i = ((j >> st) << (st + 1)) + jm;
-      float2* r = buf + 2 * k * kFP;
-      const float2 a = r[i], c = cmul(r[i + s], conjf2(tw[jm << (6 - st)]));
-      r[i] = cadd(a, c);
-      r[i + s] = csub(a, c);
-    }
-    __syncthreads();
+  const float2 t1 = tw[2 * lane];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const float2 a = v[2 * p], b = v[2 * p + 1];
+    v[2 * p] = cadd(a, b);
+    v[2 * p + 1] = cmul(csub(a, b), t1);
   }
-}
-
-// 65 columns (stride kFP): decimation in frequency
-__device__ void cols_dif(float2* buf, const float2* tw) {
-  for (int st = 0; st < 7; ++st) {
-    const int ls = 6 - st, s = 1 << ls;
-    for (int b = threadIdx.x; b < kFBins * 64; b += blockDim.x) {
-      const int j = b / kFBins, m = b - j * kFBins, jm = j & (s - 1);
-      const int i = ((j >> ls) << (ls + 1)) + jm;
-      float2* p = buf + m;
-      const float2 a = p[i * kFP], c = p[(i + s) * kFP];
-      p[i * kFP] = cadd(a, c);
-      p[(i + s) * kFP] = cmul(csub(a, c), tw[jm << st]);
-    }
-    __syncthreads();
-  }
-}
-
-// 65 columns: decimation in time, conjugate twiddles
-__device__ void cols_dit_inv(float2* buf, const float2* tw) {
-  for (int st = 0; st < 7; ++st) {
-    const int s = 1 << st;
-    for (int b = threadIdx.x; b < kFBins * 64; b += blockDim.x) {
-      const int j = b / kFBins, m = b - j * kFBins, jm = j & (s - 1);
-      const int i = ((j >> st) << (st + 1)) + jm;
-      float2* p = buf + m;
-      const float2 a = p[i * kFP], c = cmul(p[(i + s) * kFP], conjf2(tw[jm << (6 - st)]));
-      p[i * kFP] = cadd(a, c);
-      p[(i + s) * kFP] = csub(a, c);
-    }
-    __syncthreads();
-  }
-}
-
-// packed row spectra (bit-reversed) -> half spectra of the even and odd rows
-__device__ void split_rows(float2* buf) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int k = warp; k < 64; k += nw) {
-    float2* r = buf + 2 * k * kFP;
-    float2 e[3], o[3];
-    int ms[3] = {lane, lane + 32, 64};
-    const int cnt = lane == 0 ? 3 : 2;
-    for (int q = 0; q < cnt; ++q) {
-      const int m = ms[q];
-      const float2 cm = r[rev7(m)], cn = conjf2(r[rev7((128 - m) & 127)]);
-      e[q] = make_float2(0.5f * (cm.x + cn.x), 0.5f * (cm.y + cn.y));
-      const float2 d = csub(cm, cn);  // (cm - conj(c_-m)) / (2i) = -i d / 2
-      o[q] = make_float2(0.5f * d.y, -0.5f * d.x);
-    }
-    __syncwarp();
-    for (int q = 0; q < cnt; ++q) {
-      r[ms[q]] = e[q];
-      r[kFP + ms[q]] = o[q];
-    }
-    __syncwarp();
-  }
-  __syncthreads();
-}
-
-// half spectra of row pairs -> packed full spectra in bit-reversed order
-__device__ void merge_rows(float2* buf) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int k = warp; k < 64; k += nw) {
-    float2* r = buf + 2 * k * kFP;
-    float2 d[4];
+#pragma unroll
+  for (int st = 2; st < 7; ++st) {
+    const int s = 64 >> st;
+    const bool upper = (lane & s) != 0;
+    const float2 t = tw[(lane & (s - 1)) << st];
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int m = lane + 32 * q;
-      if (m <= 64) {
-        const float2 e = r[m], o = r[kFP + m];
-        d[q] = make_float2(e.x - o.y, e.y + o.x);  // e + i o
-      } else {
-        const float2 e = conjf2(r[128 - m]), o = conjf2(r[kFP + 128 - m]);
-        d[q] = make_float2(e.x - o.y, e.y + o.x);
-      }
+      float2 o;
+      o.x = __shfl_xor_sync(0xffffffffu, v[q].x, s);
+      o.y = __shfl_xor_sync(0xffffffffu, v[q].y, s);
+      v[q] = upper ? cmul(csub(o, v[q]), t) : cadd(v[q], o);
     }
+  }
+}
+
+// Inverse (conjugate twiddles), decimation in time: bit-reversed in,
+// natural out, unscaled.
+__device__ __forceinline__ void warp_ifft_dit(float2 (&v)[4], const float2* tw, int lane) {
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int s = 1 << st;
+    const bool upper = (lane & s) != 0;
+    const float2 t = conjf2(tw[(lane & (s - 1)) << (6 - st)]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 w = upper ? cmul(v[q], t) : v[q];
+      float2 o;
+      o.x = __shfl_xor_sync(0xffffffffu, w.x, s);
+      o.y = __shfl_xor_sync(0xffffffffu, w.y, s);
+      v[q] = upper ? csub(o, w) : cadd(w, o);
+    }
+  }
+  const float2 t1 = conjf2(tw[2 * lane]);
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const float2 a = v[2 * p], b = cmul(v[2 * p + 1], t1);
+    v[2 * p] = cadd(a, b);
+    v[2 * p + 1] = csub(a, b);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const float2 a = v[q], b = cmul(v[q + 2], conjf2(tw[32 * q + lane]));
+    v[q] = cadd(a, b);
+    v[q + 2] = csub(a, b);
+  }
+}
+
+// packed row spectrum of a pair (bit-reversed, at r) -> half spectra of the
+// even row (r[0..64]) and the odd row (r[kFP .. kFP+64]); one warp
+__device__ __forceinline__ void split_pair(float2* r, int lane) {
+  float2 e[3], o[3];
+  const int ms[3] = {lane, lane + 32, 64};
+  const int cnt = lane == 0 ? 3 : 2;
+  for (int q = 0; q < cnt; ++q) {
+    const int m = ms[q];
+    const float2 cm = r[rev7(m)], cn = conjf2(r[rev7((128 - m) & 127)]);
+    e[q] = make_float2(0.5f * (cm.x + cn.x), 0.5f * (cm.y + cn.y));
+    const float2 d = csub(cm, cn);  // (cm - conj(c_-m)) / (2i) = -i d / 2
+    o[q] = make_float2(0.5f * d.y, -0.5f * d.x);
+  }
+  __syncwarp();
+  for (int q = 0; q < cnt; ++q) {
+    r[ms[q]] = e[q];
+    r[kFP + ms[q]] = o[q];
+  }
+  __syncwarp();
+}
+
+// half spectra of a row pair -> packed full spectrum, bit-reversed; one warp
+__device__ __forceinline__ void merge_pair(float2* r, int lane) {
+  float2 d[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int m = lane + 32 * q;
+    float2 e, o;
+    if (m <= 64) {
+      e = r[m];
+      o = r[kFP + m];
+    } else {
+      e = conjf2(r[128 - m]);
+      o = conjf2(r[kFP + 128 - m]);
+    }
+    d[q] = make_float2(e.x - o.y, e.y + o.x);  // e + i o
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) r[rev7(lane + 32 * q)] = d[q];
+  __syncwarp();
+}
+
+// forward real 2D transform in place (see the file comment)
+__device__ void r2c_2d(float2* buf, const float2* tw) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = warp; k < 64; k += nw) {
+    float2* r = buf + 2 * k * kFP;
+    float2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = r[32 * q + lane];
+    warp_fft_dif(v, tw, lane);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) r[32 * q + lane] = v[q];
     __syncwarp();
-    for (int q = 0; q < 4; ++q) r[rev7(lane + 32 * q)] = d[q];
-    __syncwarp();
+    split_pair(r, lane);
+  }
+  __syncthreads();
+  for (int m = warp; m < kFBins; m += nw) {
+    float2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = buf[(32 * q + lane) * kFP + m];
+    warp_fft_dif(v, tw, lane);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) buf[(32 * q + lane) * kFP + m] = v[q];
   }
   __syncthreads();
 }
 
-__device__ __forceinline__ void r2c_2d(float2* buf, const float2* tw) {
-  rows_dif(buf, tw);
-  split_rows(buf);
-  cols_dif(buf, tw);
-}
-
-__device__ __forceinline__ void c2r_2d(float2* buf, const float2* tw) {
-  cols_dit_inv(buf, tw);
-  merge_rows(buf);
-  rows_dit_inv(buf, tw);
+// inverse real 2D transform in place (unscaled)
+__device__ void c2r_2d(float2* buf, const float2* tw) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int m = warp; m < kFBins; m += nw) {
+    float2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = buf[(32 * q + lane) * kFP + m];
+    warp_ifft_dit(v, tw, lane);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) buf[(32 * q + lane) * kFP + m] = v[q];
+  }
+  __syncthreads();
+  for (int k = warp; k < 64; k += nw) {
+    float2* r = buf + 2 * k * kFP;
+    merge_pair(r, lane);
+    float2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = r[32 * q + lane];
+    warp_ifft_dit(v, tw, lane);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) r[32 * q + lane] = v[q];
+  }
+  __syncthreads();
 }
 
 // value of tile pixel (P, Q) after c2r_2d (unscaled)
@@ -196,20 +234,49 @@ __device__ __forceinline__ float tile_at(const float2* buf, int P, int Q) {
   return (P & 1) ? v.y : v.x;
 }
 
-// the 128 x 128 region with origin (r0, c0) of a padded plane, zero outside
-// the H x W image, packed into buf
-__device__ void load_region(float2* buf, const float* plane, const Geom& g, int r0, int c0) {
+// asynchronous 4-byte global -> shared copies (no register staging)
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// start copying the 128 x 128 region with origin (r0, c0) of a padded plane
+// into stg (row-major, zero outside the H x W image)
+__device__ void region_async(float* stg, const float* plane, const Geom& g, int r0, int c0) {
+  for (int e = threadIdx.x; e < kFT * kFT; e += blockDim.x) {
+    const int P = e >> 7, Q = e & (kFT - 1);
+    const int i = r0 + P, j = c0 + Q;
+    if (i >= 0 && i < g.H && j >= 0 && j < g.W)
+      cp_async4(stg + e, plane + (long long)(g.B + i) * g.P + g.B + j);
+    else
+      stg[e] = 0.f;
+  }
+  cp_async_commit();
+}
+
+// wait for the copies, then pack row pairs of stg into buf
+__device__ void pack_region(float2* buf, const float* stg) {
+  cp_async_wait_all();
+  __syncthreads();
   for (int e = threadIdx.x; e < 64 * kFT; e += blockDim.x) {
     const int k = e >> 7, j = e & (kFT - 1);
-    const int i = r0 + 2 * k, jj = c0 + j;
-    float a = 0.f, b = 0.f;
-    if (jj >= 0 && jj < g.W) {
-      if (i >= 0 && i < g.H) a = plane[(long long)(g.B + i) * g.P + g.B + jj];
-      if (i + 1 >= 0 && i + 1 < g.H) b = plane[(long long)(g.B + i + 1) * g.P + g.B + jj];
-    }
-    buf[2 * k * kFP + j] = make_float2(a, b);
+    buf[2 * k * kFP + j] = make_float2(stg[2 * k * kFT + j], stg[(2 * k + 1) * kFT + j]);
   }
   __syncthreads();
+}
+
+// a thread's share of one PSF half spectrum (element e = tid + q kFThreads of
+// the 128 x 65 array), held in registers so that the next exposure's
+// spectrum loads while the current transform runs
+constexpr int kSpecPer = (kFT * kFBins + kFThreads - 1) / kFThreads;  // 17
+__device__ __forceinline__ void load_spec(float2 (&k)[kSpecPer], const float2* kt) {
+#pragma unroll
+  for (int q = 0; q < kSpecPer; ++q) {
+    const int e = threadIdx.x + q * kFThreads;
+    k[q] = e < kFT * kFBins ? kt[e] : make_float2(0.f, 0.f);
+  }
 }
 
 __global__ void __launch_bounds__(kFThreads, 1)
@@ -241,28 +308,45 @@ __global__ void __launch_bounds__(kFThreads, 1)
   __shared__ float2 tw[64];
   float2* xh = fsm;
   float2* wk = fsm + kFBuf;
+  float* stg = reinterpret_cast<float*>(fsm + 2 * kFBuf);  // 128 x 128 floats
   const Geom& g = s.g;
   const int hc = s.hc, B = kFT - 2 * hc;
   const int i0 = blockIdx.y * B, j0 = blockIdx.x * B;
   init_twiddles(tw);
-  load_region(xh, a.x, g, i0 - hc, j0 - hc);
+  float2 kr[kSpecPer];
+  load_spec(kr, a.spec);
+  region_async(stg, a.x, g, i0 - hc, j0 - hc);
+  pack_region(xh, stg);
   r2c_2d(xh, tw);
   for (int t = 0; t < s.n; ++t) {
-    const float2* kt = a.spec + (long long)t * kFT * kFBins;
-    for (int e = threadIdx.x; e < kFT * kFBins; e += blockDim.x) {
-      const int rr = e / kFBins, m = e - rr * kFBins;
-      wk[rr * kFP + m] = cmul(xh[rr * kFP + m], kt[e]);
+#pragma unroll
+    for (int q = 0; q < kSpecPer; ++q) {
+      const int e = threadIdx.x + q * kFThreads;
+      if (e < kFT * kFBins) {
+        const int rr = e / kFBins, m = e - rr * kFBins;
+        wk[rr * kFP + m] = cmul(xh[rr * kFP + m], kr[q]);
+      }
     }
-    __syncthreads();
-    c2r_2d(wk, tw);
+    // u of this exposure (B x B, row-major in stg) arrives during the
+    // inverse transform; the next spectrum too
     const long long tplane = (long long)t * g.plane;
     for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
       const int p = e / B, q = e - p * B;
       const int i = i0 + p, j = j0 + q;
-      if (i < g.H && j < g.W) {
-        const long long gi = tplane + (long long)(g.B + i) * g.P + g.B + j;
-        a.w[gi] = a.u[gi] * (tile_at(wk, p + 2 * hc, q + 2 * hc) * kFScale);
-      }
+      if (i < g.H && j < g.W) cp_async4(stg + e, a.u + tplane + (long long)(g.B + i) * g.P + g.B + j);
+    }
+    cp_async_commit();
+    __syncthreads();
+    if (t + 1 < s.n) load_spec(kr, a.spec + (long long)(t + 1) * kFT * kFBins);
+    c2r_2d(wk, tw);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+      const int p = e / B, q = e - p * B;
+      const int i = i0 + p, j = j0 + q;
+      if (i < g.H && j < g.W)
+        a.w[tplane + (long long)(g.B + i) * g.P + g.B + j] =
+            stg[e] * (tile_at(wk, p + 2 * hc, q + 2 * hc) * kFScale);
     }
     __syncthreads();
   }
@@ -274,21 +358,31 @@ __global__ void __launch_bounds__(kFThreads, 1)
   __shared__ float2 tw[64];
   float2* sh = fsm;
   float2* wk = fsm + kFBuf;
+  float* stg = reinterpret_cast<float*>(fsm + 2 * kFBuf);  // 128 x 128 floats
   const Geom& g = s.g;
   const int hc = s.hc, B = kFT - 2 * hc;
   const int i0 = blockIdx.y * B, j0 = blockIdx.x * B;
   init_twiddles(tw);
   for (int e = threadIdx.x; e < kFBuf; e += blockDim.x) sh[e] = make_float2(0.f, 0.f);
+  float2 kr[kSpecPer];
+  load_spec(kr, a.spec);
+  region_async(stg, a.w, g, i0 - hc, j0 - hc);
   for (int t = 0; t < s.n; ++t) {
-    load_region(wk, a.w + (long long)t * g.plane, g, i0 - hc, j0 - hc);
+    pack_region(wk, stg);
+    // the next exposure's region arrives during this transform
+    if (t + 1 < s.n) region_async(stg, a.w + (long long)(t + 1) * g.plane, g, i0 - hc, j0 - hc);
     r2c_2d(wk, tw);
-    const float2* kt = a.spec + (long long)t * kFT * kFBins;
-    for (int e = threadIdx.x; e < kFT * kFBins; e += blockDim.x) {
-      const int rr = e / kFBins, m = e - rr * kFBins;
-      const int o = rr * kFP + m;
-      sh[o] = cadd(sh[o], cmulc(wk[o], kt[e]));
+#pragma unroll
+    for (int q = 0; q < kSpecPer; ++q) {
+      const int e = threadIdx.x + q * kFThreads;
+      if (e < kFT * kFBins) {
+        const int rr = e / kFBins, m = e - rr * kFBins;
+        const int o = rr * kFP + m;
+        sh[o] = cadd(sh[o], cmulc(wk[o], kr[q]));
+      }
     }
     __syncthreads();
+    if (t + 1 < s.n) load_spec(kr, a.spec + (long long)(t + 1) * kFT * kFBins);
   }
   c2r_2d(sh, tw);
   for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
@@ -323,7 +417,8 @@ size_t fft_buffer_bytes(const Shape& s) {
   return ((spec + 255) & ~(size_t)255) + wpl;
 }
 
-size_t fft_smem_bytes() { return 2 * (size_t)kFBuf * sizeof(float2); }
+// two transform buffers and a 128 x 128 float staging area
+size_t fft_smem_bytes() { return 2 * (size_t)kFBuf * sizeof(float2) + (size_t)kFT * kFT * sizeof(float); }
 
 int fft_tile_side(const Shape& s) { return kFT - 2 * s.hc; }
 
