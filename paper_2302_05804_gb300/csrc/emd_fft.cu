@@ -60,27 +60,49 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a conj(b)
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ int rev7(int m) { return (int)(__brev((unsigned)m) >> 25); }
 
-// tw[k] = exp(-2 pi i k / 128), k < 64
-__device__ __forceinline__ void init_twiddles(float2* tw) {
-  for (int k = threadIdx.x; k < 64; k += blockDim.x) {
-    float sn, cs;
-    sincospif((float)k / 64.f, &sn, &cs);
-    tw[k] = make_float2(cs, -sn);
+// Twiddles exp(-2 pi i k / 128), laid out so that the 32 lanes of a warp
+// read consecutive entries at every stage (no bank conflicts):
+//   w[k]          k < 64 (first stage: lane l, value q reads w[32 q + l])
+//   lane2[l]      w[2 l] (second stage)
+//   sh[st - 2][l] w[(l & (s - 1)) << st], s = 64 >> st, st = 2 .. 6
+struct TwTab {
+  float2 w[64];
+  float2 lane2[32];
+  float2 sh[5][32];
+};
+
+__device__ __forceinline__ float2 twiddle(int k) {
+  float sn, cs;
+  sincospif((float)k / 64.f, &sn, &cs);
+  return make_float2(cs, -sn);
+}
+
+__device__ __forceinline__ void init_twiddles(TwTab& T) {
+  for (int e = threadIdx.x; e < 64 + 32 + 5 * 32; e += blockDim.x) {
+    if (e < 64) {
+      T.w[e] = twiddle(e);
+    } else if (e < 96) {
+      T.lane2[e - 64] = twiddle(2 * (e - 64));
+    } else {
+      const int st = 2 + (e - 96) / 32, l = (e - 96) & 31, s = 64 >> st;
+      T.sh[st - 2][l] = twiddle((l & (s - 1)) << st);
+    }
   }
+  __syncthreads();
 }
 
 // One 128-point FFT per warp, in registers: lane l holds v[q] = x[32 q + l].
 // Decimation in frequency (natural in, bit-reversed out): the spans 64 and
 // 32 pair the four values a lane holds; spans 16 .. 1 pair lanes l and
 // l ^ s through shuffles.
-__device__ __forceinline__ void warp_fft_dif(float2 (&v)[4], const float2* tw, int lane) {
+__device__ __forceinline__ void warp_fft_dif(float2 (&v)[4], const TwTab& T, int lane) {
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const float2 a = v[q], b = v[q + 2];
     v[q] = cadd(a, b);
-    v[q + 2] = cmul(csub(a, b), tw[32 * q + lane]);
+    v[q + 2] = cmul(csub(a, b), T.w[32 * q + lane]);
   }
-  const float2 t1 = tw[2 * lane];
+  const float2 t1 = T.lane2[lane];
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     const float2 a = v[2 * p], b = v[2 * p + 1];
@@ -91,7 +113,7 @@ __device__ __forceinline__ void warp_fft_dif(float2 (&v)[4], const float2* tw, i
   for (int st = 2; st < 7; ++st) {
     const int s = 64 >> st;
     const bool upper = (lane & s) != 0;
-    const float2 t = tw[(lane & (s - 1)) << st];
+    const float2 t = T.sh[st - 2][lane];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       float2 o;
@@ -103,13 +125,13 @@ __device__ __forceinline__ void warp_fft_dif(float2 (&v)[4], const float2* tw, i
 }
 
 // Inverse (conjugate twiddles), decimation in time: bit-reversed in,
-// natural out, unscaled.
-__device__ __forceinline__ void warp_ifft_dit(float2 (&v)[4], const float2* tw, int lane) {
+// natural out, unscaled. Stage st (span 1 << st) uses sh[4 - st].
+__device__ __forceinline__ void warp_ifft_dit(float2 (&v)[4], const TwTab& T, int lane) {
 #pragma unroll
   for (int st = 0; st < 5; ++st) {
     const int s = 1 << st;
     const bool upper = (lane & s) != 0;
-    const float2 t = conjf2(tw[(lane & (s - 1)) << (6 - st)]);
+    const float2 t = conjf2(T.sh[4 - st][lane]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float2 w = upper ? cmul(v[q], t) : v[q];
@@ -119,7 +141,7 @@ __device__ __forceinline__ void warp_ifft_dit(float2 (&v)[4], const float2* tw, 
       v[q] = upper ? csub(o, w) : cadd(w, o);
     }
   }
-  const float2 t1 = conjf2(tw[2 * lane]);
+  const float2 t1 = conjf2(T.lane2[lane]);
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     const float2 a = v[2 * p], b = cmul(v[2 * p + 1], t1);
@@ -128,7 +150,7 @@ __device__ __forceinline__ void warp_ifft_dit(float2 (&v)[4], const float2* tw, 
   }
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    const float2 a = v[q], b = cmul(v[q + 2], conjf2(tw[32 * q + lane]));
+    const float2 a = v[q], b = cmul(v[q + 2], conjf2(T.w[32 * q + lane]));
     v[q] = cadd(a, b);
     v[q + 2] = csub(a, b);
   }
@@ -177,55 +199,130 @@ __device__ __forceinline__ void merge_pair(float2* r, int lane) {
   __syncwarp();
 }
 
-// forward real 2D transform in place (see the file comment)
-__device__ void r2c_2d(float2* buf, const float2* tw) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int k = warp; k < 64; k += nw) {
+// The column passes are split between the warps: warp w owns columns
+// w, w + 16, ... (kColsPerWarp at most). A PSF spectrum is stored column by
+// column (column m: 128 rows, contiguous), so a warp loads the values of its
+// columns coalesced into registers: kr[c][q] = spectrum(row 32 q + lane,
+// column w + 16 c).
+constexpr int kWarps = kFThreads / 32;
+constexpr int kColsPerWarp = (kFBins + kWarps - 1) / kWarps;  // 5
+using SpecRegs = float2[kColsPerWarp][4];
+
+__device__ __forceinline__ void load_spec_cols(SpecRegs& kr, const float2* kt) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < kColsPerWarp; ++c) {
+    const int m = warp + kWarps * c;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      kr[c][q] = m < kFBins ? kt[m * kFT + 32 * q + lane] : make_float2(0.f, 0.f);
+  }
+}
+
+// forward 2D transform, rows: 64 packed row FFTs and the split
+__device__ void r2c_rows(float2* buf, const TwTab& T) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = warp; k < 64; k += kWarps) {
     float2* r = buf + 2 * k * kFP;
     float2 v[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) v[q] = r[32 * q + lane];
-    warp_fft_dif(v, tw, lane);
+    warp_fft_dif(v, T, lane);
 #pragma unroll
     for (int q = 0; q < 4; ++q) r[32 * q + lane] = v[q];
     __syncwarp();
     split_pair(r, lane);
   }
   __syncthreads();
-  for (int m = warp; m < kFBins; m += nw) {
+}
+
+// forward real 2D transform in place (see the file comment)
+__device__ void r2c_2d(float2* buf, const TwTab& T) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  r2c_rows(buf, T);
+  for (int m = warp; m < kFBins; m += kWarps) {
     float2 v[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) v[q] = buf[(32 * q + lane) * kFP + m];
-    warp_fft_dif(v, tw, lane);
+    warp_fft_dif(v, T, lane);
 #pragma unroll
     for (int q = 0; q < 4; ++q) buf[(32 * q + lane) * kFP + m] = v[q];
   }
   __syncthreads();
 }
 
-// inverse real 2D transform in place (unscaled)
-__device__ void c2r_2d(float2* buf, const float2* tw) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int m = warp; m < kFBins; m += nw) {
-    float2 v[4];
+// forward transform of buf (destroyed) added, times conj(spectrum), into acc:
+// acc += FFT(buf) conj(k^), the column FFTs never written back
+__device__ void r2c_2d_accumulate(float2* buf, float2* acc, const SpecRegs& kr, const TwTab& T) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  r2c_rows(buf, T);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = buf[(32 * q + lane) * kFP + m];
-    warp_ifft_dit(v, tw, lane);
+  for (int c = 0; c < kColsPerWarp; ++c) {
+    const int m = warp + kWarps * c;
+    if (m < kFBins) {
+      float2 v[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) buf[(32 * q + lane) * kFP + m] = v[q];
+      for (int q = 0; q < 4; ++q) v[q] = buf[(32 * q + lane) * kFP + m];
+      warp_fft_dif(v, T, lane);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float2* o = acc + (32 * q + lane) * kFP + m;
+        *o = cadd(*o, cmulc(v[q], kr[c][q]));
+      }
+    }
   }
   __syncthreads();
-  for (int k = warp; k < 64; k += nw) {
+}
+
+// inverse transform, rows: merge and 64 packed row inverse FFTs
+__device__ void c2r_rows(float2* buf, const TwTab& T) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = warp; k < 64; k += kWarps) {
     float2* r = buf + 2 * k * kFP;
     merge_pair(r, lane);
     float2 v[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) v[q] = r[32 * q + lane];
-    warp_ifft_dit(v, tw, lane);
+    warp_ifft_dit(v, T, lane);
 #pragma unroll
     for (int q = 0; q < 4; ++q) r[32 * q + lane] = v[q];
   }
   __syncthreads();
+}
+
+// inverse real 2D transform in place (unscaled)
+__device__ void c2r_2d(float2* buf, const TwTab& T) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int m = warp; m < kFBins; m += kWarps) {
+    float2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = buf[(32 * q + lane) * kFP + m];
+    warp_ifft_dit(v, T, lane);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) buf[(32 * q + lane) * kFP + m] = v[q];
+  }
+  __syncthreads();
+  c2r_rows(buf, T);
+}
+
+// dst = C2R(src . k^) (unscaled); src is left intact
+__device__ void c2r_2d_product(const float2* src, float2* dst, const SpecRegs& kr,
+                               const TwTab& T) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < kColsPerWarp; ++c) {
+    const int m = warp + kWarps * c;
+    if (m < kFBins) {
+      float2 v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = cmul(src[(32 * q + lane) * kFP + m], kr[c][q]);
+      warp_ifft_dit(v, T, lane);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[(32 * q + lane) * kFP + m] = v[q];
+    }
+  }
+  __syncthreads();
+  c2r_rows(dst, T);
 }
 
 // value of tile pixel (P, Q) after c2r_2d (unscaled)
@@ -267,24 +364,12 @@ __device__ void pack_region(float2* buf, const float* stg) {
   __syncthreads();
 }
 
-// a thread's share of one PSF half spectrum (element e = tid + q kFThreads of
-// the 128 x 65 array), held in registers so that the next exposure's
-// spectrum loads while the current transform runs
-constexpr int kSpecPer = (kFT * kFBins + kFThreads - 1) / kFThreads;  // 17
-__device__ __forceinline__ void load_spec(float2 (&k)[kSpecPer], const float2* kt) {
-#pragma unroll
-  for (int q = 0; q < kSpecPer; ++q) {
-    const int e = threadIdx.x + q * kFThreads;
-    k[q] = e < kFT * kFBins ? kt[e] : make_float2(0.f, 0.f);
-  }
-}
-
 __global__ void __launch_bounds__(kFThreads, 1)
     fft_spectra_kernel(const float* __restrict__ f, int K, float2* __restrict__ spec) {
   extern __shared__ float2 fsm[];
-  __shared__ float2 tw[64];
+  __shared__ TwTab T;
   float2* buf = fsm;
-  init_twiddles(tw);
+  init_twiddles(T);
   const float* ft = f + (long long)blockIdx.x * K * K;
   for (int e = threadIdx.x; e < 64 * kFT; e += blockDim.x) {
     const int k = e >> 7, j = e & (kFT - 1);
@@ -294,10 +379,11 @@ __global__ void __launch_bounds__(kFThreads, 1)
     buf[2 * k * kFP + j] = make_float2(a, b);
   }
   __syncthreads();
-  r2c_2d(buf, tw);
+  r2c_2d(buf, T);
+  // column by column: out[m][row]
   float2* out = spec + (long long)blockIdx.x * kFT * kFBins;
   for (int e = threadIdx.x; e < kFT * kFBins; e += blockDim.x) {
-    const int rr = e / kFBins, m = e - rr * kFBins;
+    const int m = e >> 7, rr = e & (kFT - 1);
     out[e] = buf[rr * kFP + m];
   }
 }
@@ -305,30 +391,22 @@ __global__ void __launch_bounds__(kFThreads, 1)
 __global__ void __launch_bounds__(kFThreads, 1)
     fft_forward_kernel(const Shape s, const FftLaunch a) {
   extern __shared__ float2 fsm[];
-  __shared__ float2 tw[64];
+  __shared__ TwTab T;
   float2* xh = fsm;
   float2* wk = fsm + kFBuf;
   float* stg = reinterpret_cast<float*>(fsm + 2 * kFBuf);  // 128 x 128 floats
   const Geom& g = s.g;
   const int hc = s.hc, B = kFT - 2 * hc;
   const int i0 = blockIdx.y * B, j0 = blockIdx.x * B;
-  init_twiddles(tw);
-  float2 kr[kSpecPer];
-  load_spec(kr, a.spec);
+  init_twiddles(T);
+  SpecRegs kr;
+  load_spec_cols(kr, a.spec);
   region_async(stg, a.x, g, i0 - hc, j0 - hc);
   pack_region(xh, stg);
-  r2c_2d(xh, tw);
+  r2c_2d(xh, T);
   for (int t = 0; t < s.n; ++t) {
-#pragma unroll
-    for (int q = 0; q < kSpecPer; ++q) {
-      const int e = threadIdx.x + q * kFThreads;
-      if (e < kFT * kFBins) {
-        const int rr = e / kFBins, m = e - rr * kFBins;
-        wk[rr * kFP + m] = cmul(xh[rr * kFP + m], kr[q]);
-      }
-    }
     // u of this exposure (B x B, row-major in stg) arrives during the
-    // inverse transform; the next spectrum too
+    // inverse transform
     const long long tplane = (long long)t * g.plane;
     for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
       const int p = e / B, q = e - p * B;
@@ -336,9 +414,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
       if (i < g.H && j < g.W) cp_async4(stg + e, a.u + tplane + (long long)(g.B + i) * g.P + g.B + j);
     }
     cp_async_commit();
-    __syncthreads();
-    if (t + 1 < s.n) load_spec(kr, a.spec + (long long)(t + 1) * kFT * kFBins);
-    c2r_2d(wk, tw);
+    c2r_2d_product(xh, wk, kr, T);
+    // the next spectrum loads during the epilogue and the next column pass
+    if (t + 1 < s.n) load_spec_cols(kr, a.spec + (long long)(t + 1) * kFT * kFBins);
     cp_async_wait_all();
     __syncthreads();
     for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
@@ -355,36 +433,26 @@ __global__ void __launch_bounds__(kFThreads, 1)
 __global__ void __launch_bounds__(kFThreads, 1)
     fft_adjoint_kernel(const Shape s, const FftLaunch a) {
   extern __shared__ float2 fsm[];
-  __shared__ float2 tw[64];
+  __shared__ TwTab T;
   float2* sh = fsm;
   float2* wk = fsm + kFBuf;
   float* stg = reinterpret_cast<float*>(fsm + 2 * kFBuf);  // 128 x 128 floats
   const Geom& g = s.g;
   const int hc = s.hc, B = kFT - 2 * hc;
   const int i0 = blockIdx.y * B, j0 = blockIdx.x * B;
-  init_twiddles(tw);
+  init_twiddles(T);
   for (int e = threadIdx.x; e < kFBuf; e += blockDim.x) sh[e] = make_float2(0.f, 0.f);
-  float2 kr[kSpecPer];
-  load_spec(kr, a.spec);
+  SpecRegs kr;
+  load_spec_cols(kr, a.spec);
   region_async(stg, a.w, g, i0 - hc, j0 - hc);
   for (int t = 0; t < s.n; ++t) {
     pack_region(wk, stg);
     // the next exposure's region arrives during this transform
     if (t + 1 < s.n) region_async(stg, a.w + (long long)(t + 1) * g.plane, g, i0 - hc, j0 - hc);
-    r2c_2d(wk, tw);
-#pragma unroll
-    for (int q = 0; q < kSpecPer; ++q) {
-      const int e = threadIdx.x + q * kFThreads;
-      if (e < kFT * kFBins) {
-        const int rr = e / kFBins, m = e - rr * kFBins;
-        const int o = rr * kFP + m;
-        sh[o] = cadd(sh[o], cmulc(wk[o], kr[q]));
-      }
-    }
-    __syncthreads();
-    if (t + 1 < s.n) load_spec(kr, a.spec + (long long)(t + 1) * kFT * kFBins);
+    r2c_2d_accumulate(wk, sh, kr, T);
+    if (t + 1 < s.n) load_spec_cols(kr, a.spec + (long long)(t + 1) * kFT * kFBins);
   }
-  c2r_2d(sh, tw);
+  c2r_2d(sh, T);
   for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
     const int p = e / B, q = e - p * B;
     const int i = i0 + p, j = j0 + q;

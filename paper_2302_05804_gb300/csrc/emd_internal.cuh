@@ -127,7 +127,7 @@ struct FftLaunch {
   const float* N;       // numerator
   const float* u;       // n weight planes
   float* w;             // n planes of u_t z_t (written by the forward pass)
-  const float2* spec;   // n half spectra of the PSFs, 128 x 65 each
+  const float2* spec;   // n half spectra of the PSFs, 65 columns x 128 rows each
 };
 size_t fft_buffer_bytes(const Shape& s);
 size_t fft_smem_bytes();
