@@ -64,7 +64,9 @@ __device__ __forceinline__ int rev7(int m) { return (int)(__brev((unsigned)m) >>
 // read consecutive entries at every stage (no bank conflicts):
 //   w[k]          k < 64 (first stage: lane l, value q reads w[32 q + l])
 //   lane2[l]      w[2 l] (second stage)
-//   sh[st - 2][l] w[(l & (s - 1)) << st], s = 64 >> st, st = 2 .. 6
+//   sh[st - 2][l] w[(l & (s - 1)) << st], s = 64 >> st, st = 2 .. 6, for the
+//                 lanes with bit s set, and 1 for the others (so that every
+//                 lane runs the same instructions; see warp_fft_dif)
 struct TwTab {
   float2 w[64];
   float2 lane2[32];
@@ -85,7 +87,7 @@ __device__ __forceinline__ void init_twiddles(TwTab& T) {
       T.lane2[e - 64] = twiddle(2 * (e - 64));
     } else {
       const int st = 2 + (e - 96) / 32, l = (e - 96) & 31, s = 64 >> st;
-      T.sh[st - 2][l] = twiddle((l & (s - 1)) << st);
+      T.sh[st - 2][l] = (l & s) ? twiddle((l & (s - 1)) << st) : make_float2(1.f, 0.f);
     }
   }
   __syncthreads();
@@ -109,17 +111,19 @@ __device__ __forceinline__ void warp_fft_dif(float2 (&v)[4], const TwTab& T, int
     v[2 * p] = cadd(a, b);
     v[2 * p + 1] = cmul(csub(a, b), t1);
   }
+  // lane pairs (l, l ^ s): the lower lane keeps v + o, the upper one
+  // (o - v) t; both as (o + sgn v) t' with t' = 1 on the lower lane
 #pragma unroll
   for (int st = 2; st < 7; ++st) {
     const int s = 64 >> st;
-    const bool upper = (lane & s) != 0;
+    const float sgn = (lane & s) ? -1.f : 1.f;
     const float2 t = T.sh[st - 2][lane];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       float2 o;
       o.x = __shfl_xor_sync(0xffffffffu, v[q].x, s);
       o.y = __shfl_xor_sync(0xffffffffu, v[q].y, s);
-      v[q] = upper ? cmul(csub(o, v[q]), t) : cadd(v[q], o);
+      v[q] = cmul(make_float2(fmaf(sgn, v[q].x, o.x), fmaf(sgn, v[q].y, o.y)), t);
     }
   }
 }
@@ -127,18 +131,20 @@ __device__ __forceinline__ void warp_fft_dif(float2 (&v)[4], const TwTab& T, int
 // Inverse (conjugate twiddles), decimation in time: bit-reversed in,
 // natural out, unscaled. Stage st (span 1 << st) uses sh[4 - st].
 __device__ __forceinline__ void warp_ifft_dit(float2 (&v)[4], const TwTab& T, int lane) {
+  // lane pairs (l, l ^ s): the upper lane's value is first multiplied by
+  // the twiddle (t' = 1 on the lower lane); then lower: w + o, upper: o - w
 #pragma unroll
   for (int st = 0; st < 5; ++st) {
     const int s = 1 << st;
-    const bool upper = (lane & s) != 0;
+    const float sgn = (lane & s) ? -1.f : 1.f;
     const float2 t = conjf2(T.sh[4 - st][lane]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float2 w = upper ? cmul(v[q], t) : v[q];
+      const float2 w = cmul(v[q], t);
       float2 o;
       o.x = __shfl_xor_sync(0xffffffffu, w.x, s);
       o.y = __shfl_xor_sync(0xffffffffu, w.y, s);
-      v[q] = upper ? csub(o, w) : cadd(w, o);
+      v[q] = make_float2(fmaf(sgn, w.x, o.x), fmaf(sgn, w.y, o.y));
     }
   }
   const float2 t1 = conjf2(T.lane2[lane]);
