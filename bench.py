@@ -275,6 +275,40 @@ def run_serving(p, args):
                         "64 slots"}
 
 
+def run_variants(p, steps=5, warmup=2):
+    """The other built forms of the iteration on the same frame set, each in
+    its own context: CUDA events per iteration on the context's stream."""
+    import torch
+    from paper_2302_05804_gb300 import emd
+    forms = [("fft", emd.EMD_PREC_FFT_FP32, 0.0), ("split_bf16", emd.EMD_PREC_SPLIT_BF16, 0.0),
+             ("bf16", emd.EMD_PREC_BF16, 0.0), ("student_t_nu3", emd.EMD_PREC_FP32, 3.0)]
+    out = {}
+    for name, prec, nu in forms:
+        if prec == emd.EMD_PREC_FFT_FP32 and p.r != 1:
+            continue
+        st = torch.cuda.Stream()
+        d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r, stream=st)
+        try:
+            d.set_frames(p.y, p.v, p.f, p.mask)
+            if prec:
+                d.set_precision(prec)
+            if nu > 0:
+                d.set_noise(emd.EMD_NOISE_STUDENT_T, nu)
+            d.iterate(warmup)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            d.iterate(steps)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+        finally:
+            d.close()
+        out[name] = {"ms_per_iteration": ms,
+                     "value": p.r * p.r * p.H * p.W * p.n / (ms / 1e3) / 1e9, "unit": UNIT}
+    return out
+
+
 def run_psf_fit(p, iters):
     """Eq. (4) fit of super-resolved PSFs for every exposure: the workload's
     coarse PSFs (n x K x K) to r = 2 fine PSFs (2 (K-1) + 1 per side), g a
@@ -324,8 +358,9 @@ def config_of(args, extra=None):
          "H": H, "W": W, "n": n, "K": K, "r": r,
          "precision": args.precision,
          "noise": (f"student-t nu={args.nu:g}" if getattr(args, "nu", 0) > 0 else "gaussian"),
-         "l2": ("no flush: each step streams the u planes "
-                f"({n * H * W * 4 / 1e9:.1f} GB), far above the 129 MB L2"),
+         "l2": (f"no flush: each step streams the u planes ({n * H * W * 4 / 1e9:.2f} GB), "
+                + ("far above" if n * H * W * 4 > 4 * 129e6 else "not far above")
+                + " the 129 MB L2"),
          "parallelism": "replicas"}
     if extra:
         c.update(extra)
@@ -472,6 +507,9 @@ def run_ours(args):
     psf_fit = None
     if args.psf_iters > 0 and prec == 0:
         psf_fit = run_psf_fit(p, args.psf_iters)
+    variants = None
+    if args.variants and prec == 0 and args.nu == 0:
+        variants = run_variants(p)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -491,7 +529,7 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": args.steps * LAUNCHES_PER_STEP[args.precision] * (2 if args.nu > 0 else 1),
             "clocks": clocks,
-            "serving": serving, "psf_fit": psf_fit,
+            "serving": serving, "psf_fit": psf_fit, "variants": variants,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -515,6 +553,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=40,
                     help="jobs in the serving sample (0 disables it)")
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="skip timing the FFT, tensor-core and heavy-tailed forms")
     ap.add_argument("--nu", type=float, default=0.0,
                     help="Student-t degrees of freedom of the heavy-tailed noise model "
                          "(0: Gaussian, Eq. (1))")

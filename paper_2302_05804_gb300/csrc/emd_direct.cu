@@ -232,6 +232,9 @@ __device__ __forceinline__ double block_sum_f64(double v, double* red /* >= 8 */
 // One 128 x 128 tile (rows i0.., cols j0..) handled by CTA q of a pair; the
 // caller owns the mbarrier, its phase, the timeout flag and the chi-square
 // accumulator so a persistent kernel can run many tiles per CTA pair.
+// STUDENT: heavy-tailed weights (a.nu > 0); compiled separately so that the
+// Gaussian kernel carries none of that code.
+template <bool STUDENT>
 __device__ __forceinline__ void fused_tile(const Shape& s, const FusedArgs& a, const int mode,
                                            const int i0, const int j0, const int q, float* smem,
                                            uint64_t* mbar, uint32_t& phase, bool& timed_out,
@@ -307,7 +310,7 @@ __device__ __forceinline__ void fused_tile(const Shape& s, const FusedArgs& a, c
           const long long grow = tplane + (long long)(i0 + hc + rr) * g.P + j0 + hc;
           if (xchg) {
             float* wrow = srow(ws, rr - kHalf * q);
-            if (a.nu > 0.f) {
+            if (STUDENT) {
               const float nu1 = a.nu + 1.f;
 #pragma unroll
               for (int c = 0; c < 16; ++c) {
@@ -333,7 +336,7 @@ __device__ __forceinline__ void fused_tile(const Shape& s, const FusedArgs& a, c
               if (rr >= hc && rr < hc + kTile && cc >= hc && cc < hc + kTile && i < g.H &&
                   j < g.W && uv != 0.f) {
                 const double d = (double)a.y[grow + cc] - (double)acc[p][c];
-                if (a.nu > 0.f)
+                if (STUDENT)
                   chi += ((double)a.nu + 1.0) * log1p((double)uv * d * d / (double)a.nu);
                 else
                   chi += (double)uv * d * d;
@@ -431,6 +434,7 @@ __device__ __forceinline__ void fused_tile(const Shape& s, const FusedArgs& a, c
   if (xchg) cluster_wait();  // [B_{n-1}]
 }
 
+template <bool STUDENT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     fused_kernel(const Shape s, const FusedArgs a, const int mode, double* __restrict__ part) {
   extern __shared__ __align__(128) float smem[];
@@ -446,8 +450,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   uint32_t phase = 0;
   bool timed_out = false;
   double chi = 0.0;
-  fused_tile(s, a, mode, blockIdx.y * kTile, (blockIdx.x >> 1) * kTile, q, smem, &mbar_s, phase,
-             timed_out, chi);
+  fused_tile<STUDENT>(s, a, mode, blockIdx.y * kTile, (blockIdx.x >> 1) * kTile, q, smem, &mbar_s,
+                      phase, timed_out, chi);
   if (mode == 2) {
     const double tot = block_sum_f64(chi, red);
     if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = tot;
@@ -459,18 +463,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   }
 }
 
+template <bool STUDENT>
+cudaError_t launch_fused_t(const Shape& s, const FusedArgs& a, int mode, double* part,
+                           cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(fused_kernel<STUDENT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)s.smem_fused);
+  if (e != cudaSuccess) return e;
+  dim3 grid(2 * s.gx, s.gy), block(kThreads);
+  fused_kernel<STUDENT><<<grid, block, s.smem_fused, st>>>(s, a, mode, part);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fused(const Shape& s, const FusedArgs& a, int mode, double* part,
                          cudaStream_t st) {
-  static size_t attr_bytes = 0;  // largest dynamic shared memory opted into so far
-  if (s.smem_fused > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)s.smem_fused);
-    if (e != cudaSuccess) return e;
-    attr_bytes = s.smem_fused;
-  }
-  dim3 grid(2 * s.gx, s.gy), block(kThreads);
-  fused_kernel<<<grid, block, s.smem_fused, st>>>(s, a, mode, part);
-  return cudaGetLastError();
+  return a.nu > 0.f ? launch_fused_t<true>(s, a, mode, part, st)
+                    : launch_fused_t<false>(s, a, mode, part, st);
 }
 
 int fused_blocks(const Shape& s) { return 2 * s.gx * s.gy; }
@@ -511,7 +519,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const BatchJob& J = jobs[w.x];
     if (J.remaining <= 0) continue;
     const int tx = w.y % J.s.gx, ty = w.y / J.s.gx;
-    fused_tile(J.s, J.a[J.cur], 0, ty * kTile, tx * kTile, q, smem, &mbar_s, phase, timed_out,
+    fused_tile<false>(J.s, J.a[J.cur], 0, ty * kTile, tx * kTile, q, smem, &mbar_s, phase, timed_out,
                chi);
   }
   if (timed_out) {
