@@ -59,6 +59,12 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a conj(b)
 }
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ int rev7(int m) { return (int)(__brev((unsigned)m) >> 25); }
+// Position of element p of a packed row's spectrum between the row FFT and
+// the split (or between the merge and the inverse row FFT): bits 0-2 XORed
+// with bits 4-6, so that both the row FFT's natural accesses and the
+// bit-reversed accesses of the split and the merge (whose 16 lanes per
+// 64-bit phase differ only in bits 3-6) fall in distinct banks.
+__device__ __forceinline__ int swz(int p) { return p ^ ((p >> 4) & 7); }
 
 // Twiddles exp(-2 pi i k / 128), laid out so that the 32 lanes of a warp
 // read consecutive entries at every stage (no bank conflicts):
@@ -170,7 +176,7 @@ __device__ __forceinline__ void split_pair(float2* r, int lane) {
   const int cnt = lane == 0 ? 3 : 2;
   for (int q = 0; q < cnt; ++q) {
     const int m = ms[q];
-    const float2 cm = r[rev7(m)], cn = conjf2(r[rev7((128 - m) & 127)]);
+    const float2 cm = r[swz(rev7(m))], cn = conjf2(r[swz(rev7((128 - m) & 127))]);
     e[q] = make_float2(0.5f * (cm.x + cn.x), 0.5f * (cm.y + cn.y));
     const float2 d = csub(cm, cn);  // (cm - conj(c_-m)) / (2i) = -i d / 2
     o[q] = make_float2(0.5f * d.y, -0.5f * d.x);
@@ -201,7 +207,7 @@ __device__ __forceinline__ void merge_pair(float2* r, int lane) {
   }
   __syncwarp();
 #pragma unroll
-  for (int q = 0; q < 4; ++q) r[rev7(lane + 32 * q)] = d[q];
+  for (int q = 0; q < 4; ++q) r[swz(rev7(lane + 32 * q))] = d[q];
   __syncwarp();
 }
 
@@ -235,7 +241,7 @@ __device__ void r2c_rows(float2* buf, const TwTab& T) {
     for (int q = 0; q < 4; ++q) v[q] = r[32 * q + lane];
     warp_fft_dif(v, T, lane);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) r[32 * q + lane] = v[q];
+    for (int q = 0; q < 4; ++q) r[swz(32 * q + lane)] = v[q];
     __syncwarp();
     split_pair(r, lane);
   }
@@ -288,7 +294,7 @@ __device__ void c2r_rows(float2* buf, const TwTab& T) {
     merge_pair(r, lane);
     float2 v[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = r[32 * q + lane];
+    for (int q = 0; q < 4; ++q) v[q] = r[swz(32 * q + lane)];
     warp_ifft_dit(v, T, lane);
 #pragma unroll
     for (int q = 0; q < 4; ++q) r[32 * q + lane] = v[q];
