@@ -52,7 +52,7 @@ namespace {
 
 constexpr int kPsfThreads = 512;
 constexpr int kPsfWarps = kPsfThreads / 32;
-constexpr int kStrip = 8;
+constexpr int kStrip = 4;
 constexpr int kMaxCluster = 8;
 
 __host__ __device__ constexpr int rup4(int v) { return (v + 3) & ~3; }
