@@ -284,8 +284,6 @@ def run_variants(p, steps=5, warmup=2):
              ("bf16", emd.EMD_PREC_BF16, 0.0), ("student_t_nu3", emd.EMD_PREC_FP32, 3.0)]
     out = {}
     for name, prec, nu in forms:
-        if prec == emd.EMD_PREC_FFT_FP32 and p.r != 1:
-            continue
         st = torch.cuda.Stream()
         d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r, stream=st)
         try:
@@ -427,10 +425,11 @@ def run_ours(args):
         # = 2.5 N log2 N, N = 128^2) and of the spectrum products, against
         # the FP32 peak; the direct-form flops it replaces are reported beside
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        B = 128 - (p.K - 1)
+        hc = ((p.K - 1) // 2 + p.r - 1) // p.r
+        B = 128 - 2 * hc
         tiles = -(-p.H // B) * -(-p.W // B)
-        ffts = tiles * (2 * p.n + 2)
-        fl = ffts * 2.5 * 16384 * 14 + tiles * 2 * p.n * 6 * 128 * 65
+        ffts = tiles * (2 * p.n + 2 * p.r * p.r)
+        fl = ffts * 2.5 * 16384 * 14 + tiles * 2 * p.n * p.r * p.r * 6 * 128 * 65
         ex = fl / launch_s / 1e12
         roofline = {"bound": "alu", "achieved": ex, "peak": peak, "unit": "TFLOP/s",
                     "frac": ex / peak, "traffic": None,

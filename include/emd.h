@@ -144,10 +144,11 @@ int emd_loglik(emd_ctx *ctx, double *out, double *chi2);
 /* Select the convolution arithmetic (enum emd_precision). Modes not built
  * into this library return EMD_EUNSUPPORTED and leave the mode unchanged.
  * EMD_PREC_FFT_FP32 computes the forward model and the adjoint of each
- * iteration by FP32 FFTs (overlap-save: output tiles of 128 - 2h pixels,
- * h = (K-1)/2, transformed as 128 x 128 real tiles); it needs r = 1
- * (EMD_EUNSUPPORTED otherwise) and n extra exposure planes of device memory
- * for the weighted model images u_t z_t, allocated on first selection.
+ * iteration by FP32 FFTs (overlap-save: output tiles of 128 - 2 hc pixels,
+ * hc = floor(((K-1)/2 + r - 1) / r), transformed as 128 x 128 real tiles
+ * of the polyphase planes); it needs n extra exposure planes of device
+ * memory for the weighted model images u_t z_t and, for r > 1, a per-tile
+ * scratch of r^2 spectra (66.5 KB each), allocated on first selection.
  * emd_loglik and emd_iterate_streaming use the direct FP32 kernel in every
  * mode. */
 int emd_set_precision(emd_ctx *ctx, int mode);

@@ -97,6 +97,7 @@ struct emd_ctx {
   char* fft_arena = nullptr;
   float2* fft_spec = nullptr;
   float* fft_w = nullptr;
+  float2* fft_scratch = nullptr;
   bool fft_ready = false;
   bool frames = false;
   int prec = EMD_PREC_FP32;
@@ -328,10 +329,6 @@ int emd_set_precision(emd_ctx* c, int mode) {
   }
   DeviceGuard dg(c->device);
   if (mode == EMD_PREC_FFT_FP32) {
-    if (c->s.r != 1) {
-      set_err("emd_set_precision: the FFT path supports r = 1 only");
-      return EMD_EUNSUPPORTED;
-    }
     if (!c->fft_arena) {
       const size_t need = emd::fft_buffer_bytes(c->s);
       void* p = nullptr;
@@ -342,9 +339,11 @@ int emd_set_precision(emd_ctx* c, int mode) {
       }
       CK(cudaMemsetAsync(p, 0, need, c->st));
       c->fft_arena = static_cast<char*>(p);
-      const size_t spec = ((size_t)c->s.n * 128 * 65 * sizeof(float2) + 255) & ~(size_t)255;
+      const size_t spec = ((size_t)c->s.n * c->s.R2 * 128 * 65 * sizeof(float2) + 255) &
+                          ~(size_t)255;
       c->fft_spec = reinterpret_cast<float2*>(c->fft_arena);
       c->fft_w = reinterpret_cast<float*>(c->fft_arena + spec);
+      c->fft_scratch = reinterpret_cast<float2*>(c->fft_arena + emd::fft_scratch_offset(c->s));
       c->fft_ready = false;
     }
     c->prec = mode;
@@ -480,7 +479,7 @@ int emd_iterate(emd_ctx* c, int k) {
   DeviceGuard dg(c->device);
   if (c->prec == EMD_PREC_FFT_FP32 && k > 0) {
     if (!c->fft_ready) {
-      CK(emd::launch_fft_spectra(c->s, c->fraw, c->fft_spec, c->st));
+      CK(emd::launch_fft_spectra(c->s, c->ka, c->fft_spec, c->st));
       c->fft_ready = true;
     }
     for (int it = 0; it < k; ++it) {
@@ -491,6 +490,7 @@ int emd_iterate(emd_ctx* c, int k) {
       L.u = c->u;
       L.w = c->fft_w;
       L.spec = c->fft_spec;
+      L.scratch = c->fft_scratch;
       CK(emd::launch_fft_iter(c->s, L, c->st));
       c->cur ^= 1;
     }

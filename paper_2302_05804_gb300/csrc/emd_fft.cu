@@ -1,6 +1,8 @@
 // emd_fft.cu -- the forward model and the adjoint of Eq. (2) by FFT
 // (overlap-save on 128 x 128 tiles), an alternative to the direct FP32
-// kernel for r = 1. Same arithmetic type (FP32), different rounding.
+// kernel. Same arithmetic type (FP32), different rounding. For r > 1 every
+// operator below acts on the polyphase planes with the Kc x Kc phase
+// kernels (hc in place of h), summed over the phases in the forward model.
 //
 // For an output tile with origin (i0, j0) and side B = 128 - 2 hc (hc =
 // (K-1)/2), the input region is rows/cols [i0 - hc, i0 - hc + 128) of the
@@ -376,18 +378,20 @@ __device__ void pack_region(float2* buf, const float* stg) {
   __syncthreads();
 }
 
+// one block per (exposure, phase): the Kc x Kc phase kernel (row pitch KP;
+// for r = 1 the PSF itself) at the top-left of a zero 128 x 128 tile
 __global__ void __launch_bounds__(kFThreads, 1)
-    fft_spectra_kernel(const float* __restrict__ f, int K, float2* __restrict__ spec) {
+    fft_spectra_kernel(const float* __restrict__ ka, int Kc, int KP, float2* __restrict__ spec) {
   extern __shared__ float2 fsm[];
   __shared__ TwTab T;
   float2* buf = fsm;
   init_twiddles(T);
-  const float* ft = f + (long long)blockIdx.x * K * K;
+  const float* ft = ka + (long long)blockIdx.x * Kc * KP;
   for (int e = threadIdx.x; e < 64 * kFT; e += blockDim.x) {
     const int k = e >> 7, j = e & (kFT - 1);
     const int i = 2 * k;
-    const float a = (i < K && j < K) ? ft[i * K + j] : 0.f;
-    const float b = (i + 1 < K && j < K) ? ft[(i + 1) * K + j] : 0.f;
+    const float a = (i < Kc && j < Kc) ? ft[i * KP + j] : 0.f;
+    const float b = (i + 1 < Kc && j < Kc) ? ft[(i + 1) * KP + j] : 0.f;
     buf[2 * k * kFP + j] = make_float2(a, b);
   }
   __syncthreads();
@@ -400,6 +404,31 @@ __global__ void __launch_bounds__(kFThreads, 1)
   }
 }
 
+// r > 1: dst = C2R(sum_phi x^_phi . k^_phi) with both spectra read from
+// global memory (x^ from this tile's scratch, L2-resident), column by column
+__device__ void c2r_2d_phase_sum(const float2* xs, const float2* kt, int R2, float2* dst,
+                                 const TwTab& T) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per = kFT * kFBins;
+  for (int m = warp; m < kFBins; m += kWarps) {
+    float2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = make_float2(0.f, 0.f);
+    for (int ph = 0; ph < R2; ++ph) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int o = ph * per + m * kFT + 32 * q + lane;
+        v[q] = cadd(v[q], cmul(xs[o], kt[o]));
+      }
+    }
+    warp_ifft_dit(v, T, lane);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[(32 * q + lane) * kFP + m] = v[q];
+  }
+  __syncthreads();
+  c2r_rows(dst, T);
+}
+
 __global__ void __launch_bounds__(kFThreads, 1)
     fft_forward_kernel(const Shape s, const FftLaunch a) {
   extern __shared__ float2 fsm[];
@@ -408,14 +437,30 @@ __global__ void __launch_bounds__(kFThreads, 1)
   float2* wk = fsm + kFBuf;
   float* stg = reinterpret_cast<float*>(fsm + 2 * kFBuf);  // 128 x 128 floats
   const Geom& g = s.g;
-  const int hc = s.hc, B = kFT - 2 * hc;
+  const int hc = s.hc, B = kFT - 2 * hc, R2 = s.R2;
   const int i0 = blockIdx.y * B, j0 = blockIdx.x * B;
+  const int per = kFT * kFBins;
+  float2* xs = a.scratch + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * R2 * per;
   init_twiddles(T);
   SpecRegs kr;
-  load_spec_cols(kr, a.spec);
-  region_async(stg, a.x, g, i0 - hc, j0 - hc);
-  pack_region(xh, stg);
-  r2c_2d(xh, T);
+  if (R2 == 1) {
+    load_spec_cols(kr, a.spec);
+    region_async(stg, a.x, g, i0 - hc, j0 - hc);
+    pack_region(xh, stg);
+    r2c_2d(xh, T);
+  } else {
+    // the phases' spectra, column by column, into this tile's scratch
+    for (int ph = 0; ph < R2; ++ph) {
+      region_async(stg, a.x + (long long)ph * g.plane, g, i0 - hc, j0 - hc);
+      pack_region(xh, stg);
+      r2c_2d(xh, T);
+      for (int e = threadIdx.x; e < per; e += blockDim.x) {
+        const int m = e >> 7, rr = e & (kFT - 1);
+        xs[ph * per + e] = xh[rr * kFP + m];
+      }
+      __syncthreads();
+    }
+  }
   for (int t = 0; t < s.n; ++t) {
     // u of this exposure (B x B, row-major in stg) arrives during the
     // inverse transform
@@ -426,9 +471,13 @@ __global__ void __launch_bounds__(kFThreads, 1)
       if (i < g.H && j < g.W) cp_async4(stg + e, a.u + tplane + (long long)(g.B + i) * g.P + g.B + j);
     }
     cp_async_commit();
-    c2r_2d_product(xh, wk, kr, T);
-    // the next spectrum loads during the epilogue and the next column pass
-    if (t + 1 < s.n) load_spec_cols(kr, a.spec + (long long)(t + 1) * kFT * kFBins);
+    if (R2 == 1) {
+      c2r_2d_product(xh, wk, kr, T);
+      // the next spectrum loads during the epilogue and the next column pass
+      if (t + 1 < s.n) load_spec_cols(kr, a.spec + (long long)(t + 1) * per);
+    } else {
+      c2r_2d_phase_sum(xs, a.spec + (long long)t * R2 * per, R2, wk, T);
+    }
     cp_async_wait_all();
     __syncthreads();
     for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
@@ -442,34 +491,37 @@ __global__ void __launch_bounds__(kFThreads, 1)
   }
 }
 
-__global__ void __launch_bounds__(kFThreads, 1)
-    fft_adjoint_kernel(const Shape s, const FftLaunch a) {
-  extern __shared__ float2 fsm[];
-  __shared__ TwTab T;
-  float2* sh = fsm;
-  float2* wk = fsm + kFBuf;
-  float* stg = reinterpret_cast<float*>(fsm + 2 * kFBuf);  // 128 x 128 floats
-  const Geom& g = s.g;
-  const int hc = s.hc, B = kFT - 2 * hc;
-  const int i0 = blockIdx.y * B, j0 = blockIdx.x * B;
-  init_twiddles(T);
-  for (int e = threadIdx.x; e < kFBuf; e += blockDim.x) sh[e] = make_float2(0.f, 0.f);
-  SpecRegs kr;
-  load_spec_cols(kr, a.spec);
-  region_async(stg, a.w, g, i0 - hc, j0 - hc);
-  for (int t = 0; t < s.n; ++t) {
-    pack_region(wk, stg);
-    // the next exposure's region arrives during this transform
-    if (t + 1 < s.n) region_async(stg, a.w + (long long)(t + 1) * g.plane, g, i0 - hc, j0 - hc);
-    r2c_2d_accumulate(wk, sh, kr, T);
-    if (t + 1 < s.n) load_spec_cols(kr, a.spec + (long long)(t + 1) * kFT * kFBins);
+// r > 1: acc_phi += FFT(buf) conj(k^_phi) for every phase, accumulators in
+// this tile's scratch (column by column, each element one lane's)
+__device__ void r2c_2d_accumulate_phases(float2* buf, float2* acc, const float2* kt, int R2,
+                                         const TwTab& T) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per = kFT * kFBins;
+  r2c_rows(buf, T);
+  for (int m = warp; m < kFBins; m += kWarps) {
+    float2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = buf[(32 * q + lane) * kFP + m];
+    warp_fft_dif(v, T, lane);
+    for (int ph = 0; ph < R2; ++ph) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int o = ph * per + m * kFT + 32 * q + lane;
+        acc[o] = cadd(acc[o], cmulc(v[q], kt[o]));
+      }
+    }
   }
-  c2r_2d(sh, T);
+  __syncthreads();
+}
+
+// Den of one phase (in sh after the inverse transform) -> the update
+__device__ void update_phase(const float2* sh, const FftLaunch& a, const Geom& g, long long off,
+                             int i0, int j0, int B) {
   for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
     const int p = e / B, q = e - p * B;
     const int i = i0 + p, j = j0 + q;
     if (i < g.H && j < g.W) {
-      const long long gi = (long long)(g.B + i) * g.P + g.B + j;
+      const long long gi = off + (long long)(g.B + i) * g.P + g.B + j;
       const float d = tile_at(sh, p, q) * kFScale;
       const float xo = a.x[gi], nraw = a.N[gi];
       float xv = xo;
@@ -489,12 +541,74 @@ __global__ void __launch_bounds__(kFThreads, 1)
   }
 }
 
+__global__ void __launch_bounds__(kFThreads, 1)
+    fft_adjoint_kernel(const Shape s, const FftLaunch a) {
+  extern __shared__ float2 fsm[];
+  __shared__ TwTab T;
+  float2* sh = fsm;
+  float2* wk = fsm + kFBuf;
+  float* stg = reinterpret_cast<float*>(fsm + 2 * kFBuf);  // 128 x 128 floats
+  const Geom& g = s.g;
+  const int hc = s.hc, B = kFT - 2 * hc, R2 = s.R2;
+  const int i0 = blockIdx.y * B, j0 = blockIdx.x * B;
+  const int per = kFT * kFBins;
+  float2* acc = a.scratch + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * R2 * per;
+  init_twiddles(T);
+  SpecRegs kr;
+  if (R2 == 1) {
+    for (int e = threadIdx.x; e < kFBuf; e += blockDim.x) sh[e] = make_float2(0.f, 0.f);
+    load_spec_cols(kr, a.spec);
+  } else {
+    for (int e = threadIdx.x; e < R2 * per; e += blockDim.x) acc[e] = make_float2(0.f, 0.f);
+  }
+  region_async(stg, a.w, g, i0 - hc, j0 - hc);
+  for (int t = 0; t < s.n; ++t) {
+    pack_region(wk, stg);
+    // the next exposure's region arrives during this transform
+    if (t + 1 < s.n) region_async(stg, a.w + (long long)(t + 1) * g.plane, g, i0 - hc, j0 - hc);
+    if (R2 == 1) {
+      r2c_2d_accumulate(wk, sh, kr, T);
+      if (t + 1 < s.n) load_spec_cols(kr, a.spec + (long long)(t + 1) * per);
+    } else {
+      r2c_2d_accumulate_phases(wk, acc, a.spec + (long long)t * R2 * per, R2, T);
+    }
+  }
+  if (R2 == 1) {
+    c2r_2d(sh, T);
+    update_phase(sh, a, g, 0, i0, j0, B);
+  } else {
+    for (int ph = 0; ph < R2; ++ph) {
+      for (int e = threadIdx.x; e < per; e += blockDim.x) {
+        const int m = e >> 7, rr = e & (kFT - 1);
+        sh[rr * kFP + m] = acc[ph * per + e];
+      }
+      __syncthreads();
+      c2r_2d(sh, T);
+      update_phase(sh, a, g, (long long)ph * g.plane, i0, j0, B);
+      __syncthreads();
+    }
+  }
+}
+
 }  // namespace
 
+static size_t fft_tiles(const Shape& s) {
+  const int B = kFT - 2 * s.hc;
+  return (size_t)((s.g.W + B - 1) / B) * ((s.g.H + B - 1) / B);
+}
+
+// layout of the FFT buffer: PSF spectra (n R2), w planes (n), then for r > 1
+// the per-tile scratch (tiles R2 spectra)
+size_t fft_scratch_offset(const Shape& s) {
+  const size_t spec = ((size_t)s.n * s.R2 * kFT * kFBins * sizeof(float2) + 255) & ~(size_t)255;
+  const size_t wpl = ((size_t)s.n * s.g.plane * sizeof(float) + 255) & ~(size_t)255;
+  return spec + wpl;
+}
+
 size_t fft_buffer_bytes(const Shape& s) {
-  const size_t spec = (size_t)s.n * kFT * kFBins * sizeof(float2);
-  const size_t wpl = (size_t)s.n * s.g.plane * sizeof(float);
-  return ((spec + 255) & ~(size_t)255) + wpl;
+  const size_t scratch =
+      s.R2 > 1 ? fft_tiles(s) * s.R2 * kFT * kFBins * sizeof(float2) : 0;
+  return fft_scratch_offset(s) + scratch;
 }
 
 // two transform buffers and a 128 x 128 float staging area
@@ -502,12 +616,12 @@ size_t fft_smem_bytes() { return 2 * (size_t)kFBuf * sizeof(float2) + (size_t)kF
 
 int fft_tile_side(const Shape& s) { return kFT - 2 * s.hc; }
 
-cudaError_t launch_fft_spectra(const Shape& s, const float* f, float2* spec, cudaStream_t st) {
+cudaError_t launch_fft_spectra(const Shape& s, const float* ka, float2* spec, cudaStream_t st) {
   const size_t smem = (size_t)kFBuf * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(fft_spectra_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fft_spectra_kernel<<<s.n, kFThreads, smem, st>>>(f, s.K, spec);
+  fft_spectra_kernel<<<s.n * s.R2, kFThreads, smem, st>>>(ka, s.Kc, s.KP, spec);
   return cudaGetLastError();
 }
 

@@ -1,7 +1,8 @@
 """The FFT form of the forward model and adjoint (EMD_PREC_FFT_FP32) against
 the FP64 oracle: the same bars as the direct FP32 kernel (relative L2 1e-5
 after one iteration, 1e-4 after 50), on ragged shapes, masks, a delta PSF,
-the largest PSF footprint, and the full-size workload on sampled pixels."""
+the largest PSF footprint, super-resolution (r = 2, 3), and the full-size
+workloads on sampled pixels."""
 import numpy as np
 import pytest
 
@@ -71,23 +72,31 @@ def test_fft_parity_shapes(emd, H, W, n, K, mf):
     assert (x5 >= 0).all()
 
 
-def test_fft_needs_r_one(emd):
-    p = synth.make_problem("hsc", H=48, W=40, n=2, K=9, r=2, n_points=5, n_gal=1)
-    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
-    d.set_frames(p.y, p.v, p.f, p.mask)
-    with pytest.raises(emd.EMDError) as e:
-        d.set_precision(emd.EMD_PREC_FFT_FP32)
-    assert e.value.code == emd.EMD_EUNSUPPORTED
-    d.close()
+@pytest.mark.parametrize("H,W,n,K,r,mf", [(96, 80, 2, 15, 2, 0.05), (33, 47, 3, 21, 2, 0.0),
+                                          (40, 36, 2, 7, 3, 0.05), (130, 110, 2, 85, 2, 0.02)])
+def test_fft_parity_super_resolution(emd, H, W, n, K, r, mf):
+    """Eq. (3): the phases' spectra and the adjoint's accumulators go
+    through a per-tile scratch buffer."""
+    p = synth.make_problem("hsc", H=H, W=W, n=n, K=K, r=r, mask_frac=mf,
+                           fwhm=(1.5 * r, 3.0 * r), n_points=max(3, H * W // 400), n_gal=2)
+    g = np.random.default_rng(H + W)
+    x0 = (g.uniform(0.5, 1.5, (r * H, r * W)) * max(np.nanmean(p.y), 1.0) / r ** 2).astype(np.float32)
+    x1 = gpu_run(emd, p, x0, 1, emd.EMD_PREC_FFT_FP32)
+    assert rel_l2(x1, oracle_run(p, x0, 1)) <= 1e-5
+    x5 = gpu_run(emd, p, x0, 5, emd.EMD_PREC_FFT_FP32)
+    assert rel_l2(x5, oracle_run(p, x0, 5)) <= 2e-5
+    assert (x5 >= 0).all()
 
 
-def test_fft_full_size_sampled(emd):
-    """4096^2 x 33, 43 x 43 PSFs: one FFT iteration against the oracle's
-    single-pixel evaluation of Eq. (2) at sampled pixels (corners, tile
-    seams of the 86-pixel FFT tiles, random points), plus properties of the
-    whole image."""
-    p = synth.make_problem("hsc")
-    x0 = (np.random.default_rng(5).uniform(0.5, 1.5, (p.H, p.W)) * 10.0).astype(np.float32)
+@pytest.mark.parametrize("recipe", ["hsc", "sr2"])
+def test_fft_full_size_sampled(emd, recipe):
+    """4096^2 x 33, 43 x 43 PSFs (and 33 x 2048^2 exposures, 85 x 85 fine
+    PSFs, r = 2): one FFT iteration against the oracle's single-pixel
+    evaluation of Eq. (2) at sampled pixels (corners, tile seams of the
+    86-pixel FFT tiles, random points), plus properties of the whole image."""
+    p = synth.make_problem(recipe)
+    Hf, Wf = p.r * p.H, p.r * p.W
+    x0 = (np.random.default_rng(5).uniform(0.5, 1.5, (Hf, Wf)) * 10.0).astype(np.float32)
     d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
     d.set_frames(p.y, p.v, p.f, p.mask)
     d.set_precision(emd.EMD_PREC_FFT_FP32)
@@ -100,11 +109,12 @@ def test_fft_full_size_sampled(emd):
     assert np.isfinite(x1).all() and (x1 >= 0).all()
     assert ll1 >= ll0 - 1e-7 * abs(ll0)
     g = np.random.default_rng(17)
-    Bt = 128 - (p.K - 1)
-    pts = [(0, 0), (0, p.W - 1), (p.H - 1, 0), (p.H - 1, p.W - 1), (Bt - 1, Bt), (Bt, Bt - 1),
-           (2 * Bt, 3 * Bt - 1), (p.H - 2, p.W // 2)]
-    pts += [(int(a), int(b)) for a, b in zip(g.integers(0, p.H, 24), g.integers(0, p.W, 24))]
-    idx = np.array([a * p.W + b for a, b in pts], np.int64)
+    hc = ((p.K - 1) // 2 + p.r - 1) // p.r
+    Bt = p.r * (128 - 2 * hc)  # FFT tile seams on the latent grid
+    pts = [(0, 0), (0, Wf - 1), (Hf - 1, 0), (Hf - 1, Wf - 1), (Bt - 1, Bt), (Bt, Bt - 1),
+           (2 * Bt, 3 * Bt - 1), (Hf - 2, Wf // 2)]
+    pts += [(int(a), int(b)) for a, b in zip(g.integers(0, Hf, 24), g.integers(0, Wf, 24))]
+    idx = np.array([a * Wf + b for a, b in pts], np.int64)
     u, _ = oracle.weights(p.v, p.mask, p.y)
     xo, _, _ = oracle.em_step_at(x0, p.y, u, p.f, idx, p.r)
     got = x1.ravel()[idx].astype(np.float64)
