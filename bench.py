@@ -456,6 +456,9 @@ def run_ours(args):
             roofline["hbm_peak_source"] = hsrc
         if clocks.get("sm_mhz"):
             roofline["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ)
+        fma = emd.emd_measure_fma_rate()
+        roofline["fma_chain_measured_tflops"] = fma
+        roofline["frac_of_measured_fma"] = achieved / fma
     else:
         nprod = 3 if args.precision.startswith("split") else 1
         ex = tc_executed_flops(p.H, p.W, p.n, p.K, p.r, nprod) / launch_s / 1e12

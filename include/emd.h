@@ -313,6 +313,16 @@ int emd_fit_psf(const float *f, int n, int K, int r, const float *g, int Kg,
                 const float *h0, float lambda, float lr, int iters, float *h_out,
                 float *loss_out);
 
+/*
+ * emd_measure_fma_rate -- the FP32 FMA rate of the current GPU, measured:
+ * independent FMA chains in 8 blocks of 256 threads per SM, `iters` rounds
+ * of 128 FMAs per thread, one timed launch after a warm-up, on a private
+ * stream (blocks until done). *tflops = 2 x FMAs / s / 1e12. The paper has
+ * no counterpart: this is the denominator of the direct kernel's roofline.
+ * EMD_EINVAL for NULL tflops or iters < 1; EMD_ECUDA on CUDA failures.
+ */
+int emd_measure_fma_rate(int iters, double *tflops);
+
 #ifdef __cplusplus
 }
 #endif

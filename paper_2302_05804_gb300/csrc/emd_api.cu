@@ -13,6 +13,8 @@
 #include <vector>
 
 #include "emd_internal.cuh"
+#include "emd_tc.cuh"
+#include "emd_fft.cuh"
 
 using emd::Shape;
 

@@ -39,6 +39,7 @@
 #include <math.h>
 
 #include "emd_internal.cuh"
+#include "emd_fft.cuh"
 
 namespace emd {
 namespace {

@@ -119,62 +119,4 @@ cudaError_t launch_scatter_latent(const Shape& s, const float* nat, float* plane
 cudaError_t launch_gather_latent(const Shape& s, const float* planes, float* nat,
                                  cudaStream_t st);
 
-// ---- tensor-core path (emd_tc.cu) ----
-// FFT path (r = 1): overlap-save on 128 x 128 tiles
-struct FftLaunch {
-  const float* x;       // current iterate (padded plane)
-  float* xn;            // next iterate
-  const float* N;       // numerator
-  const float* u;       // n weight planes
-  float* w;             // n planes of u_t z_t (written by the forward pass)
-  const float2* spec;   // n R2 half spectra of the phase kernels, 65 columns x 128 rows each
-  float2* scratch;      // r > 1: per tile, R2 half spectra (x^ of the phases, then the
-                        // adjoint's accumulators); unused for r = 1
-};
-size_t fft_buffer_bytes(const Shape& s);
-size_t fft_smem_bytes();
-int fft_tile_side(const Shape& s);
-size_t fft_scratch_offset(const Shape& s);  // bytes before the scratch in the FFT buffer
-cudaError_t launch_fft_spectra(const Shape& s, const float* ka, float2* spec, cudaStream_t st);
-cudaError_t launch_fft_iter(const Shape& s, const FftLaunch& a, cudaStream_t st);
-
-struct TcShape {
-  int mode, fp16, nprod;
-  int TC;           // Den columns per CTA (64); Den rows per CTA = 128 (MMA M)
-  int Nf, Kf, Ka;   // forward N, forward K extent, adjoint K extent (= Nf)
-  int XRp, WRp;     // staged x-band rows and w rows (multiples of 8)
-  int Sf, Sa;       // Hankel core matrices per filter row (forward, adjoint)
-  int gxt, gyt;     // tiles
-  int stage_bytes;  // one ring stage (forward hi + lo)
-  int hank_block;   // bytes of the Hankel block of one (t, phi, a)
-  size_t smem;
-};
-
-struct TcLaunch {
-  const float* x;
-  float* xn;
-  const float* N;
-  float* Den;
-  const float* u;
-  uint16_t* xb;          // [2 ping-pong][2 hi/lo][R2] 16-bit planes
-  const uint16_t* hank;  // Hankel blocks
-  int pp;                // ping-pong slot of the current x
-  const float* scales;   // device {z, w, Den, x} scales (all 1 for BF16)
-  int write_xb;
-  int* err;
-};
-
-bool make_tc_shape(const Shape& s, int mode, TcShape* t, const char** why);
-size_t tc_buffer_bytes(const Shape& s, const TcShape& t);
-int make_x_tensormap(const Shape& s, const TcShape& t, void* xb, CUtensorMap* map);
-cudaError_t launch_build_hankel(const Shape& s, const TcShape& t, const float* kf, const float* ka,
-                                uint16_t* hank, float gscale, cudaStream_t st);
-cudaError_t launch_split_x(const Shape& s, const TcShape& t, const float* x, uint16_t* xb, int pp,
-                           const float* scales, cudaStream_t st);
-cudaError_t launch_max_nonneg(const float* v, long long count, unsigned int* out, cudaStream_t st);
-cudaError_t launch_fp16_scales(const unsigned int* xmax_bits, float gscale, float umax, float fsum,
-                               float* scales, cudaStream_t st);
-cudaError_t launch_tc_iter(const Shape& s, const TcShape& t, const TcLaunch& L,
-                           const CUtensorMap& map, cudaStream_t st);
-
 }  // namespace emd

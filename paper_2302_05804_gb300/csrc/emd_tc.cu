@@ -32,6 +32,7 @@
 #include <stdio.h>
 
 #include "emd_internal.cuh"
+#include "emd_tc.cuh"
 
 namespace emd {
 

@@ -41,6 +41,7 @@ EXPORTS = [
     "emd_batch_create", "emd_batch_destroy", "emd_batch_add", "emd_batch_remove",
     "emd_batch_step", "emd_batch_remaining", "emd_batch_sync", "emd_batch_config",
     "emd_selftest_wait_timeout", "emd_iterate_streaming", "emd_fit_psf", "emd_set_noise",
+    "emd_measure_fma_rate",
 ]
 
 
@@ -111,6 +112,8 @@ def load(build_if_missing: bool = False):
         lib.emd_fit_psf.restype = i
         lib.emd_set_noise.argtypes = [vp, i, C.c_double]
         lib.emd_set_noise.restype = i
+        lib.emd_measure_fma_rate.argtypes = [i, dp]
+        lib.emd_measure_fma_rate.restype = i
         for name in ("emd_batch_add", "emd_batch_remove", "emd_batch_step",
                      "emd_batch_remaining", "emd_batch_sync", "emd_batch_config"):
             getattr(lib, name).restype = i
@@ -255,6 +258,13 @@ def emd_fit_psf(f, g, r: int, lam: float, lr: float, iters: int, h0=None, h_out=
 def emd_selftest_wait_timeout(ctx, spins: int = 1000) -> int:
     """Returns the raw status (EMD_ETIMEOUT expected)."""
     return int(load().emd_selftest_wait_timeout(ctx, int(spins)))
+
+
+def emd_measure_fma_rate(iters: int = 20000) -> float:
+    """Measured FP32 FMA rate of the current GPU, TFLOP/s."""
+    out = C.c_double()
+    _check(load().emd_measure_fma_rate(int(iters), C.byref(out)))
+    return out.value
 
 
 def emd_set_noise(ctx, model: int, nu: float = 0.0) -> None:
