@@ -83,6 +83,11 @@ emd_ctx *emd_create(int H, int W, int n, int psf_k, int r);
 /* Device bytes a context of this shape holds (0 for invalid shapes). */
 size_t emd_ctx_bytes(int H, int W, int n, int psf_k, int r);
 
+/* The same plus the buffers emd_set_precision(mode) adds (the tensor-core
+ * operands, or the FFT form's spectra, w planes and scratch); 0 for an
+ * invalid shape or a mode this shape does not support. Host only. */
+size_t emd_ctx_bytes_precision(int H, int W, int n, int psf_k, int r, int mode);
+
 /* Destroy a context and free its device memory. NULL is ignored. */
 void emd_destroy(emd_ctx *ctx);
 

@@ -241,6 +241,19 @@ size_t emd_ctx_bytes(int H, int W, int n, int psf_k, int r) {
   return make_layout(s).total;
 }
 
+size_t emd_ctx_bytes_precision(int H, int W, int n, int psf_k, int r, int mode) {
+  Shape s;
+  const char* why = nullptr;
+  if (!emd::make_shape(H, W, n, psf_k, r, &s, &why)) return 0;
+  const size_t base = make_layout(s).total;
+  if (mode == EMD_PREC_FP32) return base;
+  if (mode == EMD_PREC_FFT_FP32) return base + emd::fft_buffer_bytes(s);
+  if (mode < EMD_PREC_FP32 || mode > EMD_PREC_FFT_FP32) return 0;
+  emd::TcShape t;
+  if (!emd::make_tc_shape(s, mode, &t, &why)) return 0;
+  return base + emd::tc_buffer_bytes(s, t);
+}
+
 emd_ctx* emd_create(int H, int W, int n, int psf_k, int r) {
   Shape s;
   const char* why = nullptr;
@@ -778,7 +791,14 @@ struct emd_batch {
   int max_clusters = 0;
   bool dirty = true;
   int njobs_table = 0;
-  // captured step graphs, one per cluster count
+  // FFT jobs: their own table, work list and counters (forward, adjoint)
+  emd::FftBatchJob* d_fjobs = nullptr;
+  int2* d_fitems = nullptr;
+  int* d_fnitems = nullptr;
+  int* d_fcounters = nullptr;
+  int fft_ctas = 0;
+  bool has_direct = false, has_fft = false;
+  // captured step graphs, one per (cluster count, parts present)
   std::map<int, cudaGraphExec_t> graphs;
   // autotuner: decision per composition, and the candidates still to try
   std::map<std::string, TuneChoice> tuned;
@@ -800,7 +820,7 @@ std::string composition_signature(emd_batch* b) {
     int sb = 0;
     for (int v = c->s.H > c->s.W ? c->s.H : c->s.W; v > 1; v >>= 1) ++sb;
     char buf[64];
-    snprintf(buf, sizeof(buf), "%d.%d.%d.%d", sb, c->s.Kc, c->s.r, (c->s.n + 7) / 8);
+    snprintf(buf, sizeof(buf), "%d.%d.%d.%d.%d", sb, c->s.Kc, c->s.r, (c->s.n + 7) / 8, c->prec);
     parts.push_back(buf);
   }
   std::sort(parts.begin(), parts.end());
@@ -811,13 +831,36 @@ std::string composition_signature(emd_batch* b) {
 
 int upload_table(emd_batch* b) {
   std::vector<emd::BatchJob> tab(b->job.size());
+  std::vector<emd::FftBatchJob> ftab(b->job.size());
   struct It { long long cost; int job, tile; };
   std::vector<It> its;
+  std::vector<int2> fitems;
   for (size_t i = 0; i < b->job.size(); ++i) {
     emd_ctx* c = b->job[i];
     emd::BatchJob& J = tab[i];
     memset(&J, 0, sizeof(J));
+    memset(&ftab[i], 0, sizeof(ftab[i]));
     if (!c) continue;
+    if (c->prec == EMD_PREC_FFT_FP32) {
+      emd::FftBatchJob& F = ftab[i];
+      F.s = c->s;
+      for (int k = 0; k < 2; ++k) {
+        emd::FftLaunch& L = F.a[k];
+        L.x = c->x[k];
+        L.xn = c->x[k ^ 1];
+        L.N = c->N;
+        L.u = c->u;
+        L.w = c->fft_w;
+        L.spec = c->fft_spec;
+        L.scratch = c->fft_scratch;
+      }
+      F.cur = c->cur;
+      F.remaining = b->remaining[i];
+      F.gxt = emd::fft_tiles_x(c->s);
+      if (F.remaining > 0)
+        for (int t = 0; t < emd::fft_tiles_total(c->s); ++t) fitems.push_back(make_int2((int)i, t));
+      continue;  // not in the direct table (remaining 0 there)
+    }
     J.s = c->s;
     for (int k = 0; k < 2; ++k) {
       const int save = c->cur;
@@ -831,7 +874,7 @@ int upload_table(emd_batch* b) {
     const long long cost = (long long)c->s.n * c->s.R2 * c->s.Kc * c->s.Kc;
     for (int t = 0; t < c->s.gx * c->s.gy; ++t) its.push_back({cost, (int)i, t});
   }
-  if (its.size() > (size_t)kBatchItemCap) {
+  if (its.size() > (size_t)kBatchItemCap || fitems.size() > (size_t)kBatchItemCap) {
     set_err("emd_batch_step: more than %d tiles in one step", kBatchItemCap);
     return EMD_EINVAL;
   }
@@ -845,21 +888,37 @@ int upload_table(emd_batch* b) {
   if (n) CK(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int2),
                             cudaMemcpyHostToDevice, b->st));
   CK(cudaMemcpyAsync(b->d_nitems, &n, sizeof(int), cudaMemcpyHostToDevice, b->st));
+  const int nf = (int)fitems.size();
+  CK(cudaMemcpyAsync(b->d_fjobs, ftab.data(), ftab.size() * sizeof(emd::FftBatchJob),
+                     cudaMemcpyHostToDevice, b->st));
+  if (nf) CK(cudaMemcpyAsync(b->d_fitems, fitems.data(), fitems.size() * sizeof(int2),
+                             cudaMemcpyHostToDevice, b->st));
+  CK(cudaMemcpyAsync(b->d_fnitems, &nf, sizeof(int), cudaMemcpyHostToDevice, b->st));
   CK(cudaStreamSynchronize(b->st));
   b->njobs_table = (int)tab.size();
+  b->has_direct = n > 0;
+  b->has_fft = nf > 0;
   return EMD_OK;
 }
 
 int get_graph(emd_batch* b, int clusters, cudaGraphExec_t* out) {
-  auto it = b->graphs.find(clusters);
+  // a step: the persistent direct kernel over the FP32 jobs' tiles, then the
+  // persistent FFT forward and adjoint kernels over the FFT jobs' tiles
+  const int key = clusters | (b->has_direct ? 1 << 20 : 0) | (b->has_fft ? 1 << 21 : 0);
+  auto it = b->graphs.find(key);
   if (it != b->graphs.end()) {
     *out = it->second;
     return EMD_OK;
   }
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = emd::launch_batch(b->d_jobs, b->max_jobs, b->d_items, b->d_nitems, b->d_counter,
-                                    b->d_err, clusters, b->smem, b->st);
+  cudaError_t e = cudaSuccess;
+  if (b->has_direct)
+    e = emd::launch_batch(b->d_jobs, b->max_jobs, b->d_items, b->d_nitems, b->d_counter, b->d_err,
+                          clusters, b->smem, b->st);
+  if (e == cudaSuccess && b->has_fft)
+    e = emd::launch_fft_batch(b->d_fjobs, b->max_jobs, b->d_fitems, b->d_fnitems, b->d_fcounters,
+                              b->fft_ctas, b->st);
   cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -873,7 +932,7 @@ int get_graph(emd_batch* b, int clusters, cudaGraphExec_t* out) {
     set_err("batch graph instantiate failed: %s", cudaGetErrorString(e));
     return EMD_ECUDA;
   }
-  b->graphs[clusters] = ex;
+  b->graphs[key] = ex;
   *out = ex;
   return EMD_OK;
 }
@@ -902,8 +961,10 @@ emd_batch* emd_batch_create(int max_jobs) {
   b->remaining.assign(max_jobs, 0);
   const size_t jb = (sizeof(emd::BatchJob) * max_jobs + 255) & ~(size_t)255;
   const size_t ib = (sizeof(int2) * (size_t)kBatchItemCap + 255) & ~(size_t)255;
+  const size_t fjb = (sizeof(emd::FftBatchJob) * max_jobs + 255) & ~(size_t)255;
+  const size_t total = jb + ib + 1024 + fjb + ib + 1024;
   void* p = nullptr;
-  if (cudaMalloc(&p, jb + ib + 1024) != cudaSuccess) {
+  if (cudaMalloc(&p, total) != cudaSuccess) {
     cudaGetLastError();
     set_err("emd_batch_create: out of device memory");
     delete b;
@@ -915,6 +976,17 @@ emd_batch* emd_batch_create(int max_jobs) {
   b->d_nitems = reinterpret_cast<int*>(b->arena + jb + ib);
   b->d_counter = reinterpret_cast<int*>(b->arena + jb + ib + 256);
   b->d_err = reinterpret_cast<int*>(b->arena + jb + ib + 512);
+  char* fa = b->arena + jb + ib + 1024;
+  b->d_fjobs = reinterpret_cast<emd::FftBatchJob*>(fa);
+  b->d_fitems = reinterpret_cast<int2*>(fa + fjb);
+  b->d_fnitems = reinterpret_cast<int*>(fa + fjb + ib);
+  b->d_fcounters = reinterpret_cast<int*>(fa + fjb + ib + 256);
+  {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->fft_ctas = sms > 0 ? sms : 1;  // one persistent FFT CTA per SM
+  }
   b->smem = emd::batch_smem_bytes();
   b->max_clusters = emd::batch_max_clusters(b->smem);
   if (b->max_clusters <= 0) {
@@ -932,7 +1004,7 @@ emd_batch* emd_batch_create(int max_jobs) {
   }
   b->own_stream = true;
   // zeroed on the batch's own stream, ahead of every table upload and step
-  if (cudaMemsetAsync(b->arena, 0, jb + ib + 1024, b->st) != cudaSuccess) {
+  if (cudaMemsetAsync(b->arena, 0, total, b->st) != cudaSuccess) {
     cudaGetLastError();
     set_err("emd_batch_create: memset failed");
     cudaStreamDestroy(b->st);
@@ -964,8 +1036,9 @@ int emd_batch_add(emd_batch* b, emd_ctx* c, int iterations) {
     set_err("emd_batch_add: iterations must be >= 0");
     return EMD_EINVAL;
   }
-  if (c->prec != EMD_PREC_FP32 || c->noise != EMD_NOISE_GAUSSIAN) {
-    set_err("emd_batch_add: batched jobs run the FP32 Gaussian-noise kernel");
+  if ((c->prec != EMD_PREC_FP32 && c->prec != EMD_PREC_FFT_FP32) ||
+      c->noise != EMD_NOISE_GAUSSIAN) {
+    set_err("emd_batch_add: batched jobs run the FP32 direct or FFT Gaussian-noise forms");
     return EMD_EUNSUPPORTED;
   }
   if (c->device != b->device) {
@@ -979,8 +1052,13 @@ int emd_batch_add(emd_batch* b, emd_ctx* c, int iterations) {
     }
   for (int i = 0; i < b->max_jobs; ++i) {
     if (!b->job[i]) {
-      // the job's own stream work (set_frames, set_x) must be done first
+      // the job's own stream work (set_frames, set_x, its PSF spectra) must
+      // be done first
       DeviceGuard dg(c->device);
+      if (c->prec == EMD_PREC_FFT_FP32 && !c->fft_ready) {
+        CK(emd::launch_fft_spectra(c->s, c->ka, c->fft_spec, c->st));
+        c->fft_ready = true;
+      }
       CK(cudaStreamSynchronize(c->st));
       b->job[i] = c;
       b->remaining[i] = iterations;

@@ -430,19 +430,18 @@ __device__ void c2r_2d_phase_sum(const float2* xs, const float2* kt, int R2, flo
   c2r_rows(dst, T);
 }
 
-__global__ void __launch_bounds__(kFThreads, 1)
-    fft_forward_kernel(const Shape s, const FftLaunch a) {
-  extern __shared__ float2 fsm[];
-  __shared__ TwTab T;
+// the forward pass of one tile (tile index `tile` = ty gx + tx of its job);
+// starts and ends at a CTA barrier, so a persistent CTA can run many
+__device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int tx, int tile,
+                                 float2* fsm, const TwTab& T) {
   float2* xh = fsm;
   float2* wk = fsm + kFBuf;
   float* stg = reinterpret_cast<float*>(fsm + 2 * kFBuf);  // 128 x 128 floats
   const Geom& g = s.g;
   const int hc = s.hc, B = kFT - 2 * hc, R2 = s.R2;
-  const int i0 = blockIdx.y * B, j0 = blockIdx.x * B;
+  const int i0 = ty * B, j0 = tx * B;
   const int per = kFT * kFBins;
-  float2* xs = a.scratch + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * R2 * per;
-  init_twiddles(T);
+  float2* xs = a.scratch + (long long)tile * R2 * per;
   SpecRegs kr;
   if (R2 == 1) {
     load_spec_cols(kr, a.spec);
@@ -490,6 +489,14 @@ __global__ void __launch_bounds__(kFThreads, 1)
     }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(kFThreads, 1)
+    fft_forward_kernel(const Shape s, const FftLaunch a) {
+  extern __shared__ float2 fsm[];
+  __shared__ TwTab T;
+  init_twiddles(T);
+  fft_forward_tile(s, a, blockIdx.y, blockIdx.x, blockIdx.y * gridDim.x + blockIdx.x, fsm, T);
 }
 
 // r > 1: acc_phi += FFT(buf) conj(k^_phi) for every phase, accumulators in
@@ -542,19 +549,18 @@ __device__ void update_phase(const float2* sh, const FftLaunch& a, const Geom& g
   }
 }
 
-__global__ void __launch_bounds__(kFThreads, 1)
-    fft_adjoint_kernel(const Shape s, const FftLaunch a) {
-  extern __shared__ float2 fsm[];
-  __shared__ TwTab T;
+// the adjoint pass and the update of one tile; starts and ends at a CTA
+// barrier
+__device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int tx, int tile,
+                                 float2* fsm, const TwTab& T) {
   float2* sh = fsm;
   float2* wk = fsm + kFBuf;
   float* stg = reinterpret_cast<float*>(fsm + 2 * kFBuf);  // 128 x 128 floats
   const Geom& g = s.g;
   const int hc = s.hc, B = kFT - 2 * hc, R2 = s.R2;
-  const int i0 = blockIdx.y * B, j0 = blockIdx.x * B;
+  const int i0 = ty * B, j0 = tx * B;
   const int per = kFT * kFBins;
-  float2* acc = a.scratch + (long long)(blockIdx.y * gridDim.x + blockIdx.x) * R2 * per;
-  init_twiddles(T);
+  float2* acc = a.scratch + (long long)tile * R2 * per;
   SpecRegs kr;
   if (R2 == 1) {
     for (int e = threadIdx.x; e < kFBuf; e += blockDim.x) sh[e] = make_float2(0.f, 0.f);
@@ -588,6 +594,70 @@ __global__ void __launch_bounds__(kFThreads, 1)
       update_phase(sh, a, g, (long long)ph * g.plane, i0, j0, B);
       __syncthreads();
     }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kFThreads, 1)
+    fft_adjoint_kernel(const Shape s, const FftLaunch a) {
+  extern __shared__ float2 fsm[];
+  __shared__ TwTab T;
+  init_twiddles(T);
+  fft_adjoint_tile(s, a, blockIdx.y, blockIdx.x, blockIdx.y * gridDim.x + blockIdx.x, fsm, T);
+}
+
+// Persistent forms for a batch of FFT jobs: every CTA claims (job, tile)
+// items from a device counter until the list is exhausted; jobs whose
+// iterations are done are skipped. One launch for the forward passes of all
+// jobs, then one for the adjoints (the adjoint reads its neighbours' w).
+__device__ __forceinline__ int claim_item(int* counter, int* slot) {
+  __syncthreads();  // the previous item's readers of *slot are done
+  if (threadIdx.x == 0) *slot = atomicAdd(counter, 1);
+  __syncthreads();
+  return *slot;
+}
+
+__global__ void __launch_bounds__(kFThreads, 1)
+    fft_batch_forward_kernel(const FftBatchJob* __restrict__ jobs, const int2* __restrict__ items,
+                             const int* __restrict__ n_items, int* __restrict__ counter) {
+  extern __shared__ float2 fsm[];
+  __shared__ TwTab T;
+  __shared__ int slot;
+  init_twiddles(T);
+  const int total = *n_items;
+  for (;;) {
+    const int item = claim_item(counter, &slot);
+    if (item >= total) break;
+    const int2 w = items[item];
+    const FftBatchJob& J = jobs[w.x];
+    if (J.remaining <= 0) continue;
+    fft_forward_tile(J.s, J.a[J.cur], w.y / J.gxt, w.y % J.gxt, w.y, fsm, T);
+  }
+}
+
+__global__ void __launch_bounds__(kFThreads, 1)
+    fft_batch_adjoint_kernel(const FftBatchJob* __restrict__ jobs, const int2* __restrict__ items,
+                             const int* __restrict__ n_items, int* __restrict__ counter) {
+  extern __shared__ float2 fsm[];
+  __shared__ TwTab T;
+  __shared__ int slot;
+  init_twiddles(T);
+  const int total = *n_items;
+  for (;;) {
+    const int item = claim_item(counter, &slot);
+    if (item >= total) break;
+    const int2 w = items[item];
+    const FftBatchJob& J = jobs[w.x];
+    if (J.remaining <= 0) continue;
+    fft_adjoint_tile(J.s, J.a[J.cur], w.y / J.gxt, w.y % J.gxt, w.y, fsm, T);
+  }
+}
+
+__global__ void fft_batch_advance_kernel(FftBatchJob* __restrict__ jobs, int njobs) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < njobs && jobs[j].remaining > 0) {
+    jobs[j].remaining -= 1;
+    jobs[j].cur ^= 1;
   }
 }
 
@@ -623,6 +693,34 @@ cudaError_t launch_fft_spectra(const Shape& s, const float* ka, float2* spec, cu
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   fft_spectra_kernel<<<s.n * s.R2, kFThreads, smem, st>>>(ka, s.Kc, s.KP, spec);
+  return cudaGetLastError();
+}
+
+int fft_tiles_x(const Shape& s) {
+  const int B = kFT - 2 * s.hc;
+  return (s.g.W + B - 1) / B;
+}
+
+int fft_tiles_total(const Shape& s) { return (int)fft_tiles(s); }
+
+cudaError_t launch_fft_batch(const FftBatchJob* jobs, int njobs, const int2* items,
+                             const int* n_items, int* counters, int ctas, cudaStream_t st) {
+  const size_t smem = fft_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(fft_batch_forward_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fft_batch_adjoint_kernel,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 2 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  fft_batch_forward_kernel<<<ctas, kFThreads, smem, st>>>(jobs, items, n_items, counters);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  fft_batch_adjoint_kernel<<<ctas, kFThreads, smem, st>>>(jobs, items, n_items, counters + 1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  fft_batch_advance_kernel<<<(njobs + 127) / 128, 128, 0, st>>>(const_cast<FftBatchJob*>(jobs),
+                                                                njobs);
   return cudaGetLastError();
 }
 

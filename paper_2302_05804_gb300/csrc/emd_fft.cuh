@@ -25,4 +25,17 @@ size_t fft_scratch_offset(const Shape& s);  // bytes before the scratch in the F
 cudaError_t launch_fft_spectra(const Shape& s, const float* ka, float2* spec, cudaStream_t st);
 cudaError_t launch_fft_iter(const Shape& s, const FftLaunch& a, cudaStream_t st);
 
+// batch of FFT jobs: persistent forward and adjoint kernels over (job, tile)
+struct FftBatchJob {
+  Shape s;
+  FftLaunch a[2];  // with x = buffer c, xn = buffer c^1, for c = cur
+  int cur;
+  int remaining;   // iterations still to run (0: skipped)
+  int gxt;         // FFT tiles per row
+};
+int fft_tiles_x(const Shape& s);
+int fft_tiles_total(const Shape& s);
+cudaError_t launch_fft_batch(const FftBatchJob* jobs, int njobs, const int2* items,
+                             const int* n_items, int* counters, int ctas, cudaStream_t st);
+
 }  // namespace emd

@@ -41,7 +41,7 @@ EXPORTS = [
     "emd_batch_create", "emd_batch_destroy", "emd_batch_add", "emd_batch_remove",
     "emd_batch_step", "emd_batch_remaining", "emd_batch_sync", "emd_batch_config",
     "emd_selftest_wait_timeout", "emd_iterate_streaming", "emd_fit_psf", "emd_set_noise",
-    "emd_measure_fma_rate",
+    "emd_measure_fma_rate", "emd_ctx_bytes_precision",
 ]
 
 
@@ -77,6 +77,8 @@ def load(build_if_missing: bool = False):
         lib.emd_create.argtypes = [i, i, i, i, i]
         lib.emd_create.restype = vp
         lib.emd_ctx_bytes.argtypes = [i, i, i, i, i]
+        lib.emd_ctx_bytes_precision.argtypes = [i, i, i, i, i, i]
+        lib.emd_ctx_bytes_precision.restype = C.c_size_t
         lib.emd_ctx_bytes.restype = C.c_size_t
         lib.emd_destroy.argtypes = [vp]
         lib.emd_destroy.restype = None
@@ -161,6 +163,10 @@ def emd_create(H: int, W: int, n: int, psf_k: int, r: int = 1) -> int:
 
 def emd_ctx_bytes(H: int, W: int, n: int, psf_k: int, r: int = 1) -> int:
     return int(load().emd_ctx_bytes(H, W, n, psf_k, r))
+
+
+def emd_ctx_bytes_precision(H: int, W: int, n: int, psf_k: int, r: int, mode: int) -> int:
+    return int(load().emd_ctx_bytes_precision(H, W, n, psf_k, r, int(mode)))
 
 
 def emd_destroy(ctx) -> None:

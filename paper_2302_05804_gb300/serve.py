@@ -1,7 +1,9 @@
 """Continuous-batching server for EM deconvolution jobs.
 
 Jobs (sky patches of uneven size, exposure count and PSF size) arrive over
-time. Each admitted job owns a library context (its x, y, u and PSFs stay
+time. Every job runs either the direct FP32 form (persistent direct kernel)
+or the FFT form (persistent FFT kernels of the same step), as the server is
+configured. Each admitted job owns a library context (its x, y, u and PSFs stay
 resident in device memory) and joins the running batch: every
 ``emd_batch_step`` advances ALL admitted jobs by one EM iteration in a
 single persistent-kernel launch (replayed from a CUDA graph). New jobs are
@@ -111,13 +113,15 @@ class Server:
     only while the HBM budget allows. The stepping thread adds ready jobs
     between steps, steps, and retires finished jobs (read back, freed)."""
 
-    def __init__(self, hbm_budget: float = 80e9, max_slots: int = 64, keep_results: bool = False):
+    def __init__(self, hbm_budget: float = 80e9, max_slots: int = 64, keep_results: bool = False,
+                 precision: int = 0):
         import threading
         import torch
         self.torch = torch
         self.budget = hbm_budget
         self.max_slots = max_slots
         self.keep = keep_results
+        self.precision = precision  # EMD_PREC_FP32 (direct) or EMD_PREC_FFT_FP32
         self.batch = emd.emd_batch_create(max_slots)
         self.used = 0
         self.lock = threading.Condition()
@@ -149,7 +153,8 @@ class Server:
                     delay = spec.arrival - self.now()
                     if delay > 0:
                         time.sleep(delay)
-                need = emd.emd_ctx_bytes(spec.H, spec.W, spec.n, spec.K, spec.r)
+                need = emd.emd_ctx_bytes_precision(spec.H, spec.W, spec.n, spec.K, spec.r,
+                                                   self.precision)
                 with self.lock:
                     # wait for memory and for a slot to be in sight (a job
                     # larger than the budget runs alone)
@@ -162,6 +167,8 @@ class Server:
                 ctx = emd.emd_create(spec.H, spec.W, spec.n, spec.K, spec.r)
                 emd.emd_set_stream(ctx, stream)
                 emd.emd_set_frames(ctx, data.y, data.v, data.f, data.mask)
+                if self.precision:
+                    emd.emd_set_precision(ctx, self.precision)
                 with self.lock:
                     self.ready.append(dict(spec=spec, ctx=ctx, bytes=need, stream=stream,
                                            prepared=self.now()))

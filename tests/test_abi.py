@@ -83,3 +83,14 @@ def test_fit_psf_rejects_bad_arguments_before_touching_the_gpu(lib):
         with pytest.raises(emd.EMDError) as e:
             emd.emd_fit_psf(f, g, r, lam, lr, it)
         assert e.value.code == emd.EMD_EINVAL
+
+
+def test_ctx_bytes_precision_host_only(lib):
+    from paper_2302_05804_gb300 import emd
+    base = emd.emd_ctx_bytes(4096, 4096, 33, 43, 1)
+    assert emd.emd_ctx_bytes_precision(4096, 4096, 33, 43, 1, emd.EMD_PREC_FP32) == base
+    fft = emd.emd_ctx_bytes_precision(4096, 4096, 33, 43, 1, emd.EMD_PREC_FFT_FP32)
+    assert base + 33 * 4096 * 4096 * 4 < fft < base + 33 * 4300 * 4300 * 4 + 10e6
+    assert emd.emd_ctx_bytes_precision(4096, 4096, 33, 43, 1, emd.EMD_PREC_SPLIT_BF16) > base
+    assert emd.emd_ctx_bytes_precision(256, 256, 4, 14, 1, emd.EMD_PREC_FFT_FP32) == 0
+    assert emd.emd_ctx_bytes_precision(256, 256, 4, 15, 1, 99) == 0

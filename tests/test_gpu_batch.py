@@ -80,3 +80,73 @@ def test_batch_remove_midway_keeps_reached_iterate():
     np.testing.assert_array_equal(x3, e.x())
     d.close(); e.close()
     emd.emd_batch_destroy(b)
+
+
+def test_mixed_direct_and_fft_batch_matches_solo_runs_bitwise():
+    """FFT-form jobs run in the persistent FFT kernels of the same step (one
+    forward launch and one adjoint launch over all their tiles); each job's
+    iterate equals its solo run (direct or FFT) bit for bit, including r = 2
+    and a job that joins mid-run."""
+    from paper_2302_05804_gb300 import emd
+    iters = [5, 4, 6, 3, 4]
+    forms = [emd.EMD_PREC_FFT_FP32, emd.EMD_PREC_FP32, emd.EMD_PREC_FFT_FP32,
+             emd.EMD_PREC_FFT_FP32, emd.EMD_PREC_FP32]
+    probs = [make(i) for i in range(len(JOBS))]
+
+    def ctx(i):
+        d = ctx_for(emd, probs[i])
+        d.set_precision(forms[i])
+        return d
+
+    solo = []
+    for i in range(len(probs)):
+        d = ctx(i)
+        d.iterate(iters[i])
+        solo.append(d.x())
+        d.close()
+    b = emd.emd_batch_create(8)
+    ds = [ctx(i) for i in range(len(probs))]
+    slots = {}
+    for i in range(4):
+        slots[i] = emd.emd_batch_add(b, ds[i].ctx, iters[i])
+    done, step = 0, 0
+    while done < len(probs):
+        if step == 1:
+            slots[4] = emd.emd_batch_add(b, ds[4].ctx, iters[4])
+        done += emd.emd_batch_step(b)
+        step += 1
+        assert step < 50
+    emd.emd_batch_sync(b)
+    for i in range(len(probs)):
+        assert emd.emd_batch_remaining(b, slots[i]) == 0
+        np.testing.assert_array_equal(ds[i].x(), solo[i])
+        emd.emd_batch_remove(b, slots[i])
+        ds[i].close()
+    emd.emd_batch_destroy(b)
+
+
+def test_fft_only_batch():
+    from paper_2302_05804_gb300 import emd
+    probs = [make(i) for i in (0, 3)]
+    solo = []
+    for p in probs:
+        d = ctx_for(emd, p)
+        d.set_precision(emd.EMD_PREC_FFT_FP32)
+        d.iterate(3)
+        solo.append(d.x())
+        d.close()
+    b = emd.emd_batch_create(4)
+    ds = []
+    for p in probs:
+        d = ctx_for(emd, p)
+        d.set_precision(emd.EMD_PREC_FFT_FP32)
+        ds.append(d)
+    sl = [emd.emd_batch_add(b, d.ctx, 3) for d in ds]
+    for _ in range(3):
+        emd.emd_batch_step(b)
+    emd.emd_batch_sync(b)
+    for d, s_, x in zip(ds, sl, solo):
+        np.testing.assert_array_equal(d.x(), x)
+        emd.emd_batch_remove(b, s_)
+        d.close()
+    emd.emd_batch_destroy(b)

@@ -9,14 +9,16 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-def test_served_results_equal_solo_results():
+@pytest.mark.parametrize("form", ["direct", "fft"])
+def test_served_results_equal_solo_results(form):
     from paper_2302_05804_gb300 import emd, serve
+    prec = emd.EMD_PREC_FFT_FP32 if form == "fft" else emd.EMD_PREC_FP32
     pool = serve.DataPool(synth.make_problem("hsc", H=640, W=640, n=6, mask_frac=0.05))
     trace = serve.poisson_trace(8, rate=200.0, seed=4004, s_range=(64, 300), n_range=(2, 6),
                                 k_range=(15, 43), iters=6)
     # a budget that holds only a few jobs at once forces queueing and reuse
-    budget = 3 * max(emd.emd_ctx_bytes(s.H, s.W, s.n, s.K, s.r) for s in trace)
-    srv = serve.Server(hbm_budget=budget, max_slots=4, keep_results=True)
+    budget = 3 * max(emd.emd_ctx_bytes_precision(s.H, s.W, s.n, s.K, s.r, prec) for s in trace)
+    srv = serve.Server(hbm_budget=budget, max_slots=4, keep_results=True, precision=prec)
     try:
         res = srv.run(trace, pool.make, realtime=True, time_limit=120)
     finally:
@@ -29,6 +31,7 @@ def test_served_results_equal_solo_results():
         d = pool.make(spec)
         solo = emd.Deconvolver(spec.H, spec.W, spec.n, spec.K, spec.r)
         solo.set_frames(d.y, d.v, d.f, d.mask)
+        solo.set_precision(prec)
         solo.iterate(spec.iters)
         np.testing.assert_array_equal(by_id[spec.jid].x, solo.x())
         solo.close()
