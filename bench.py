@@ -232,7 +232,7 @@ def run_reference(args):
     return 0
 
 
-def run_serving(p, args):
+def run_serving(p, args, precision=0):
     """Continuous-batching sample: jobs with sides log-uniform in [128, 2048],
     4-40 exposures, odd PSF sides 15-43, 50 iterations each, cut from the
     resident frame set; an 80 GB budget. First all jobs at t=0 (saturated
@@ -243,7 +243,7 @@ def run_serving(p, args):
     kw = dict(s_range=(128, min(2048, p.H)), n_range=(4, 40), k_range=(15, min(43, p.K)),
               iters=50)
     sat_trace = serve.poisson_trace(args.serve_jobs, rate=1e9, seed=4004, **kw)
-    srv = serve.Server(hbm_budget=80e9, max_slots=64)
+    srv = serve.Server(hbm_budget=80e9, max_slots=64, precision=precision)
     try:
         res = srv.run(sat_trace, pool.make, realtime=False)
     finally:
@@ -253,7 +253,7 @@ def run_serving(p, args):
     for frac in (0.5, 0.7, 0.9):
         rate_f = frac * sat["jobs_per_s"]
         trace_f = serve.poisson_trace(args.serve_jobs, rate=rate_f, seed=4005, **kw)
-        srv = serve.Server(hbm_budget=80e9, max_slots=64)
+        srv = serve.Server(hbm_budget=80e9, max_slots=64, precision=precision)
         try:
             res_f = srv.run(trace_f, pool.make, realtime=True)
         finally:
@@ -261,7 +261,8 @@ def run_serving(p, args):
         per_rate[frac] = (rate_f, trace_f, res_f, serve.Server.summary(res_f))
     rate, trace, res, live = per_rate[0.7]
     fma = sum(2.0 * s.n * s.H * s.W * s.K ** 2 * s.iters for s in trace)
-    return {"jobs": len(res), "saturated_jobs_per_s": sat["jobs_per_s"],
+    return {"form": "fft" if precision == 5 else "direct fp32",
+            "jobs": len(res), "saturated_jobs_per_s": sat["jobs_per_s"],
             "by_load": {f"{frac}x": {"arrival_rate_jobs_per_s": v[0], "p50_latency_s": v[3]["p50_s"],
                                      "p99_latency_s": v[3]["p99_s"], "jobs_per_s": v[3]["jobs_per_s"]}
                         for frac, v in per_rate.items()},
@@ -503,9 +504,10 @@ def run_ours(args):
                "step": "set_frames + iterations + loglik + get_x, host pinned buffers"}
     d.close()
 
-    serving = None
+    serving = serving_direct = None
     if args.serve_jobs > 0 and prec == 0:
-        serving = run_serving(p, args)
+        serving = run_serving(p, args, precision=5)
+        serving_direct = run_serving(p, args, precision=0)
     psf_fit = None
     if args.psf_iters > 0 and prec == 0:
         psf_fit = run_psf_fit(p, args.psf_iters)
@@ -531,7 +533,8 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": args.steps * LAUNCHES_PER_STEP[args.precision] * (2 if args.nu > 0 else 1),
             "clocks": clocks,
-            "serving": serving, "psf_fit": psf_fit, "variants": variants,
+            "serving": serving, "serving_direct_fp32": serving_direct, "psf_fit": psf_fit,
+            "variants": variants,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
