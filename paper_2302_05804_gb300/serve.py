@@ -107,14 +107,14 @@ class DataPool:
 class Server:
     """Admission + continuous batching over the library's batch API.
 
-    A preparation thread turns arrived requests into ready contexts
+    Preparation threads turn arrived requests into ready contexts
     (inputs cut, context created, frames uploaded on the job's own stream)
     while the stepping thread keeps the batch running; contexts are created
     only while the HBM budget allows. The stepping thread adds ready jobs
     between steps, steps, and retires finished jobs (read back, freed)."""
 
     def __init__(self, hbm_budget: float = 80e9, max_slots: int = 64, keep_results: bool = False,
-                 precision: int = 0):
+                 precision: int = 0, prep_threads: int = 4):
         import threading
         import torch
         self.torch = torch
@@ -122,6 +122,7 @@ class Server:
         self.max_slots = max_slots
         self.keep = keep_results
         self.precision = precision  # EMD_PREC_FP32 (direct) or EMD_PREC_FFT_FP32
+        self.prep_threads = max(1, prep_threads)
         self.batch = emd.emd_batch_create(max_slots)
         self.used = 0
         self.lock = threading.Condition()
@@ -145,10 +146,18 @@ class Server:
         emd.emd_batch_destroy(self.batch)
         self.batch = None
 
-    # -- preparation thread ---------------------------------------------------
-    def _prepare(self, trace, data_of, realtime):
+    # -- preparation threads ----------------------------------------------------
+    def _prepare(self, it, it_lock, data_of, realtime):
+        """One preparation worker: takes the next request in arrival order and
+        readies its context. Cutting the inputs, uploading them and creating
+        the device buffers take host time per job; several workers overlap
+        them (numpy copies and the library calls release the GIL)."""
         try:
-            for spec in trace:
+            while not self.error:
+                with it_lock:
+                    spec = next(it, None)
+                if spec is None:
+                    return
                 if realtime:
                     delay = spec.arrival - self.now()
                     if delay > 0:
@@ -170,8 +179,12 @@ class Server:
                 if self.precision:
                     emd.emd_set_precision(ctx, self.precision)
                 with self.lock:
-                    self.ready.append(dict(spec=spec, ctx=ctx, bytes=need, stream=stream,
-                                           prepared=self.now()))
+                    # ready jobs are admitted in arrival order
+                    rec = dict(spec=spec, ctx=ctx, bytes=need, stream=stream, prepared=self.now())
+                    k = len(self.ready)
+                    while k > 0 and self.ready[k - 1]["spec"].arrival > spec.arrival:
+                        k -= 1
+                    self.ready.insert(k, rec)
                     self.lock.notify_all()
         except Exception as e:  # surfaced by run()
             self.error = e
@@ -211,9 +224,11 @@ class Server:
         import threading
         self.t0 = time.perf_counter()
         total = len(trace)
-        prep = threading.Thread(target=self._prepare, args=(list(trace), data_of, realtime),
-                                daemon=True)
-        prep.start()
+        it, it_lock = iter(list(trace)), threading.Lock()
+        preps = [threading.Thread(target=self._prepare, args=(it, it_lock, data_of, realtime),
+                                  daemon=True) for _ in range(self.prep_threads)]
+        for t in preps:
+            t.start()
         while len(self.results) < total:
             if self.error:
                 raise self.error
@@ -228,7 +243,8 @@ class Server:
                         self.lock.wait(0.01)
             if time_limit and self.now() > time_limit:
                 break
-        prep.join(timeout=60)
+        for t in preps:
+            t.join(timeout=60)
         emd.emd_batch_sync(self.batch)
         if self.error:
             raise self.error
