@@ -282,7 +282,8 @@ def run_variants(p, steps=5, warmup=2):
     import torch
     from paper_2302_05804_gb300 import emd
     forms = [("fft", emd.EMD_PREC_FFT_FP32, 0.0), ("split_bf16", emd.EMD_PREC_SPLIT_BF16, 0.0),
-             ("bf16", emd.EMD_PREC_BF16, 0.0), ("student_t_nu3", emd.EMD_PREC_FP32, 3.0)]
+             ("bf16", emd.EMD_PREC_BF16, 0.0), ("student_t_nu3", emd.EMD_PREC_FP32, 3.0),
+             ("student_t_nu3_fft", emd.EMD_PREC_FFT_FP32, 3.0)]
     out = {}
     for name, prec, nu in forms:
         st = torch.cuda.Stream()
@@ -429,8 +430,11 @@ def run_ours(args):
         hc = ((p.K - 1) // 2 + p.r - 1) // p.r
         B = 128 - 2 * hc
         tiles = -(-p.H // B) * -(-p.W // B)
-        ffts = tiles * (2 * p.n + 2 * p.r * p.r)
-        fl = ffts * 2.5 * 16384 * 14 + tiles * 2 * p.n * p.r * p.r * 6 * 128 * 65
+        # forward: R2 + n transforms; adjoint: n + R2, or 2n + 2 R2 with the
+        # heavy-tailed numerator planes
+        m = 2 if args.nu > 0 else 1
+        ffts = tiles * ((1 + m) * (p.n + p.r * p.r))
+        fl = ffts * 2.5 * 16384 * 14 + tiles * (1 + m) * p.n * p.r * p.r * 6 * 128 * 65
         ex = fl / launch_s / 1e12
         roofline = {"bound": "alu", "achieved": ex, "peak": peak, "unit": "TFLOP/s",
                     "frac": ex / peak, "traffic": None,

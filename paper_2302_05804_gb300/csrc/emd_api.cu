@@ -97,8 +97,10 @@ struct emd_ctx {
   float* Ns = nullptr;  // heavy-tailed numerator (latent planes), allocated on first use
   // FFT path (allocated when EMD_PREC_FFT_FP32 is first selected)
   char* fft_arena = nullptr;
+  size_t fft_bytes = 0;
   float2* fft_spec = nullptr;
   float* fft_w = nullptr;
+  float* fft_w2 = nullptr;
   float2* fft_scratch = nullptr;
   bool fft_ready = false;
   bool frames = false;
@@ -247,7 +249,7 @@ size_t emd_ctx_bytes_precision(int H, int W, int n, int psf_k, int r, int mode) 
   if (!emd::make_shape(H, W, n, psf_k, r, &s, &why)) return 0;
   const size_t base = make_layout(s).total;
   if (mode == EMD_PREC_FP32) return base;
-  if (mode == EMD_PREC_FFT_FP32) return base + emd::fft_buffer_bytes(s);
+  if (mode == EMD_PREC_FFT_FP32) return base + emd::fft_buffer_bytes(s, false);
   if (mode < EMD_PREC_FP32 || mode > EMD_PREC_FFT_FP32) return 0;
   emd::TcShape t;
   if (!emd::make_tc_shape(s, mode, &t, &why)) return 0;
@@ -328,6 +330,43 @@ int emd_set_stream(emd_ctx* c, void* stream) {
   return EMD_OK;
 }
 
+namespace {
+
+// the FFT form's buffers, sized for the context's noise model (the
+// heavy-tailed form adds the w2 planes and a larger per-tile scratch);
+// a buffer that grows is re-made and its PSF spectra recomputed
+int ensure_fft_arena(emd_ctx* c) {
+  const bool student = c->noise == EMD_NOISE_STUDENT_T;
+  const size_t need = emd::fft_buffer_bytes(c->s, student);
+  if (c->fft_arena && c->fft_bytes >= need) return EMD_OK;
+  if (c->fft_arena) {
+    CK(cudaStreamSynchronize(c->st));
+    cudaFree(c->fft_arena);
+    c->fft_arena = nullptr;
+    c->fft_bytes = 0;
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, need) != cudaSuccess) {
+    cudaGetLastError();
+    set_err("cudaMalloc(%zu) for the FFT path failed", need);
+    return EMD_ENOMEM;
+  }
+  CK(cudaMemsetAsync(p, 0, need, c->st));
+  c->fft_arena = static_cast<char*>(p);
+  c->fft_bytes = need;
+  const size_t spec =
+      ((size_t)c->s.n * c->s.R2 * 128 * 65 * sizeof(float2) + 255) & ~(size_t)255;
+  c->fft_spec = reinterpret_cast<float2*>(c->fft_arena);
+  c->fft_w = reinterpret_cast<float*>(c->fft_arena + spec);
+  c->fft_w2 = student ? reinterpret_cast<float*>(c->fft_arena + emd::fft_w2_offset(c->s)) : nullptr;
+  c->fft_scratch =
+      reinterpret_cast<float2*>(c->fft_arena + emd::fft_scratch_offset(c->s, student));
+  c->fft_ready = false;
+  return EMD_OK;
+}
+
+}  // namespace
+
 int emd_set_precision(emd_ctx* c, int mode) {
   if (int rc = check_ctx(c, false)) return rc;
   if (mode == EMD_PREC_FP32) {
@@ -338,31 +377,15 @@ int emd_set_precision(emd_ctx* c, int mode) {
     set_err("unknown precision mode %d", mode);
     return EMD_EINVAL;
   }
-  if (c->noise != EMD_NOISE_GAUSSIAN) {
-    set_err("emd_set_precision: the heavy-tailed update runs on the FP32 kernel only");
-    return EMD_EUNSUPPORTED;
-  }
   DeviceGuard dg(c->device);
   if (mode == EMD_PREC_FFT_FP32) {
-    if (!c->fft_arena) {
-      const size_t need = emd::fft_buffer_bytes(c->s);
-      void* p = nullptr;
-      if (cudaMalloc(&p, need) != cudaSuccess) {
-        cudaGetLastError();
-        set_err("emd_set_precision: cudaMalloc(%zu) for the FFT path failed", need);
-        return EMD_ENOMEM;
-      }
-      CK(cudaMemsetAsync(p, 0, need, c->st));
-      c->fft_arena = static_cast<char*>(p);
-      const size_t spec = ((size_t)c->s.n * c->s.R2 * 128 * 65 * sizeof(float2) + 255) &
-                          ~(size_t)255;
-      c->fft_spec = reinterpret_cast<float2*>(c->fft_arena);
-      c->fft_w = reinterpret_cast<float*>(c->fft_arena + spec);
-      c->fft_scratch = reinterpret_cast<float2*>(c->fft_arena + emd::fft_scratch_offset(c->s));
-      c->fft_ready = false;
-    }
+    if (int rc = ensure_fft_arena(c)) return rc;
     c->prec = mode;
     return EMD_OK;
+  }
+  if (c->noise != EMD_NOISE_GAUSSIAN) {
+    set_err("emd_set_precision: the heavy-tailed update runs on the FP32 direct and FFT forms");
+    return EMD_EUNSUPPORTED;
   }
   emd::TcShape t;
   const char* why = nullptr;
@@ -493,6 +516,7 @@ int emd_iterate(emd_ctx* c, int k) {
   }
   DeviceGuard dg(c->device);
   if (c->prec == EMD_PREC_FFT_FP32 && k > 0) {
+    if (int rc = ensure_fft_arena(c)) return rc;  // grows if the noise model changed
     if (!c->fft_ready) {
       CK(emd::launch_fft_spectra(c->s, c->ka, c->fft_spec, c->st));
       c->fft_ready = true;
@@ -506,6 +530,11 @@ int emd_iterate(emd_ctx* c, int k) {
       L.w = c->fft_w;
       L.spec = c->fft_spec;
       L.scratch = c->fft_scratch;
+      if (c->noise == EMD_NOISE_STUDENT_T) {
+        L.y = c->y;
+        L.w2 = c->fft_w2;
+        L.nu = (float)c->nu;
+      }
       CK(emd::launch_fft_iter(c->s, L, c->st));
       c->cur ^= 1;
     }
@@ -610,8 +639,8 @@ int emd_set_noise(emd_ctx* c, int model, double nu) {
     set_err("emd_set_noise: nu must be finite and in (0, 1e30]");
     return EMD_EINVAL;
   }
-  if (c->prec != EMD_PREC_FP32) {
-    set_err("emd_set_noise: the heavy-tailed update runs on the FP32 kernel (set precision FP32)");
+  if (c->prec != EMD_PREC_FP32 && c->prec != EMD_PREC_FFT_FP32) {
+    set_err("emd_set_noise: the heavy-tailed update runs on the FP32 direct and FFT forms");
     return EMD_EUNSUPPORTED;
   }
   if (!c->Ns) {

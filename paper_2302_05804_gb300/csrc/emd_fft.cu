@@ -441,7 +441,8 @@ __device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int
   const int hc = s.hc, B = kFT - 2 * hc, R2 = s.R2;
   const int i0 = ty * B, j0 = tx * B;
   const int per = kFT * kFBins;
-  float2* xs = a.scratch + (long long)tile * R2 * per;
+  // this tile's scratch block (sized for the adjoint's accumulators)
+  float2* xs = a.scratch + (long long)tile * (a.nu > 0.f ? 2 * R2 : R2) * per;
   SpecRegs kr;
   if (R2 == 1) {
     load_spec_cols(kr, a.spec);
@@ -480,12 +481,30 @@ __device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int
     }
     cp_async_wait_all();
     __syncthreads();
-    for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
-      const int p = e / B, q = e - p * B;
-      const int i = i0 + p, j = j0 + q;
-      if (i < g.H && j < g.W)
-        a.w[tplane + (long long)(g.B + i) * g.P + g.B + j] =
-            stg[e] * (tile_at(wk, p + 2 * hc, q + 2 * hc) * kFScale);
+    if (a.nu > 0.f) {
+      // heavy-tailed weights u' = u (nu+1) / (nu + u (y - z)^2): both u' z
+      // (denominator) and u' y (numerator) go to planes
+      const float nu1 = a.nu + 1.f;
+      for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+        const int p = e / B, q = e - p * B;
+        const int i = i0 + p, j = j0 + q;
+        if (i < g.H && j < g.W) {
+          const long long gi = tplane + (long long)(g.B + i) * g.P + g.B + j;
+          const float z = tile_at(wk, p + 2 * hc, q + 2 * hc) * kFScale;
+          const float uv = stg[e], yv = a.y[gi], d = yv - z;
+          const float us = uv > 0.f ? uv * nu1 / fmaf(uv * d, d, a.nu) : 0.f;
+          a.w[gi] = us * z;
+          a.w2[gi] = us * yv;
+        }
+      }
+    } else {
+      for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+        const int p = e / B, q = e - p * B;
+        const int i = i0 + p, j = j0 + q;
+        if (i < g.H && j < g.W)
+          a.w[tplane + (long long)(g.B + i) * g.P + g.B + j] =
+              stg[e] * (tile_at(wk, p + 2 * hc, q + 2 * hc) * kFScale);
+      }
     }
     __syncthreads();
   }
@@ -522,9 +541,10 @@ __device__ void r2c_2d_accumulate_phases(float2* buf, float2* acc, const float2*
   __syncthreads();
 }
 
-// Den of one phase (in sh after the inverse transform) -> the update
-__device__ void update_phase(const float2* sh, const FftLaunch& a, const Geom& g, long long off,
-                             int i0, int j0, int B) {
+// Den of one phase (in sh after the inverse transform) -> the update; the
+// numerator is a.N, or (Student-t) the transformed tile num
+__device__ void update_phase(const float2* sh, const float2* num, const FftLaunch& a,
+                             const Geom& g, long long off, int i0, int j0, int B) {
   for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
     const int p = e / B, q = e - p * B;
     const int i = i0 + p, j = j0 + q;
@@ -532,13 +552,15 @@ __device__ void update_phase(const float2* sh, const FftLaunch& a, const Geom& g
       const long long gi = off + (long long)(g.B + i) * g.P + g.B + j;
       const float d = tile_at(sh, p, q) * kFScale;
       const float xo = a.x[gi], nraw = a.N[gi];
+      const float nt = num ? tile_at(num, p, q) * kFScale : nraw;
       float xv = xo;
       // The transform leaves a rounding floor (~1e-7 of the tile's weighted
       // model) where the exact denominator is 0; N, from the direct kernel,
       // is exactly 0 when no valid pixel lies in the footprint, which is
-      // then the sign of a zero denominator (x unchanged, as for Den = 0).
+      // then the sign of a zero denominator (x unchanged, as for Den = 0);
+      // with Student-t weights too, since u' = 0 exactly where u = 0.
       if (d > 0.f && nraw != 0.f) {
-        const float nv = fmaxf(nraw, 0.f);
+        const float nv = fmaxf(nt, 0.f);
         if (d < 1e-30f)  // denominator near zero: guarded ratio in FP64
           xv = (float)((double)xo * (double)nv / (double)d);
         else
@@ -550,7 +572,9 @@ __device__ void update_phase(const float2* sh, const FftLaunch& a, const Geom& g
 }
 
 // the adjoint pass and the update of one tile; starts and ends at a CTA
-// barrier
+// barrier. r = 1 Gaussian: one accumulator in shared memory. Otherwise the
+// accumulators live in the tile's scratch: R2 for Den, and for Student-t R2
+// more for N' (the w2 planes, transformed the same way).
 __device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int tx, int tile,
                                  float2* fsm, const TwTab& T) {
   float2* sh = fsm;
@@ -560,38 +584,51 @@ __device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int
   const int hc = s.hc, B = kFT - 2 * hc, R2 = s.R2;
   const int i0 = ty * B, j0 = tx * B;
   const int per = kFT * kFBins;
-  float2* acc = a.scratch + (long long)tile * R2 * per;
+  const bool student = a.nu > 0.f;
+  const bool in_smem = R2 == 1 && !student;
+  const int nacc = student ? 2 * R2 : R2;
+  float2* acc = a.scratch + (long long)tile * nacc * per;
+  // sources in order: w_0 (, w2_0), w_1 (, w2_1), ...
+  const int nsrc = student ? 2 * s.n : s.n;
+  auto src_plane = [&](int k) -> const float* {
+    return student ? ((k & 1) ? a.w2 : a.w) + (long long)(k >> 1) * g.plane
+                   : a.w + (long long)k * g.plane;
+  };
   SpecRegs kr;
-  if (R2 == 1) {
+  if (in_smem) {
     for (int e = threadIdx.x; e < kFBuf; e += blockDim.x) sh[e] = make_float2(0.f, 0.f);
     load_spec_cols(kr, a.spec);
   } else {
-    for (int e = threadIdx.x; e < R2 * per; e += blockDim.x) acc[e] = make_float2(0.f, 0.f);
+    for (int e = threadIdx.x; e < nacc * per; e += blockDim.x) acc[e] = make_float2(0.f, 0.f);
   }
-  region_async(stg, a.w, g, i0 - hc, j0 - hc);
-  for (int t = 0; t < s.n; ++t) {
+  region_async(stg, src_plane(0), g, i0 - hc, j0 - hc);
+  for (int k = 0; k < nsrc; ++k) {
     pack_region(wk, stg);
-    // the next exposure's region arrives during this transform
-    if (t + 1 < s.n) region_async(stg, a.w + (long long)(t + 1) * g.plane, g, i0 - hc, j0 - hc);
-    if (R2 == 1) {
+    // the next source's region arrives during this transform
+    if (k + 1 < nsrc) region_async(stg, src_plane(k + 1), g, i0 - hc, j0 - hc);
+    if (in_smem) {
       r2c_2d_accumulate(wk, sh, kr, T);
-      if (t + 1 < s.n) load_spec_cols(kr, a.spec + (long long)(t + 1) * per);
+      if (k + 1 < nsrc) load_spec_cols(kr, a.spec + (long long)(k + 1) * per);
     } else {
-      r2c_2d_accumulate_phases(wk, acc, a.spec + (long long)t * R2 * per, R2, T);
+      const int t = student ? k >> 1 : k, base = student ? (k & 1) * R2 : 0;
+      r2c_2d_accumulate_phases(wk, acc + (long long)base * per, a.spec + (long long)t * R2 * per,
+                               R2, T);
     }
   }
-  if (R2 == 1) {
+  if (in_smem) {
     c2r_2d(sh, T);
-    update_phase(sh, a, g, 0, i0, j0, B);
+    update_phase(sh, nullptr, a, g, 0, i0, j0, B);
   } else {
     for (int ph = 0; ph < R2; ++ph) {
       for (int e = threadIdx.x; e < per; e += blockDim.x) {
         const int m = e >> 7, rr = e & (kFT - 1);
         sh[rr * kFP + m] = acc[ph * per + e];
+        if (student) wk[rr * kFP + m] = acc[(R2 + ph) * per + e];
       }
       __syncthreads();
       c2r_2d(sh, T);
-      update_phase(sh, a, g, (long long)ph * g.plane, i0, j0, B);
+      if (student) c2r_2d(wk, T);
+      update_phase(sh, student ? wk : nullptr, a, g, (long long)ph * g.plane, i0, j0, B);
       __syncthreads();
     }
   }
@@ -668,18 +705,23 @@ static size_t fft_tiles(const Shape& s) {
   return (size_t)((s.g.W + B - 1) / B) * ((s.g.H + B - 1) / B);
 }
 
-// layout of the FFT buffer: PSF spectra (n R2), w planes (n), then for r > 1
-// the per-tile scratch (tiles R2 spectra)
-size_t fft_scratch_offset(const Shape& s) {
+// layout of the FFT buffer: PSF spectra (n R2), w planes (n), for Student-t
+// the w2 planes (n), then the per-tile scratch (r > 1: tiles R2 spectra;
+// Student-t: tiles 2 R2)
+size_t fft_w2_offset(const Shape& s) {
   const size_t spec = ((size_t)s.n * s.R2 * kFT * kFBins * sizeof(float2) + 255) & ~(size_t)255;
   const size_t wpl = ((size_t)s.n * s.g.plane * sizeof(float) + 255) & ~(size_t)255;
   return spec + wpl;
 }
 
-size_t fft_buffer_bytes(const Shape& s) {
-  const size_t scratch =
-      s.R2 > 1 ? fft_tiles(s) * s.R2 * kFT * kFBins * sizeof(float2) : 0;
-  return fft_scratch_offset(s) + scratch;
+size_t fft_scratch_offset(const Shape& s, bool student) {
+  const size_t wpl = ((size_t)s.n * s.g.plane * sizeof(float) + 255) & ~(size_t)255;
+  return fft_w2_offset(s) + (student ? wpl : 0);
+}
+
+size_t fft_buffer_bytes(const Shape& s, bool student) {
+  const int nacc = student ? 2 * s.R2 : (s.R2 > 1 ? s.R2 : 0);
+  return fft_scratch_offset(s, student) + fft_tiles(s) * nacc * kFT * kFBins * sizeof(float2);
 }
 
 // two transform buffers and a 128 x 128 float staging area

@@ -15,13 +15,18 @@ struct FftLaunch {
   const float* u;       // n weight planes
   float* w;             // n planes of u_t z_t (written by the forward pass)
   const float2* spec;   // n R2 half spectra of the phase kernels, 65 columns x 128 rows each
-  float2* scratch;      // r > 1: per tile, R2 half spectra (x^ of the phases, then the
-                        // adjoint's accumulators); unused for r = 1
+  float2* scratch;      // per tile (r > 1 or Student-t): R2 half spectra of the phases
+                        // of x, then the adjoint's accumulators (R2, or 2 R2 for
+                        // Student-t: Den then N'); unused for r = 1 Gaussian
+  const float* y;       // Student-t: n data planes (masked pixels 0)
+  float* w2;            // Student-t: n planes of u'_t y_t
+  float nu;             // Student-t degrees of freedom; 0 = Gaussian
 };
-size_t fft_buffer_bytes(const Shape& s);
+size_t fft_buffer_bytes(const Shape& s, bool student);
 size_t fft_smem_bytes();
 int fft_tile_side(const Shape& s);
-size_t fft_scratch_offset(const Shape& s);  // bytes before the scratch in the FFT buffer
+size_t fft_w2_offset(const Shape& s);                      // bytes before the w2 planes
+size_t fft_scratch_offset(const Shape& s, bool student);  // bytes before the scratch
 cudaError_t launch_fft_spectra(const Shape& s, const float* ka, float2* spec, cudaStream_t st);
 cudaError_t launch_fft_iter(const Shape& s, const FftLaunch& a, cudaStream_t st);
 

@@ -44,10 +44,12 @@ def start(p, seed=0):
     return (g.uniform(0.5, 1.5, (p.r * p.H, p.r * p.W)) * 20.0).astype(np.float32)
 
 
-def gpu_run(emd, p, x0, k, nu):
+def gpu_run(emd, p, x0, k, nu, prec=0):
     d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
     try:
         d.set_frames(p.y, p.v, p.f, p.mask)
+        if prec:
+            d.set_precision(prec)
         d.set_noise(emd.EMD_NOISE_STUDENT_T, nu)
         d.set_x(x0)
         d.iterate(k)
@@ -141,6 +143,8 @@ def test_student_guards(emd):
     with pytest.raises(emd.EMDError) as e:
         d.set_precision(emd.EMD_PREC_SPLIT_BF16)
     assert e.value.code == emd.EMD_EUNSUPPORTED
+    d.set_precision(emd.EMD_PREC_FFT_FP32)   # the FFT form takes heavy tails
+    d.set_precision(emd.EMD_PREC_FP32)
     with pytest.raises(emd.EMDError) as e:
         d.iterate_streaming(1)
     assert e.value.code == emd.EMD_EUNSUPPORTED
@@ -150,3 +154,43 @@ def test_student_guards(emd):
     assert e.value.code == emd.EMD_EUNSUPPORTED
     emd.emd_batch_destroy(b)
     d.close()
+
+
+@pytest.mark.parametrize("H,W,n,K,r,nu", [(200, 150, 3, 15, 1, 3.0), (130, 257, 2, 43, 1, 1.0),
+                                          (96, 80, 2, 15, 2, 5.0)])
+def test_student_parity_fft_form(emd, H, W, n, K, r, nu):
+    """The heavy-tailed update in the FFT form: the forward pass writes u'z
+    and u'y, the adjoint transforms both; same bars as the direct form."""
+    p = problem(H, W, n, K, r, seed=H + 1)
+    x0 = start(p, H + W + 1)
+    x1, _ = gpu_run(emd, p, x0, 1, nu, emd.EMD_PREC_FFT_FP32)
+    assert rel_l2(x1, oracle_run(p, x0, 1, nu)) <= 1e-5
+    x30, (ll, _) = gpu_run(emd, p, x0, 30, nu, emd.EMD_PREC_FFT_FP32)
+    xo = oracle_run(p, x0, 30, nu)
+    assert rel_l2(x30, xo) <= 1e-4
+    assert (x30 >= 0).all()
+
+
+def test_student_noise_set_after_the_fft_form(emd):
+    """Selecting the heavy-tailed model after the FFT form grows its buffers;
+    switching back to Gaussian gives the Gaussian FFT iterate bit for bit."""
+    p = problem(96, 100, 3, 15, 1, seed=21)
+    x0 = start(p, 4)
+
+    def run(order):
+        d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+        d.set_frames(p.y, p.v, p.f, p.mask)
+        d.set_precision(emd.EMD_PREC_FFT_FP32)
+        d.set_x(x0)
+        for model in order:
+            d.set_noise(model, 3.0)
+            d.iterate(2)
+        x = d.x()
+        d.close()
+        return x
+
+    g = run([emd.EMD_NOISE_GAUSSIAN, emd.EMD_NOISE_GAUSSIAN])
+    assert np.array_equal(g, run([emd.EMD_NOISE_GAUSSIAN, emd.EMD_NOISE_GAUSSIAN]))
+    xs = run([emd.EMD_NOISE_STUDENT_T, emd.EMD_NOISE_STUDENT_T])
+    xd, _ = gpu_run(emd, p, x0, 4, 3.0)
+    assert rel_l2(xs, xd) <= 2e-5
