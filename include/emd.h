@@ -175,8 +175,10 @@ int emd_set_precision(emd_ctx *ctx, int mode);
  *              - (nu+1)/2 log(1 + u (y - z)^2 / nu)]
  * and *chi2 = sum_valid (nu+1) log(1 + u (y - z)^2 / nu).
  * nu: finite, in (0, 1e30] (ignored for the Gaussian model). The heavy-tailed
- * model runs on the FP32 kernel only: EMD_EUNSUPPORTED with a tensor-core
- * precision, in emd_iterate_streaming and in emd_batch_add.
+ * model runs on the FP32 direct kernel and the FFT form (which then keeps n
+ * more exposure planes, of u'y, and a larger per-tile scratch, allocated at
+ * the next emd_set_precision or emd_iterate): EMD_EUNSUPPORTED with a
+ * tensor-core precision, in emd_iterate_streaming and in emd_batch_add.
  */
 enum emd_noise {
     EMD_NOISE_GAUSSIAN = 0,
