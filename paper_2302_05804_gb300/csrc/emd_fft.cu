@@ -289,10 +289,11 @@ __device__ void r2c_2d_accumulate(float2* buf, float2* acc, const SpecRegs& kr, 
   __syncthreads();
 }
 
-// inverse transform, rows: merge and 64 packed row inverse FFTs
-__device__ void c2r_rows(float2* buf, const TwTab& T) {
+// inverse transform, rows: merge and the packed row inverse FFTs of the row
+// pairs [k0, k1) (the rows a caller reads; the others are left undone)
+__device__ void c2r_rows(float2* buf, const TwTab& T, int k0 = 0, int k1 = 64) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = warp; k < 64; k += kWarps) {
+  for (int k = k0 + warp; k < k1; k += kWarps) {
     float2* r = buf + 2 * k * kFP;
     merge_pair(r, lane);
     float2 v[4];
@@ -305,8 +306,8 @@ __device__ void c2r_rows(float2* buf, const TwTab& T) {
   __syncthreads();
 }
 
-// inverse real 2D transform in place (unscaled)
-__device__ void c2r_2d(float2* buf, const TwTab& T) {
+// inverse real 2D transform in place (unscaled); rows of the pairs [k0, k1)
+__device__ void c2r_2d(float2* buf, const TwTab& T, int k0 = 0, int k1 = 64) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int m = warp; m < kFBins; m += kWarps) {
     float2 v[4];
@@ -317,12 +318,12 @@ __device__ void c2r_2d(float2* buf, const TwTab& T) {
     for (int q = 0; q < 4; ++q) buf[(32 * q + lane) * kFP + m] = v[q];
   }
   __syncthreads();
-  c2r_rows(buf, T);
+  c2r_rows(buf, T, k0, k1);
 }
 
-// dst = C2R(src . k^) (unscaled); src is left intact
+// dst = C2R(src . k^) (unscaled), rows of the pairs [k0, 64); src is left intact
 __device__ void c2r_2d_product(const float2* src, float2* dst, const SpecRegs& kr,
-                               const TwTab& T) {
+                               const TwTab& T, int k0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int c = 0; c < kColsPerWarp; ++c) {
@@ -337,7 +338,7 @@ __device__ void c2r_2d_product(const float2* src, float2* dst, const SpecRegs& k
     }
   }
   __syncthreads();
-  c2r_rows(dst, T);
+  c2r_rows(dst, T, k0, 64);
 }
 
 // value of tile pixel (P, Q) after c2r_2d (unscaled)
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
 // r > 1: dst = C2R(sum_phi x^_phi . k^_phi) with both spectra read from
 // global memory (x^ from this tile's scratch, L2-resident), column by column
 __device__ void c2r_2d_phase_sum(const float2* xs, const float2* kt, int R2, float2* dst,
-                                 const TwTab& T) {
+                                 const TwTab& T, int k0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per = kFT * kFBins;
   for (int m = warp; m < kFBins; m += kWarps) {
@@ -427,7 +428,7 @@ __device__ void c2r_2d_phase_sum(const float2* xs, const float2* kt, int R2, flo
     for (int q = 0; q < 4; ++q) dst[(32 * q + lane) * kFP + m] = v[q];
   }
   __syncthreads();
-  c2r_rows(dst, T);
+  c2r_rows(dst, T, k0, 64);
 }
 
 // the forward pass of one tile (tile index `tile` = ty gx + tx of its job);
@@ -473,11 +474,11 @@ __device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int
     }
     cp_async_commit();
     if (R2 == 1) {
-      c2r_2d_product(xh, wk, kr, T);
+      c2r_2d_product(xh, wk, kr, T, hc);  // z is read at rows [2 hc, 128)
       // the next spectrum loads during the epilogue and the next column pass
       if (t + 1 < s.n) load_spec_cols(kr, a.spec + (long long)(t + 1) * per);
     } else {
-      c2r_2d_phase_sum(xs, a.spec + (long long)t * R2 * per, R2, wk, T);
+      c2r_2d_phase_sum(xs, a.spec + (long long)t * R2 * per, R2, wk, T, hc);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -616,7 +617,7 @@ __device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int
     }
   }
   if (in_smem) {
-    c2r_2d(sh, T);
+    c2r_2d(sh, T, 0, (B + 1) / 2);  // Den is read at rows [0, B)
     update_phase(sh, nullptr, a, g, 0, i0, j0, B);
   } else {
     for (int ph = 0; ph < R2; ++ph) {
@@ -626,8 +627,8 @@ __device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int
         if (student) wk[rr * kFP + m] = acc[(R2 + ph) * per + e];
       }
       __syncthreads();
-      c2r_2d(sh, T);
-      if (student) c2r_2d(wk, T);
+      c2r_2d(sh, T, 0, (B + 1) / 2);
+      if (student) c2r_2d(wk, T, 0, (B + 1) / 2);
       update_phase(sh, student ? wk : nullptr, a, g, (long long)ph * g.plane, i0, j0, B);
       __syncthreads();
     }
