@@ -53,3 +53,27 @@ def test_full_size_one_iteration_sampled(recipe, k):
     err = np.abs(got - xo) / np.maximum(np.abs(xo), 1e-30)
     # per-pixel relative error; the L2 criterion of the iteration is 1e-5
     assert np.linalg.norm(got - xo) / np.linalg.norm(xo) <= 1e-5, err.max()
+
+
+@pytest.mark.parametrize("mode,tol", [(1, 5e-3), (2, 2e-3), (3, 1e-4), (4, 1e-4)])
+def test_full_size_tensor_core_forms_sampled(mode, tol):
+    """The tensor-core forms (BF16, FP16, split BF16, split FP16) at the size
+    the bench times them (4096^2 x 33, 43 x 43 PSFs): one iteration against
+    the oracle's single-pixel evaluation at sampled pixels, with the bars of
+    the smaller tensor-core parity cases (the operand rounding of each form)."""
+    from paper_2302_05804_gb300 import emd
+    p = synth.make_problem("hsc")
+    x0 = (np.random.default_rng(5).uniform(0.5, 1.5, (p.H, p.W)) * 10.0).astype(np.float32)
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    d.set_frames(p.y, p.v, p.f, p.mask)
+    d.set_precision(mode)
+    d.set_x(x0)
+    d.iterate(1)
+    x1 = d.x()
+    d.close()
+    assert np.isfinite(x1).all() and (x1 >= 0).all()
+    idx = sample_idx(p.H, p.W, 24, seed=13)
+    u, _ = oracle.weights(p.v, p.mask, p.y)
+    xo, _, _ = oracle.em_step_at(x0, p.y, u, p.f, idx, p.r)
+    got = x1.ravel()[idx].astype(np.float64)
+    assert np.linalg.norm(got - xo) / np.linalg.norm(xo) <= tol
