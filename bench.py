@@ -41,10 +41,18 @@ SM_MAX_MHZ = 2070.0
 # kernels one emd_iterate(ctx, 1) call launches: the fused kernel (FP32); the
 # x split + tensor-core kernel (BF16 modes); the x maximum, the power-of-two
 # scales, the split and the tensor-core kernel (FP16 modes)
-LAUNCHES_PER_STEP = {"fp32": 1, "bf16": 2, "split_bf16": 2, "fp16": 4, "split_fp16": 4,
-                     "fft": 2}
-KERNEL_SOURCES = ["paper_2302_05804_gb300/csrc/emd_direct.cu",
-                  "paper_2302_05804_gb300/csrc/emd_internal.cuh"]
+LAUNCHES_PER_STEP = {"fp32": 1, "fp32_pair": 1, "bf16": 2, "split_bf16": 2, "fp16": 4,
+                     "split_fp16": 4, "fft": 2}
+# sources whose change invalidates a committed DRAM-traffic record, per kernel
+KERNEL_SOURCES = {
+    "halo": ["paper_2302_05804_gb300/csrc/emd_halo.cu",
+             "paper_2302_05804_gb300/csrc/emd_halo.cuh",
+             "paper_2302_05804_gb300/csrc/emd_corr.cuh",
+             "paper_2302_05804_gb300/csrc/emd_internal.cuh"],
+    "fused": ["paper_2302_05804_gb300/csrc/emd_direct.cu",
+              "paper_2302_05804_gb300/csrc/emd_corr.cuh",
+              "paper_2302_05804_gb300/csrc/emd_internal.cuh"],
+}
 
 
 def dist_env():
@@ -91,22 +99,22 @@ def tc_executed_flops(H, W, n, K, r, nprod):
     return tiles * n * r * r * per
 
 
-def kernel_source_hash():
+def kernel_source_hash(kernel):
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, p), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def committed_traffic(workload):
-    """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary, or None when the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", f"fused_{workload}_traffic.json")
+def committed_traffic(kernel, workload):
+    """DRAM bytes per launch of a direct-form kernel ("halo" or "fused") from
+    the committed ncu summary, or None when its source changed since."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}_traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    if rec.get("source_hash") != kernel_source_hash():
+    if rec.get("source_hash") != kernel_source_hash(kernel):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -281,7 +289,8 @@ def run_variants(p, steps=5, warmup=2):
     its own context: CUDA events per iteration on the context's stream."""
     import torch
     from paper_2302_05804_gb300 import emd
-    forms = [("fft", emd.EMD_PREC_FFT_FP32, 0.0), ("split_bf16", emd.EMD_PREC_SPLIT_BF16, 0.0),
+    forms = [("fp32_pair", emd.EMD_PREC_FP32_PAIR, 0.0),
+             ("fft", emd.EMD_PREC_FFT_FP32, 0.0), ("split_bf16", emd.EMD_PREC_SPLIT_BF16, 0.0),
              ("bf16", emd.EMD_PREC_BF16, 0.0), ("student_t_nu3", emd.EMD_PREC_FP32, 3.0),
              ("student_t_nu3_fft", emd.EMD_PREC_FFT_FP32, 3.0)]
     out = {}
@@ -381,7 +390,7 @@ def run_ours(args):
     p = synth.make_problem(args.workload, **over)
     Hf, Wf = p.r * p.H, p.r * p.W
     prec = {"fp32": 0, "bf16": 1, "fp16": 2, "split_bf16": 3, "split_fp16": 4,
-            "fft": 5}[args.precision]
+            "fft": 5, "fp32_pair": 6}[args.precision]
 
     stream = torch.cuda.Stream()
     d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r, stream=stream)
@@ -442,12 +451,14 @@ def run_ours(args):
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                     "direct_equivalent_tflops": achieved,
                     "fft_tflop_per_iteration": fl / 1e12}
-    elif prec == 0:
+    elif prec in (0, 6):
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        traffic = committed_traffic(args.workload)
+        kern = "halo" if prec == 0 and args.nu == 0 else "fused"
+        traffic = committed_traffic(kern, args.workload)
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": traffic,
-                    "kernel": "fused_kernel (FP32 FMA)",
+                    "kernel": {"halo": "halo_kernel (FP32 FMA, persistent, w ring in L2)",
+                               "fused": "fused_kernel (FP32 FMA, CTA pairs)"}[kern],
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
         if traffic:
             hbm_peak, hsrc = 6800.0, "fallback 6.8 TB/s"
@@ -530,7 +541,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16": "bf16", "split_bf16": "bf16x3",
+            "dtype": {"fp32": "f32", "fp32_pair": "f32", "bf16": "bf16", "split_bf16": "bf16x3",
                       "fp16": "f16", "split_fp16": "f16x3", "fft": "f32"}[args.precision],
             "data": "synthetic",
             "config": config_of(args), "roofline": roofline, "cpu_baseline": cpu,
@@ -556,7 +567,8 @@ def main():
     ap.add_argument("--size", type=int, default=0,
                     help="override the exposure side (profiling of small cases)")
     ap.add_argument("--precision", default="fp32",
-                    choices=["fp32", "bf16", "fp16", "split_bf16", "split_fp16", "fft"])
+                    choices=["fp32", "fp32_pair", "bf16", "fp16", "split_bf16", "split_fp16",
+                             "fft"])
     ap.add_argument("--e2e-iters", type=int, default=10)
     ap.add_argument("--e2e-jobs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -63,7 +63,8 @@ enum emd_precision {
     EMD_PREC_FP16 = 2,        /* tensor cores, FP16 operands, FP32 accumulate */
     EMD_PREC_SPLIT_BF16 = 3,  /* tensor cores, hi+lo BF16 split, 3 products   */
     EMD_PREC_SPLIT_FP16 = 4,  /* tensor cores, hi+lo FP16 split, 3 products   */
-    EMD_PREC_FFT_FP32 = 5     /* FP32 FFTs, overlap-save on 128 x 128 tiles   */
+    EMD_PREC_FFT_FP32 = 5,    /* FP32 FFTs, overlap-save on 128 x 128 tiles   */
+    EMD_PREC_FP32_PAIR = 6    /* FP32 direct, per-tile CTA-pair kernel        */
 };
 
 /* Largest PSF footprint the direct kernels accept: with
@@ -83,8 +84,9 @@ emd_ctx *emd_create(int H, int W, int n, int psf_k, int r);
 /* Device bytes a context of this shape holds (0 for invalid shapes). */
 size_t emd_ctx_bytes(int H, int W, int n, int psf_k, int r);
 
-/* The same plus the buffers emd_set_precision(mode) adds (the tensor-core
- * operands, or the FFT form's spectra, w planes and scratch); 0 for an
+/* The same plus the buffers the mode adds (EMD_PREC_FP32: the w ring of
+ * the halo-exchange kernel; the tensor-core operands; the FFT form's
+ * spectra, w planes and scratch; nothing for EMD_PREC_FP32_PAIR); 0 for an
  * invalid shape or a mode this shape does not support. Host only. */
 size_t emd_ctx_bytes_precision(int H, int W, int n, int psf_k, int r, int mode);
 
@@ -154,8 +156,18 @@ int emd_loglik(emd_ctx *ctx, double *out, double *chi2);
  * of the polyphase planes); it needs n extra exposure planes of device
  * memory for the weighted model images u_t z_t and, for r > 1, a per-tile
  * scratch of r^2 spectra (66.5 KB each), allocated on first selection.
- * emd_loglik and emd_iterate_streaming use the direct FP32 kernel in every
- * mode. */
+ * EMD_PREC_FP32 (Gaussian noise) runs one persistent kernel per iteration
+ * that computes each pixel's forward model once and passes the weighted
+ * model images u_t z_t between 128 x 128 tiles through a ring of tile
+ * buffers in device memory (about 550 tiles of 64 KB at 4096^2, fewer for
+ * smaller images; emd_ctx_bytes_precision counts them), allocated at the
+ * first such iteration. EMD_PREC_FP32_PAIR gives the same iterates bit for
+ * bit from the kernel that keeps u_t z_t in the shared memory of a CTA
+ * pair per tile and recomputes the forward model on a 2 hc halo around it
+ * (no extra memory, 1.48x the multiply-adds at K = 43); the heavy-tailed
+ * model, emd_loglik, emd_iterate_streaming and batched jobs always run that
+ * kernel in the FP32 modes, and emd_loglik and emd_iterate_streaming in
+ * every mode. */
 int emd_set_precision(emd_ctx *ctx, int mode);
 
 /*

@@ -15,6 +15,7 @@
 #include "emd_internal.cuh"
 #include "emd_tc.cuh"
 #include "emd_fft.cuh"
+#include "emd_halo.cuh"
 
 using emd::Shape;
 
@@ -119,6 +120,10 @@ struct emd_ctx {
   // streaming EM: per-exposure numerators (allocated on first use)
   float* Nt = nullptr;
   bool nt_ready = false;
+  // halo-exchange form of the FP32 direct iteration: w ring, flags and
+  // counters (allocated on the first FP32 direct iteration; zeroed)
+  char* halo_arena = nullptr;
+  emd::HaloLaunch halo{};
 };
 
 namespace {
@@ -248,7 +253,8 @@ size_t emd_ctx_bytes_precision(int H, int W, int n, int psf_k, int r, int mode) 
   const char* why = nullptr;
   if (!emd::make_shape(H, W, n, psf_k, r, &s, &why)) return 0;
   const size_t base = make_layout(s).total;
-  if (mode == EMD_PREC_FP32) return base;
+  if (mode == EMD_PREC_FP32) return base + emd::halo_buffer_bytes(s);
+  if (mode == EMD_PREC_FP32_PAIR) return base;
   if (mode == EMD_PREC_FFT_FP32) return base + emd::fft_buffer_bytes(s, false);
   if (mode < EMD_PREC_FP32 || mode > EMD_PREC_FFT_FP32) return 0;
   emd::TcShape t;
@@ -313,6 +319,7 @@ void emd_destroy(emd_ctx* c) {
   if (c->Nt) cudaFree(c->Nt);
   if (c->Ns) cudaFree(c->Ns);
   if (c->fft_arena) cudaFree(c->fft_arena);
+  if (c->halo_arena) cudaFree(c->halo_arena);
   delete c;
 }
 
@@ -365,11 +372,34 @@ int ensure_fft_arena(emd_ctx* c) {
   return EMD_OK;
 }
 
+// The halo-exchange iteration's ring, flags and counters; false (no error)
+// when the shape has too many work items for it (the CTA-pair kernel runs).
+int ensure_halo_arena(emd_ctx* c, bool* ok) {
+  *ok = false;
+  if (c->halo_arena) {
+    *ok = true;
+    return EMD_OK;
+  }
+  const size_t need = emd::halo_buffer_bytes(c->s);
+  if (need == 0) return EMD_OK;
+  void* p = nullptr;
+  if (cudaMalloc(&p, need) != cudaSuccess) {
+    cudaGetLastError();
+    set_err("cudaMalloc(%zu) for the FP32 direct iteration failed", need);
+    return EMD_ENOMEM;
+  }
+  CK(cudaMemsetAsync(p, 0, need, c->st));  // flags and counters start at zero
+  c->halo_arena = static_cast<char*>(p);
+  emd::halo_bind(c->s, p, &c->halo);
+  *ok = true;
+  return EMD_OK;
+}
+
 }  // namespace
 
 int emd_set_precision(emd_ctx* c, int mode) {
   if (int rc = check_ctx(c, false)) return rc;
-  if (mode == EMD_PREC_FP32) {
+  if (mode == EMD_PREC_FP32 || mode == EMD_PREC_FP32_PAIR) {
     c->prec = mode;
     return EMD_OK;
   }
@@ -540,7 +570,7 @@ int emd_iterate(emd_ctx* c, int k) {
     }
     return EMD_OK;
   }
-  if (c->prec != EMD_PREC_FP32 && k > 0) {
+  if (c->prec != EMD_PREC_FP32 && c->prec != EMD_PREC_FP32_PAIR && k > 0) {
     // tensor-core path: 16-bit operands of the PSFs (once per frame set) and
     // of the current x, then one kernel launch per iteration
     const bool fp16 = c->ts.fp16 != 0;
@@ -616,9 +646,18 @@ int emd_iterate(emd_ctx* c, int k) {
     }
     return EMD_OK;
   }
+  bool halo = false;
+  if (c->prec == EMD_PREC_FP32 && k > 0)
+    if (int rc = ensure_halo_arena(c, &halo)) return rc;
   for (int it = 0; it < k; ++it) {
     emd::FusedArgs a = fused_args(c);
-    CK(emd::launch_fused(c->s, a, 0, c->part, c->st));
+    if (halo) {
+      emd::HaloLaunch h = c->halo;
+      h.a = a;
+      CK(emd::launch_halo_iter(c->s, h, c->st));
+    } else {
+      CK(emd::launch_fused(c->s, a, 0, c->part, c->st));
+    }
     c->cur ^= 1;
   }
   return EMD_OK;
@@ -639,7 +678,8 @@ int emd_set_noise(emd_ctx* c, int model, double nu) {
     set_err("emd_set_noise: nu must be finite and in (0, 1e30]");
     return EMD_EINVAL;
   }
-  if (c->prec != EMD_PREC_FP32 && c->prec != EMD_PREC_FFT_FP32) {
+  if (c->prec != EMD_PREC_FP32 && c->prec != EMD_PREC_FP32_PAIR &&
+      c->prec != EMD_PREC_FFT_FP32) {
     set_err("emd_set_noise: the heavy-tailed update runs on the FP32 direct and FFT forms");
     return EMD_EUNSUPPORTED;
   }
@@ -1065,7 +1105,8 @@ int emd_batch_add(emd_batch* b, emd_ctx* c, int iterations) {
     set_err("emd_batch_add: iterations must be >= 0");
     return EMD_EINVAL;
   }
-  if ((c->prec != EMD_PREC_FP32 && c->prec != EMD_PREC_FFT_FP32) ||
+  if ((c->prec != EMD_PREC_FP32 && c->prec != EMD_PREC_FP32_PAIR &&
+       c->prec != EMD_PREC_FFT_FP32) ||
       c->noise != EMD_NOISE_GAUSSIAN) {
     set_err("emd_batch_add: batched jobs run the FP32 direct or FFT Gaussian-noise forms");
     return EMD_EUNSUPPORTED;

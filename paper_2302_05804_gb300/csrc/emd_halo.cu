@@ -1,0 +1,419 @@
+// emd_halo.cu -- the FP32 direct EM iteration of Sec. 2, Eq. (2) (Eq. (3)
+// for r > 1) as one persistent kernel over two kinds of work items:
+//
+//   forward item (t, tile)   w_t = u_t . (F_t x) on the 128 x 128 tile,
+//                            stored in one slot of a ring of tile buffers
+//   adjoint item (t, tile)   Den += F_t^T w_t on the tile, reading w_t of the
+//                            tile and of its 8 neighbours from the ring; the
+//                            last exposure applies the update of Eq. (2)
+//
+// Every forward pixel is computed once. The CTA-pair kernel of
+// emd_direct.cu keeps w in shared memory instead and so recomputes a 2*hc
+// halo around each tile (176^2 forward outputs per 128^2 tile at K = 43:
+// 1.48x the algorithmic FMAs overall against 1.0x here). What this costs is
+// w passing through global memory: a ring of R tile buffers (about 550 at
+// 4096^2, 36 MB), written and read again within a few hundred items, so it
+// stays in L2; no per-exposure image is kept.
+//
+// Item order. One atomic counter hands out a fixed sequence: the first L
+// forward items, then adjoint and forward items alternately, then the last
+// L adjoint items (adjoint item a is claimed just before forward item
+// a + L). Ids count exposure-major: id = e * T + tile, e = t - t0. Waits:
+//   adjoint (e, k) needs the forward items (e, k') of its 3 x 3 neighbours
+//     (id distance <= dmax < L, so claimed earlier) and adjoint (e-1, k)
+//     (Den is read-modify-written in exposure order);
+//   forward f reuses ring slot f mod R, written last by forward f - R; it
+//     needs the adjoint items that read that tile done, ids <= f - R + dmax,
+//     claimed earlier because R > L + dmax.
+// A CTA only ever waits on an item claimed before its own, held by a running
+// CTA, so the kernel completes with any number of co-resident CTAs. Each
+// wait is bounded; one that gives up raises an abort flag that ends every
+// later wait at once, and the host sees EMD_ETIMEOUT through the error word.
+//
+// The arithmetic (tap order of each output, w = u z, Den + sum, the guarded
+// ratio) is the CTA-pair kernel's, so both give bit-identical iterates.
+#include "emd_corr.cuh"
+#include "emd_halo.cuh"
+
+namespace emd {
+
+namespace {
+
+constexpr int kTileFloats = kTile * kTile;
+constexpr int kHaloCtasMax = 160;      // grid cap (>= SMs of one GB300); sizes the ring
+constexpr uint32_t kPollLimit = 1u << 23;  // x ~0.3 us per poll: seconds, not a hang
+constexpr int kGather = 8;             // 16-byte loads in flight per thread while staging
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct HaloShape {
+  int rows;   // staged rows: kTile + 2 hc
+  int cols;   // staged columns: kTile + KP
+  int pitch;  // floats per staged row; rows also carry a skew of 4 floats every 4 rows
+  int buf;    // floats of the staged window
+  int ks;     // floats of one Kc x KP kernel
+};
+
+__host__ __device__ inline HaloShape halo_shape(const Shape& s) {
+  HaloShape h;
+  h.rows = kTile + 2 * s.hc;
+  h.cols = kTile + s.KP;
+  h.pitch = h.cols;  // a multiple of 4: rows start 16-byte aligned; even: the
+                     // 8 lanes of a load phase (rows 4 apart) hit distinct bank groups
+  h.buf = h.rows * h.pitch + 4 * ((h.rows + 3) >> 2);
+  h.ks = s.Kc * s.KP;
+  return h;
+}
+
+size_t halo_smem_bytes(const Shape& s) {
+  const HaloShape h = halo_shape(s);
+  return (size_t)(h.buf + h.ks) * sizeof(float);
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait for *p >= v. Gives up after kPollLimit polls (raising the
+// abort flag ctrl[2]) or at once when another CTA has already given up.
+__device__ bool wait_geq(const int* p, int v, unsigned long long* ctrl) {
+  const volatile unsigned long long* abort_flag = ctrl + 2;
+  for (uint32_t i = 0; i < kPollLimit; ++i) {
+    if (ld_acquire(p) >= v) return true;
+    if (*abort_flag) return false;
+    __nanosleep(200);
+  }
+  atomicExch(ctrl + 2, 1ull);
+  return false;
+}
+
+// Writes the four floats of v (image/plane columns col0 .. col0+3) into the
+// staged row, skipping columns outside [0, cols).
+__device__ __forceinline__ void put4(float* row, int C, int cols, const float4 v) {
+  if (C >= 0 && C + 3 < cols) {
+    row[C] = v.x;
+    row[C + 1] = v.y;
+    row[C + 2] = v.z;
+    row[C + 3] = v.w;
+  } else {
+    if (C >= 0 && C < cols) row[C] = v.x;
+    if (C + 1 >= 0 && C + 1 < cols) row[C + 1] = v.y;
+    if (C + 2 >= 0 && C + 2 < cols) row[C + 2] = v.z;
+    if (C + 3 >= 0 && C + 3 < cols) row[C + 3] = v.w;
+  }
+}
+
+// Forward item: the x window of rows [i0 - hc, i0 + 128 + hc) and columns
+// [j0 - hc, j0 - hc + cols) of one padded latent plane (read-only during
+// the launch), through 16-byte loads on the plane's 16-byte grid.
+__device__ void gather_plane(const Shape& s, const HaloShape& hs, const SPlane& sp,
+                             const float* __restrict__ plane, int i0, int j0) {
+  const int c0 = j0 + s.hc;  // padded column of window column 0 (border B = 2 hc)
+  const int q0 = c0 >> 2;
+  const int nq = ((c0 + hs.cols - 1) >> 2) - q0 + 1;
+  const int total = hs.rows * nq;
+  const float* base = plane + (long long)(i0 + s.hc) * s.g.P;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kThreads * kGather) {
+    float4 v[kGather];
+#pragma unroll
+    for (int q = 0; q < kGather; ++q) {
+      const int e = e0 + q * kThreads;
+      if (e < total) {
+        const int R = e / nq, m = e - R * nq;
+        v[q] = __ldg(reinterpret_cast<const float4*>(base + (long long)R * s.g.P + ((q0 + m) << 2)));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kGather; ++q) {
+      const int e = e0 + q * kThreads;
+      if (e < total) {
+        const int R = e / nq, m = e - R * nq;
+        put4(srow(sp, R), ((q0 + m) << 2) - c0, hs.cols, v[q]);
+      }
+    }
+  }
+}
+
+// Adjoint item: the w window of rows [i0 - hc, i0 + 128 + hc) and columns
+// [j0 - hc, j0 - hc + cols) from the ring slots of the tile and its
+// neighbours (nb[3 * (dy + 1) + (dx + 1)], null outside the tile grid: w = 0
+// there). Tile origins are multiples of 128, so the 16-byte image-column
+// grid is each slot's own. Loads bypass L1 (the slots are rewritten by
+// other SMs during the launch).
+__device__ void gather_ring(const HaloShape& hs, const SPlane& sp, const float* const* nb,
+                            int hc, int i0, int j0) {
+  const int c0 = j0 - hc;   // image column of window column 0
+  const int q0 = c0 >> 2;   // floor
+  const int nq = ((c0 + hs.cols - 1) >> 2) - q0 + 1;
+  const int total = hs.rows * nq;
+  const int ti = i0 >> 7, tj = j0 >> 7;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kThreads * kGather) {
+    float4 v[kGather];
+#pragma unroll
+    for (int q = 0; q < kGather; ++q) {
+      const int e = e0 + q * kThreads;
+      v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (e < total) {
+        const int R = e / nq, m = e - R * nq;
+        const int ii = i0 - hc + R, cc = (q0 + m) << 2;
+        const int tr = ii >> 7, tc = cc >> 7;  // floor: neighbour tile row / column
+        const float* src = nb[3 * (tr - ti + 1) + (tc - tj + 1)];
+        if (src)
+          v[q] = __ldcg(reinterpret_cast<const float4*>(src + (ii - (tr << 7)) * kTile +
+                                                         (cc - (tc << 7))));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kGather; ++q) {
+      const int e = e0 + q * kThreads;
+      if (e < total) {
+        const int R = e / nq, m = e - R * nq;
+        put4(srow(sp, R), ((q0 + m) << 2) - c0, hs.cols, v[q]);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    halo_kernel(const Shape s, const HaloLaunch h, const HaloPlan pl) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ long long item_s;
+  __shared__ const float* nb_s[9];
+  __shared__ int last_s;
+  const FusedArgs& a = h.a;
+  const Geom& g = s.g;
+  const HaloShape hs = halo_shape(s);
+  const SPlane sp{smem, hs.pitch, 2};
+  float* ks = smem + hs.buf;
+  const int tid = threadIdx.x;
+  const int my = tid & 31, mx = tid >> 5;  // this thread's 4 x 16 outputs: rows 4 my, cols 16 mx
+  const int T = pl.T;
+  const long long NT = pl.NT, L = pl.L, RS = pl.R;
+  const int ne = a.t1 - a.t0;
+  const int kq = hs.ks >> 2;
+  bool timed_out = false;
+
+  for (;;) {
+    __syncthreads();  // readers of the previous item's window, kernel and item id are done
+    if (tid == 0) item_s = (long long)atomicAdd(&h.ctrl[0], 1ull);
+    __syncthreads();
+    const long long sq = item_s;
+    if (sq >= 2 * NT) break;
+    bool fwd;
+    long long id;
+    if (sq < L) {
+      fwd = true;
+      id = sq;
+    } else if (sq < 2 * NT - L) {
+      const long long j = sq - L;
+      fwd = (j & 1) != 0;
+      id = fwd ? L + (j >> 1) : (j >> 1);
+    } else {
+      fwd = false;
+      id = sq - NT;
+    }
+    const int e = (int)(id / T), k = (int)(id - (long long)e * T);
+    const int ti = k / s.gx, tj = k - ti * s.gx;
+    const int i0 = ti * kTile, j0 = tj * kTile;
+    const int t = a.t0 + e;
+    bool ok = true;
+    float acc[4][16];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
+
+    if (fwd) {
+      // ---------------- forward item: w_t = u_t . F_t x on the tile ----------------
+      const long long slot = id % RS;
+      if (id >= RS && tid < 9) {
+        // the adjoint readers of the slot's previous tile (forward id - R) are done
+        const long long prev = id - RS;
+        const int pe = (int)(prev / T), pk = (int)(prev - (long long)pe * T);
+        const int nti = pk / s.gx + tid / 3 - 1, ntj = pk % s.gx + tid % 3 - 1;
+        if (nti >= 0 && nti < s.gy && ntj >= 0 && ntj < s.gx)
+          ok = wait_geq(h.adone + nti * s.gx + ntj, pe + 1, h.ctrl);
+      }
+      for (int phi = 0; phi < s.R2; ++phi) {
+        if (phi > 0) __syncthreads();  // readers of the previous phase's window are done
+        gather_plane(s, hs, sp, a.x + (long long)phi * g.plane, i0, j0);
+        const float4* kg =
+            reinterpret_cast<const float4*>(a.kf + ((long long)t * s.R2 + phi) * hs.ks);
+        for (int q = tid; q < kq; q += kThreads) reinterpret_cast<float4*>(ks)[q] = kg[q];
+        __syncthreads();  // also orders the slot wait above before the stores below
+        corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
+      }
+      float* wt = h.ring + slot * kTileFloats;
+      const float* up = a.u + (long long)t * g.plane;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const long long grow = (long long)(g.B + i0 + 4 * my + p) * g.P + g.B + j0 + 16 * mx;
+        float4* dst = reinterpret_cast<float4*>(wt + (4 * my + p) * kTile + 16 * mx);
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) {
+          float4 w;
+          w.x = __ldg(up + grow + 4 * c4 + 0) * acc[p][4 * c4 + 0];
+          w.y = __ldg(up + grow + 4 * c4 + 1) * acc[p][4 * c4 + 1];
+          w.z = __ldg(up + grow + 4 * c4 + 2) * acc[p][4 * c4 + 2];
+          w.w = __ldg(up + grow + 4 * c4 + 3) * acc[p][4 * c4 + 3];
+          dst[c4] = w;
+        }
+      }
+      if (__syncthreads_or(!ok)) timed_out = true;  // every w store of the CTA is issued
+      if (tid == 0) {
+        __threadfence();
+        st_release(h.fflag + slot, (int)(id + 1));
+      }
+    } else {
+      // ---------------- adjoint item: Den (+)= F_t^T w_t on the tile ----------------
+      if (tid < 9) {
+        const int nti = ti + tid / 3 - 1, ntj = tj + tid % 3 - 1;
+        const float* src = nullptr;
+        if (nti >= 0 && nti < s.gy && ntj >= 0 && ntj < s.gx) {
+          const long long fid = (long long)e * T + nti * s.gx + ntj;
+          const long long slot = fid % RS;
+          ok = wait_geq(h.fflag + slot, (int)(fid + 1), h.ctrl);
+          src = h.ring + slot * kTileFloats;
+        }
+        nb_s[tid] = src;
+      } else if (tid == 9 && e > 0) {
+        ok = wait_geq(h.adone + k, e, h.ctrl);  // adjoint (e - 1, k) has written Den
+      }
+      __syncthreads();
+      gather_ring(hs, sp, nb_s, s.hc, i0, j0);
+      for (int phi = 0; phi < s.R2; ++phi) {
+        if (phi > 0) {
+          __syncthreads();  // readers of the previous phase's kernel are done
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
+        }
+        const float4* kg =
+            reinterpret_cast<const float4*>(a.ka + ((long long)t * s.R2 + phi) * hs.ks);
+        for (int q = tid; q < kq; q += kThreads) reinterpret_cast<float4*>(ks)[q] = kg[q];
+        __syncthreads();
+        // each exposure's adjoint is summed from zero, then added to Den
+        corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
+        const long long pbase = (long long)phi * g.plane;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const int i = i0 + 4 * my + p;
+          const long long grow = pbase + (long long)(g.B + i) * g.P + g.B + j0 + 16 * mx;
+          if (e > 0) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[p][c] = __ldcg(a.Den + grow + c) + acc[p][c];
+          }
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int j = j0 + 16 * mx + c;
+            if (e + 1 < ne) {
+              a.Den[grow + c] = acc[p][c];
+            } else if (i < g.H && j < g.W) {
+              const float d = acc[p][c];
+              const float xo = a.x[grow + c];
+              float xv = xo;
+              if (d > 0.f) {
+                const float nv = fmaxf(a.N[grow + c], 0.f);
+                if (d < 1e-30f)  // denominator near zero: guarded ratio in FP64
+                  xv = (float)((double)xo * (double)nv / (double)d);
+                else
+                  xv = xo * nv / d;
+              }
+              a.xn[grow + c] = xv;
+            }
+          }
+        }
+      }
+      if (__syncthreads_or(!ok)) timed_out = true;  // all reads of the ring and Den are done
+      if (tid == 0) {
+        __threadfence();
+        st_release(h.adone + k, e + 1);
+      }
+    }
+  }
+
+  // The last CTA to finish resets the flags and counters for the next launch
+  // (stream order makes the reset visible to it).
+  __syncthreads();
+  if (tid == 0) {
+    if (timed_out) atomicOr(a.err, kErrTimeout);
+    __threadfence();
+    last_s = atomicAdd(&h.ctrl[1], 1ull) == (unsigned long long)(gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last_s) {
+    __threadfence();
+    for (long long i = tid; i < RS; i += kThreads) h.fflag[i] = 0;
+    for (int i = tid; i < T; i += kThreads) h.adone[i] = 0;
+    if (tid == 0) {
+      h.ctrl[0] = 0ull;
+      h.ctrl[1] = 0ull;
+      h.ctrl[2] = 0ull;
+    }
+  }
+}
+
+}  // namespace
+
+HaloPlan halo_plan(const Shape& s, int ne) {
+  HaloPlan p;
+  p.T = s.gx * s.gy;
+  // neighbour ids differ by up to gx + 1 (a row of tiles plus one column)
+  p.dmax = (s.gy > 1 ? s.gx : 0) + (s.gx > 1 ? 1 : 0);
+  p.NT = (long long)ne * p.T;
+  p.L = p.dmax + 2LL * kHaloCtasMax;
+  if (p.L > p.NT) p.L = p.NT;
+  p.R = p.L + p.dmax + 1 + kHaloCtasMax;
+  if (p.R > p.NT) p.R = p.NT;
+  return p;
+}
+
+size_t halo_buffer_bytes(const Shape& s) {
+  const HaloPlan p = halo_plan(s, s.n);
+  if (2 * p.NT + 2LL * kHaloCtasMax >= (1LL << 31)) return 0;  // 32-bit item ids
+  return align256((size_t)p.R * kTileFloats * sizeof(float)) +
+         align256((size_t)p.R * sizeof(int)) + align256((size_t)p.T * sizeof(int)) + 256;
+}
+
+void halo_bind(const Shape& s, void* buf, HaloLaunch* h) {
+  const HaloPlan p = halo_plan(s, s.n);
+  char* b = static_cast<char*>(buf);
+  h->ring = reinterpret_cast<float*>(b);
+  b += align256((size_t)p.R * kTileFloats * sizeof(float));
+  h->fflag = reinterpret_cast<int*>(b);
+  b += align256((size_t)p.R * sizeof(int));
+  h->adone = reinterpret_cast<int*>(b);
+  b += align256((size_t)p.T * sizeof(int));
+  h->ctrl = reinterpret_cast<unsigned long long*>(b);
+}
+
+cudaError_t launch_halo_iter(const Shape& s, const HaloLaunch& h, cudaStream_t st) {
+  const int ne = h.a.t1 - h.a.t0;
+  if (ne <= 0 || ne > s.n) return cudaErrorInvalidValue;
+  const HaloPlan pl = halo_plan(s, ne);
+  const size_t smem = halo_smem_bytes(s);
+  cudaError_t e =
+      cudaFuncSetAttribute(halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, occ = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_kernel, kThreads, smem)) !=
+      cudaSuccess)
+    return e;
+  long long grid = (long long)sms * (occ > 0 ? occ : 1);
+  if (grid > kHaloCtasMax) grid = kHaloCtasMax;
+  if (grid > 2 * pl.NT) grid = 2 * pl.NT;
+  halo_kernel<<<(int)grid, kThreads, smem, st>>>(s, h, pl);
+  return cudaGetLastError();
+}
+
+}  // namespace emd

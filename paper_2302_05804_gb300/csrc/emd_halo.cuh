@@ -1,0 +1,39 @@
+// emd_halo.cuh -- the halo-exchange form of the FP32 direct EM iteration
+// (declarations; the kernel is in emd_halo.cu).
+#pragma once
+
+#include "emd_internal.cuh"
+
+namespace emd {
+
+// Work plan of one launch over the exposures [t0, t1): ne = t1 - t0,
+// T = gx * gy tiles, NT = ne * T forward items and NT adjoint items.
+struct HaloPlan {
+  int T;          // tiles per exposure
+  int dmax;       // largest item-index distance between neighbouring tiles
+  long long NT;   // forward (= adjoint) items
+  long long L;    // adjoint items trail forward items by L
+  long long R;    // w ring slots (tile-sized)
+};
+
+HaloPlan halo_plan(const Shape& s, int ne);
+// device bytes of the ring, its flags and the work counters for up to n
+// exposures per launch (0 when the shape is too large for 32-bit item ids)
+size_t halo_buffer_bytes(const Shape& s);
+
+struct HaloLaunch {
+  FusedArgs a;                 // x, xn, u, kf, ka, N, Den, err, t0, t1 (Gaussian noise)
+  float* ring;                 // R slots of kTile * kTile floats
+  int* fflag;                  // R: forward item id + 1 last published in each slot
+  int* adone;                  // T: adjoint items finished per tile in this launch
+  unsigned long long* ctrl;    // [0] claim counter, [1] CTAs finished, [2] abort flag
+};
+
+// carves the ring, flags and counters out of a zeroed buffer of
+// halo_buffer_bytes(s) bytes
+void halo_bind(const Shape& s, void* buf, HaloLaunch* h);
+// one EM iteration of the exposures [a.t0, a.t1) (mode 0 of the fused
+// kernel): a.x -> a.xn, Den scratch in a.Den
+cudaError_t launch_halo_iter(const Shape& s, const HaloLaunch& h, cudaStream_t st);
+
+}  // namespace emd

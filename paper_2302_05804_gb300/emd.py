@@ -31,6 +31,7 @@ EMD_PREC_FP16 = 2
 EMD_PREC_SPLIT_BF16 = 3
 EMD_PREC_SPLIT_FP16 = 4
 EMD_PREC_FFT_FP32 = 5
+EMD_PREC_FP32_PAIR = 6
 EMD_NOISE_GAUSSIAN = 0
 EMD_NOISE_STUDENT_T = 1
 

@@ -1,0 +1,104 @@
+"""The halo-exchange FP32 kernel (EMD_PREC_FP32, csrc/emd_halo.cu) against
+the CTA-pair kernel (EMD_PREC_FP32_PAIR) and against the FP64 oracle.
+
+Both kernels evaluate every output with the same FP32 operations in the same
+order (the tap order of each forward and adjoint sum, w = u z, Den + sum,
+the guarded ratio of Eq. (2)), so their iterates must agree bit for bit.
+Shapes cover one tile, ragged edges, one row and one column of tiles, K = 1,
+r = 2, and grids large enough that the w ring's slots are reused within a
+launch; several iterations in a row also check that the kernel's flags and
+counters are reset for the next launch."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def emd():
+    from paper_2302_05804_gb300 import emd as m
+    m.load()
+    return m
+
+
+def run(emd, p, x0, k, prec):
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    try:
+        d.set_frames(p.y, p.v, p.f, p.mask)
+        d.set_precision(prec)
+        d.set_x(x0)
+        out = []
+        for _ in range(k):
+            d.iterate(1)
+            out.append(d.x())
+        return out
+    finally:
+        d.close()
+
+
+def start(p, seed=0):
+    g = np.random.default_rng(seed)
+    return (g.uniform(0.5, 1.5, (p.r * p.H, p.r * p.W)) * 10.0).astype(np.float32)
+
+
+# (H, W, n, K, r): one tile; ragged 3 x 3 tiles; one row of tiles; one column;
+# K = 1; r = 2 with a ragged grid; 8 x 8 tiles x 12 exposures (NT = 768 >
+# ring slots 499: slots reused within the launch)
+CASES = [(96, 80, 3, 15, 1), (300, 257, 5, 43, 1), (100, 1500, 3, 21, 1),
+         (1400, 90, 3, 21, 1), (260, 300, 4, 1, 1), (200, 330, 4, 9, 2),
+         (1024, 1024, 12, 43, 1)]
+
+
+@pytest.mark.parametrize("H,W,n,K,r", CASES)
+def test_bit_identical_to_cta_pair_kernel(emd, H, W, n, K, r):
+    p = synth.make_problem("hsc", H=H, W=W, n=n, K=K, r=r, mask_frac=0.05,
+                           fwhm=(2.0 * r, 5.0 * r), n_points=60, n_gal=4, seed_offset=H + W + K)
+    x0 = start(p, seed=n)
+    a = run(emd, p, x0, 3, emd.EMD_PREC_FP32)
+    b = run(emd, p, x0, 3, emd.EMD_PREC_FP32_PAIR)
+    for it in range(3):
+        assert np.array_equal(a[it], b[it]), (it, np.abs(a[it] - b[it]).max())
+
+
+def test_oracle_parity_with_ring_reuse(emd):
+    """A ragged 6 x 6 tile grid with 40 exposures: 1440 forward items through
+    a ring of 495 slots, so slots are rewritten within every launch; one and
+    five iterations against the oracle at the FP32 path's tolerances."""
+    p = synth.make_problem("hsc", H=700, W=650, n=40, K=15, r=1, mask_frac=0.05,
+                           fwhm=(2.0, 4.0), n_points=80, n_gal=5, seed_offset=3)
+    x0 = start(p, seed=1)
+    xs = run(emd, p, x0, 5, emd.EMD_PREC_FP32)
+    u, y, N, _ = oracle.prepare(p)
+    x1 = oracle.em_run(x0.astype(np.float64), N, u, p.f, 1, p.r)
+    e1 = np.linalg.norm(xs[0] - x1) / np.linalg.norm(x1)
+    assert e1 <= 1e-5, e1
+    x5 = oracle.em_run(x1, N, u, p.f, 4, p.r)
+    e5 = np.linalg.norm(xs[4] - x5) / np.linalg.norm(x5)
+    assert e5 <= 1e-4, e5
+
+
+def test_alternating_with_the_pair_kernel_and_streaming(emd):
+    """The ring kernel and the CTA-pair kernel share the context's Den plane:
+    alternate them (and the streaming pass) and compare with running the
+    CTA-pair kernel throughout."""
+    p = synth.make_problem("hsc", H=260, W=270, n=4, K=15, r=1, mask_frac=0.05,
+                           fwhm=(2.0, 4.0), n_points=40, n_gal=3, seed_offset=9)
+    x0 = start(p, seed=2)
+
+    def seq(first):
+        d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+        try:
+            d.set_frames(p.y, p.v, p.f, p.mask)
+            d.set_x(x0)
+            d.set_precision(first)
+            d.iterate(2)
+            d.iterate_streaming(1)
+            d.iterate(2)
+            return d.x()
+        finally:
+            d.close()
+
+    assert np.array_equal(seq(emd.EMD_PREC_FP32), seq(emd.EMD_PREC_FP32_PAIR))

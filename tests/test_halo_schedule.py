@@ -1,0 +1,142 @@
+"""Host-side check of the work-item schedule of the halo-exchange FP32 kernel
+(csrc/emd_halo.cu): the claim sequence, the ring of w tile slots and the
+waits, restated here and run as a discrete-event simulation.
+
+Each simulated CTA claims the next item of the sequence, waits until the
+item's dependencies are met, runs for a random time and publishes. The test
+asserts that every dependency of an item comes earlier in the claim sequence
+(so no wait can deadlock with any number of CTAs), that the simulation never
+stalls, that every adjoint item reads the w tiles of its own exposure and
+neighbours, that no forward item overwrites a slot while a reader still
+needs it, and that adjoint items of one tile run in exposure order."""
+import random
+
+import pytest
+
+
+def plan(gx, gy, ne, cap):
+    T = gx * gy
+    dmax = (gx if gy > 1 else 0) + (1 if gx > 1 else 0)
+    NT = ne * T
+    L = min(NT, dmax + 2 * cap)
+    R = min(NT, L + dmax + 1 + cap)
+    return T, dmax, NT, L, R
+
+
+def decode(sq, NT, L):
+    if sq < L:
+        return True, sq
+    if sq < 2 * NT - L:
+        j = sq - L
+        return (True, L + j // 2) if j & 1 else (False, j // 2)
+    return False, sq - NT
+
+
+def neighbours(k, gx, gy):
+    ti, tj = divmod(k, gx)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            a, b = ti + dy, tj + dx
+            if 0 <= a < gy and 0 <= b < gx:
+                yield a * gx + b
+
+
+def deps(fwd, i, gx, gy, T, R):
+    """(kind, id) items that must be finished before item (fwd, i) proceeds."""
+    out = []
+    if fwd:
+        if i >= R:
+            pe, pk = divmod(i - R, T)
+            out += [("A", pe * T + k) for k in neighbours(pk, gx, gy)]
+    else:
+        e, k = divmod(i, T)
+        out += [("F", e * T + k2) for k2 in neighbours(k, gx, gy)]
+        if e > 0:
+            out.append(("A", (e - 1) * T + k))
+    return out
+
+
+SHAPES = [(1, 1), (1, 3), (3, 1), (2, 2), (5, 4), (8, 8), (4, 9)]
+
+
+@pytest.mark.parametrize("gx,gy", SHAPES)
+@pytest.mark.parametrize("ne", [1, 2, 5])
+@pytest.mark.parametrize("cap", [1, 3, 160])
+def test_dependencies_are_claimed_earlier(gx, gy, ne, cap):
+    T, dmax, NT, L, R = plan(gx, gy, ne, cap)
+    pos = {}
+    for sq in range(2 * NT):
+        fwd, i = decode(sq, NT, L)
+        key = ("F" if fwd else "A", i)
+        assert key not in pos
+        pos[key] = sq
+    assert len(pos) == 2 * NT  # every item exactly once
+    for (kind, i), sq in pos.items():
+        for d in deps(kind == "F", i, gx, gy, T, R):
+            assert pos[d] < sq, ((kind, i), d)
+
+
+def simulate(gx, gy, ne, cap, ctas, seed):
+    T, dmax, NT, L, R = plan(gx, gy, ne, cap)
+    rng = random.Random(seed)
+    done = set()
+    ring = [None] * R         # F id whose w the slot holds
+    readers = {}              # A id -> list of (slot, expected F id)
+    next_sq = 0
+    workers = [None] * ctas   # (kind, id, state, remaining time)
+    adone_order = {}
+    time = 0
+    while len(done) < 2 * NT:
+        progressed = False
+        for wi in range(ctas):
+            w = workers[wi]
+            if w is None:
+                if next_sq < 2 * NT:
+                    fwd, i = decode(next_sq, NT, L)
+                    next_sq += 1
+                    workers[wi] = ["F" if fwd else "A", i, "wait", rng.randint(1, 5)]
+                    progressed = True
+                continue
+            kind, i, state, rem = w
+            if state == "wait":
+                if all(d in done for d in deps(kind == "F", i, gx, gy, T, R)):
+                    w[2] = "run"
+                    progressed = True
+                    if kind == "F":
+                        slot = i % R
+                        # nobody still needs the slot's previous tile
+                        for a, lst in readers.items():
+                            if ("A", a) not in done:
+                                assert (slot, ring[slot]) not in lst or ring[slot] is None
+                        ring[slot] = ("pending", i)
+                    else:
+                        e, k = divmod(i, T)
+                        need = [((e * T + k2) % R, e * T + k2) for k2 in neighbours(k, gx, gy)]
+                        for slot, fid in need:
+                            assert ring[slot] == fid, (i, slot, ring[slot], fid)
+                        readers[i] = need
+                continue
+            w[3] -= 1
+            progressed = True
+            if w[3] == 0:
+                if kind == "F":
+                    ring[i % R] = i
+                else:
+                    for slot, fid in readers[i]:
+                        assert ring[slot] == fid  # not overwritten while being read
+                    e, k = divmod(i, T)
+                    assert adone_order.get(k, -1) == e - 1
+                    adone_order[k] = e
+                done.add((kind, i))
+                workers[wi] = None
+        time += 1
+        assert progressed, "schedule stalled"
+    return time
+
+
+@pytest.mark.parametrize("gx,gy", SHAPES)
+@pytest.mark.parametrize("ne", [1, 3])
+@pytest.mark.parametrize("cap,ctas", [(1, 1), (1, 2), (2, 5), (3, 40)])
+def test_simulated_execution(gx, gy, ne, cap, ctas):
+    for seed in range(3):
+        simulate(gx, gy, ne, cap, ctas, seed)
