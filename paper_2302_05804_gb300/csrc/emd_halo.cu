@@ -180,6 +180,65 @@ __device__ void gather_ring(const HaloShape& hs, const SPlane& sp, const float* 
   }
 }
 
+// Position sq of the claim sequence -> (forward?, item id).
+__device__ __forceinline__ bool decode_item(long long sq, long long NT, long long L,
+                                            long long* id) {
+  if (sq < L) {
+    *id = sq;
+    return true;
+  }
+  if (sq < 2 * NT - L) {
+    const long long j = sq - L;
+    *id = (j & 1) ? L + (j >> 1) : (j >> 1);
+    return (j & 1) != 0;
+  }
+  *id = sq - NT;
+  return false;
+}
+
+__device__ __forceinline__ void prefetch_l2(const float* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// One warp: L2 prefetch of rows [r0, r0 + nrows), floats [c0, c0 + ncols) of
+// a padded plane (rows start 32-byte aligned; each row's range is widened to
+// the 16-byte grid the bulk prefetch wants).
+__device__ void prefetch_rect(const float* plane, int P, int r0, int nrows, int c0, int ncols,
+                              int lane) {
+  const int a0 = c0 & ~3;
+  const uint32_t bytes = (uint32_t)(((c0 + ncols - a0 + 3) & ~3) * sizeof(float));
+  for (int R = lane; R < nrows; R += 32) prefetch_l2(plane + (long long)(r0 + R) * P + a0, bytes);
+}
+
+// One warp, at the start of the item before it: brings into L2 what item sq
+// reads from DRAM (u, x and Den are each touched once per exposure, so they
+// are not in L2 any more): a forward item's x window and u tile, an adjoint
+// item's Den tile (and x and N for the update of the last exposure).
+__device__ void prefetch_item(const Shape& s, const FusedArgs& a, const HaloShape& hs,
+                              const HaloPlan& pl, long long sq, int lane) {
+  long long id;
+  const bool fwd = decode_item(sq, pl.NT, pl.L, &id);
+  const int e = (int)(id / pl.T), k = (int)(id - (long long)e * pl.T);
+  const int i0 = (k / s.gx) * kTile, j0 = (k % s.gx) * kTile;
+  const Geom& g = s.g;
+  const int t = a.t0 + e, ne = a.t1 - a.t0;
+  if (fwd) {
+    for (int phi = 0; phi < s.R2; ++phi)
+      prefetch_rect(a.x + (long long)phi * g.plane, g.P, i0 + s.hc, hs.rows, j0 + s.hc, hs.cols,
+                    lane);
+    prefetch_rect(a.u + (long long)t * g.plane, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
+  } else {
+    for (int phi = 0; phi < s.R2; ++phi) {
+      const long long pb = (long long)phi * g.plane;
+      if (e > 0) prefetch_rect(a.Den + pb, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
+      if (e + 1 == ne) {
+        prefetch_rect(a.x + pb, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
+        prefetch_rect(a.N + pb, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     halo_kernel(const Shape s, const HaloLaunch h, const HaloPlan pl) {
   extern __shared__ __align__(128) float smem[];
@@ -199,25 +258,25 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int kq = hs.ks >> 2;
   bool timed_out = false;
 
-  for (;;) {
-    __syncthreads();  // readers of the previous item's window, kernel and item id are done
-    if (tid == 0) item_s = (long long)atomicAdd(&h.ctrl[0], 1ull);
-    __syncthreads();
-    const long long sq = item_s;
-    if (sq >= 2 * NT) break;
-    bool fwd;
-    long long id;
-    if (sq < L) {
-      fwd = true;
-      id = sq;
-    } else if (sq < 2 * NT - L) {
-      const long long j = sq - L;
-      fwd = (j & 1) != 0;
-      id = fwd ? L + (j >> 1) : (j >> 1);
-    } else {
-      fwd = false;
-      id = sq - NT;
+  // Each CTA claims one item ahead: warp 0 takes the next position and
+  // prefetches its data into L2 while the CTA works on the current one. (A
+  // CTA then holds two claims; the one it has not started is later than the
+  // one it is running, so every wait still ends: the earliest unfinished
+  // claim is always running and waits only on finished ones.)
+  if (tid == 0) item_s = (long long)atomicAdd(&h.ctrl[0], 1ull);
+  __syncthreads();
+  long long sq = item_s;
+  while (sq < 2 * NT) {
+    __syncthreads();  // every thread has read item_s
+    if (tid < 32) {
+      long long nx = 0;
+      if (tid == 0) nx = (long long)atomicAdd(&h.ctrl[0], 1ull);
+      nx = __shfl_sync(0xffffffffu, nx, 0);
+      if (tid == 0) item_s = nx;
+      if (nx < 2 * NT) prefetch_item(s, a, hs, pl, nx, tid);
     }
+    long long id;
+    const bool fwd = decode_item(sq, NT, L, &id);
     const int e = (int)(id / T), k = (int)(id - (long long)e * T);
     const int ti = k / s.gx, tj = k - ti * s.gx;
     const int i0 = ti * kTile, j0 = tj * kTile;
@@ -253,15 +312,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float* up = a.u + (long long)t * g.plane;
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
+        // B and P are even: each row of the tile starts 8-byte aligned
         const long long grow = (long long)(g.B + i0 + 4 * my + p) * g.P + g.B + j0 + 16 * mx;
+        const float2* u2 = reinterpret_cast<const float2*>(up + grow);
         float4* dst = reinterpret_cast<float4*>(wt + (4 * my + p) * kTile + 16 * mx);
 #pragma unroll
         for (int c4 = 0; c4 < 4; ++c4) {
+          const float2 ua = __ldg(u2 + 2 * c4), ub = __ldg(u2 + 2 * c4 + 1);
           float4 w;
-          w.x = __ldg(up + grow + 4 * c4 + 0) * acc[p][4 * c4 + 0];
-          w.y = __ldg(up + grow + 4 * c4 + 1) * acc[p][4 * c4 + 1];
-          w.z = __ldg(up + grow + 4 * c4 + 2) * acc[p][4 * c4 + 2];
-          w.w = __ldg(up + grow + 4 * c4 + 3) * acc[p][4 * c4 + 3];
+          w.x = ua.x * acc[p][4 * c4 + 0];
+          w.y = ua.y * acc[p][4 * c4 + 1];
+          w.z = ub.x * acc[p][4 * c4 + 2];
+          w.w = ub.y * acc[p][4 * c4 + 3];
           dst[c4] = w;
         }
       }
@@ -306,16 +368,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int p = 0; p < 4; ++p) {
           const int i = i0 + 4 * my + p;
           const long long grow = pbase + (long long)(g.B + i) * g.P + g.B + j0 + 16 * mx;
+          float2* den2 = reinterpret_cast<float2*>(a.Den + grow);
           if (e > 0) {
 #pragma unroll
-            for (int c = 0; c < 16; ++c) acc[p][c] = __ldcg(a.Den + grow + c) + acc[p][c];
+            for (int c2 = 0; c2 < 8; ++c2) {
+              const float2 dv = __ldcg(den2 + c2);
+              acc[p][2 * c2] = dv.x + acc[p][2 * c2];
+              acc[p][2 * c2 + 1] = dv.y + acc[p][2 * c2 + 1];
+            }
+          }
+          if (e + 1 < ne) {
+#pragma unroll
+            for (int c2 = 0; c2 < 8; ++c2) den2[c2] = make_float2(acc[p][2 * c2], acc[p][2 * c2 + 1]);
+            continue;
           }
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
             const int j = j0 + 16 * mx + c;
-            if (e + 1 < ne) {
-              a.Den[grow + c] = acc[p][c];
-            } else if (i < g.H && j < g.W) {
+            if (i < g.H && j < g.W) {
               const float d = acc[p][c];
               const float xo = a.x[grow + c];
               float xv = xo;
@@ -337,6 +407,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         st_release(h.adone + k, e + 1);
       }
     }
+    __syncthreads();  // readers of this item's window and kernel are done; item_s is set
+    sq = item_s;
   }
 
   // The last CTA to finish resets the flags and counters for the next launch

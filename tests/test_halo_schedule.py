@@ -76,9 +76,12 @@ def test_dependencies_are_claimed_earlier(gx, gy, ne, cap):
             assert pos[d] < sq, ((kind, i), d)
 
 
-def simulate(gx, gy, ne, cap, ctas, seed):
+def simulate(gx, gy, ne, cap, ctas, seed, ahead=True):
+    """ahead: each CTA claims its next position when it starts an item (the
+    kernel's claim-ahead, which prefetches that item's data meanwhile)."""
     T, dmax, NT, L, R = plan(gx, gy, ne, cap)
     rng = random.Random(seed)
+    pending = [None] * ctas   # the claim taken ahead, not started yet
     done = set()
     ring = [None] * R         # F id whose w the slot holds
     readers = {}              # A id -> list of (slot, expected F id)
@@ -91,10 +94,15 @@ def simulate(gx, gy, ne, cap, ctas, seed):
         for wi in range(ctas):
             w = workers[wi]
             if w is None:
-                if next_sq < 2 * NT:
-                    fwd, i = decode(next_sq, NT, L)
-                    next_sq += 1
+                sq = pending[wi]
+                if sq is None:
+                    sq, next_sq = next_sq, next_sq + 1
+                pending[wi] = None
+                if sq < 2 * NT:
+                    fwd, i = decode(sq, NT, L)
                     workers[wi] = ["F" if fwd else "A", i, "wait", rng.randint(1, 5)]
+                    if ahead:
+                        pending[wi], next_sq = next_sq, next_sq + 1
                     progressed = True
                 continue
             kind, i, state, rem = w
@@ -137,6 +145,7 @@ def simulate(gx, gy, ne, cap, ctas, seed):
 @pytest.mark.parametrize("gx,gy", SHAPES)
 @pytest.mark.parametrize("ne", [1, 3])
 @pytest.mark.parametrize("cap,ctas", [(1, 1), (1, 2), (2, 5), (3, 40)])
-def test_simulated_execution(gx, gy, ne, cap, ctas):
+@pytest.mark.parametrize("ahead", [False, True])
+def test_simulated_execution(gx, gy, ne, cap, ctas, ahead):
     for seed in range(3):
-        simulate(gx, gy, ne, cap, ctas, seed)
+        simulate(gx, gy, ne, cap, ctas, seed, ahead)
