@@ -76,6 +76,12 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -268,13 +274,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   long long sq = item_s;
   while (sq < 2 * NT) {
     __syncthreads();  // every thread has read item_s
-    if (tid < 32) {
-      long long nx = 0;
-      if (tid == 0) nx = (long long)atomicAdd(&h.ctrl[0], 1ull);
-      nx = __shfl_sync(0xffffffffu, nx, 0);
-      if (tid == 0) item_s = nx;
-      if (nx < 2 * NT) prefetch_item(s, a, hs, pl, nx, tid);
-    }
+    // the next claim is taken now and used after this item's window is staged,
+    // so the atomic's round trip overlaps the staging loads
+    unsigned long long nx_raw = 0;
+    if (tid == 0) nx_raw = atomicAdd(&h.ctrl[0], 1ull);
+    auto claim_next = [&]() {
+      if (tid < 32) {
+        const long long nx = (long long)__shfl_sync(0xffffffffu, nx_raw, 0);
+        if (tid == 0) item_s = nx;
+        if (nx < 2 * NT) prefetch_item(s, a, hs, pl, nx, tid);
+      }
+    };
     long long id;
     const bool fwd = decode_item(sq, NT, L, &id);
     const int e = (int)(id / T), k = (int)(id - (long long)e * T);
@@ -291,13 +301,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (fwd) {
       // ---------------- forward item: w_t = u_t . F_t x on the tile ----------------
       const long long slot = id % RS;
+      // The slot's previous tile (forward id - R) must have been read by its
+      // adjoint readers before this item's w is stored: probe their counters
+      // now (relaxed), settle after staging (a fence, or a bounded wait).
+      const int* probe = nullptr;
+      int need = 0, seen = 0;
       if (id >= RS && tid < 9) {
-        // the adjoint readers of the slot's previous tile (forward id - R) are done
         const long long prev = id - RS;
         const int pe = (int)(prev / T), pk = (int)(prev - (long long)pe * T);
         const int nti = pk / s.gx + tid / 3 - 1, ntj = pk % s.gx + tid % 3 - 1;
-        if (nti >= 0 && nti < s.gy && ntj >= 0 && ntj < s.gx)
-          ok = wait_geq(h.adone + nti * s.gx + ntj, pe + 1, h.ctrl);
+        if (nti >= 0 && nti < s.gy && ntj >= 0 && ntj < s.gx) {
+          probe = h.adone + nti * s.gx + ntj;
+          need = pe + 1;
+          seen = ld_relaxed(probe);
+        }
       }
       for (int phi = 0; phi < s.R2; ++phi) {
         if (phi > 0) __syncthreads();  // readers of the previous phase's window are done
@@ -305,7 +322,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float4* kg =
             reinterpret_cast<const float4*>(a.kf + ((long long)t * s.R2 + phi) * hs.ks);
         for (int q = tid; q < kq; q += kThreads) reinterpret_cast<float4*>(ks)[q] = kg[q];
-        __syncthreads();  // also orders the slot wait above before the stores below
+        if (phi == 0) {
+          claim_next();
+          if (probe) {
+            if (seen >= need)
+              __threadfence();  // acquire: the readers' loads precede our stores
+            else
+              ok = wait_geq(probe, need, h.ctrl);
+          }
+        }
+        __syncthreads();  // also orders the slot check above before the stores below
         corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
       }
       float* wt = h.ring + slot * kTileFloats;
@@ -349,6 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       __syncthreads();
       gather_ring(hs, sp, nb_s, s.hc, i0, j0);
+      claim_next();
       for (int phi = 0; phi < s.R2; ++phi) {
         if (phi > 0) {
           __syncthreads();  // readers of the previous phase's kernel are done
