@@ -134,7 +134,8 @@ int emd_iterate(emd_ctx *ctx, int k);
  * (x unchanged where the denominator is 0). order: a permutation of
  * 0..n-1, or NULL for ascending. The per-exposure numerators are computed
  * on the first call after emd_set_frames (n latent planes of device memory,
- * allocated then). Runs on the FP32 kernel regardless of the precision. */
+ * allocated then). Runs the FP32 direct halo-exchange kernel whatever the
+ * precision (the CTA-pair kernel under EMD_PREC_FP32_PAIR; same iterates). */
 int emd_iterate_streaming(emd_ctx *ctx, int k, const int *order);
 
 /* Copy the current iterate to out ((rH) x (rW) float32). */
@@ -165,9 +166,8 @@ int emd_loglik(emd_ctx *ctx, double *out, double *chi2);
  * bit from the kernel that keeps u_t z_t in the shared memory of a CTA
  * pair per tile and recomputes the forward model on a 2 hc halo around it
  * (no extra memory, 1.48x the multiply-adds at K = 43); the heavy-tailed
- * model, emd_loglik, emd_iterate_streaming and batched jobs always run that
- * kernel in the FP32 modes, and emd_loglik and emd_iterate_streaming in
- * every mode. */
+ * model and batched jobs run that kernel in the FP32 modes, and emd_loglik
+ * in every mode. */
 int emd_set_precision(emd_ctx *ctx, int mode);
 
 /*

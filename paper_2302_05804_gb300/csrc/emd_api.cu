@@ -123,6 +123,8 @@ struct emd_ctx {
   // halo-exchange form of the FP32 direct iteration: w ring, flags and
   // counters (allocated on the first FP32 direct iteration; zeroed)
   char* halo_arena = nullptr;
+  size_t halo_bytes = 0;
+  bool halo_student = false;  // slots hold two tiles (heavy-tailed weights)
   emd::HaloLaunch halo{};
 };
 
@@ -253,7 +255,7 @@ size_t emd_ctx_bytes_precision(int H, int W, int n, int psf_k, int r, int mode) 
   const char* why = nullptr;
   if (!emd::make_shape(H, W, n, psf_k, r, &s, &why)) return 0;
   const size_t base = make_layout(s).total;
-  if (mode == EMD_PREC_FP32) return base + emd::halo_buffer_bytes(s);
+  if (mode == EMD_PREC_FP32) return base + emd::halo_buffer_bytes(s, false);
   if (mode == EMD_PREC_FP32_PAIR) return base;
   if (mode == EMD_PREC_FFT_FP32) return base + emd::fft_buffer_bytes(s, false);
   if (mode < EMD_PREC_FP32 || mode > EMD_PREC_FFT_FP32) return 0;
@@ -372,16 +374,32 @@ int ensure_fft_arena(emd_ctx* c) {
   return EMD_OK;
 }
 
-// The halo-exchange iteration's ring, flags and counters; false (no error)
-// when the shape has too many work items for it (the CTA-pair kernel runs).
+// The halo-exchange iteration's ring, flags and counters for the current
+// noise model (re-sized when it needs two tiles per slot); *ok = false (no
+// error) when the shape has too many work items for it (the CTA-pair
+// kernel runs).
 int ensure_halo_arena(emd_ctx* c, bool* ok) {
   *ok = false;
-  if (c->halo_arena) {
+  const bool student = c->noise == EMD_NOISE_STUDENT_T;
+  const size_t need = emd::halo_buffer_bytes(c->s, student);
+  if (need == 0) return EMD_OK;
+  if (c->halo_arena && c->halo_bytes >= need) {
+    if (student != c->halo_student) {
+      // same buffer, other slot layout: the flags and counters move, so
+      // they (and everything else) start from zero again
+      CK(cudaMemsetAsync(c->halo_arena, 0, c->halo_bytes, c->st));
+      emd::halo_bind(c->s, student, c->halo_arena, &c->halo);
+      c->halo_student = student;
+    }
     *ok = true;
     return EMD_OK;
   }
-  const size_t need = emd::halo_buffer_bytes(c->s);
-  if (need == 0) return EMD_OK;
+  if (c->halo_arena) {
+    CK(cudaStreamSynchronize(c->st));
+    cudaFree(c->halo_arena);
+    c->halo_arena = nullptr;
+    c->halo_bytes = 0;
+  }
   void* p = nullptr;
   if (cudaMalloc(&p, need) != cudaSuccess) {
     cudaGetLastError();
@@ -390,7 +408,9 @@ int ensure_halo_arena(emd_ctx* c, bool* ok) {
   }
   CK(cudaMemsetAsync(p, 0, need, c->st));  // flags and counters start at zero
   c->halo_arena = static_cast<char*>(p);
-  emd::halo_bind(c->s, p, &c->halo);
+  c->halo_bytes = need;
+  c->halo_student = student;
+  emd::halo_bind(c->s, student, p, &c->halo);
   *ok = true;
   return EMD_OK;
 }
@@ -633,10 +653,22 @@ int emd_iterate(emd_ctx* c, int k) {
     return EMD_OK;
   }
   if (c->noise == EMD_NOISE_STUDENT_T) {
-    // heavy-tailed EM: the numerator depends on x through the weights, so
-    // each iteration runs the forward model twice: N' (mode 3), then Den'
-    // and the update (mode 0), both with the weights u' of the current x
-    for (int it = 0; it < k; ++it) {
+    // heavy-tailed EM: the numerator depends on x through the weights u' of
+    // the current x. The halo-exchange kernel computes the forward model
+    // once and both adjoints (Den' and N') in one launch; the CTA-pair
+    // kernel (EMD_PREC_FP32_PAIR) runs N' (mode 3), then Den' and the update
+    // (mode 0), each with its own forward pass. Same iterates either way.
+    bool halo = false;
+    if (c->prec == EMD_PREC_FP32 && k > 0)
+      if (int rc = ensure_halo_arena(c, &halo)) return rc;
+    for (int it = 0; halo && it < k; ++it) {
+      emd::HaloLaunch h = c->halo;
+      h.a = fused_args(c);
+      h.a.Nw = c->Ns;
+      CK(emd::launch_halo_iter(c->s, h, c->st));
+      c->cur ^= 1;
+    }
+    for (int it = 0; !halo && it < k; ++it) {
       emd::FusedArgs a = fused_args(c);
       a.Nw = c->Ns;
       CK(emd::launch_fused(c->s, a, 3, c->part, c->st));
@@ -748,6 +780,11 @@ int emd_iterate_streaming(emd_ctx* c, int k, const int* order) {
     }
     c->nt_ready = true;
   }
+  // the halo-exchange kernel over the one-exposure range (the CTA-pair
+  // kernel under EMD_PREC_FP32_PAIR): the same iterates either way
+  bool halo = false;
+  if (c->prec != EMD_PREC_FP32_PAIR && k > 0)
+    if (int rc = ensure_halo_arena(c, &halo)) return rc;
   for (int it = 0; it < k; ++it) {
     for (int q = 0; q < s.n; ++q) {
       const int t = ord[q];
@@ -755,7 +792,13 @@ int emd_iterate_streaming(emd_ctx* c, int k, const int* order) {
       a.N = c->Nt + (size_t)t * lat;
       a.t0 = t;
       a.t1 = t + 1;
-      CK(emd::launch_fused(s, a, 0, c->part, c->st));
+      if (halo) {
+        emd::HaloLaunch h = c->halo;
+        h.a = a;
+        CK(emd::launch_halo_iter(s, h, c->st));
+      } else {
+        CK(emd::launch_fused(s, a, 0, c->part, c->st));
+      }
       c->cur ^= 1;
     }
   }

@@ -153,7 +153,7 @@ __device__ void gather_plane(const Shape& s, const HaloShape& hs, const SPlane& 
 // grid is each slot's own. Loads bypass L1 (the slots are rewritten by
 // other SMs during the launch).
 __device__ void gather_ring(const HaloShape& hs, const SPlane& sp, const float* const* nb,
-                            int hc, int i0, int j0) {
+                            int off, int hc, int i0, int j0) {
   const int c0 = j0 - hc;   // image column of window column 0
   const int q0 = c0 >> 2;   // floor
   const int nq = ((c0 + hs.cols - 1) >> 2) - q0 + 1;
@@ -171,7 +171,7 @@ __device__ void gather_ring(const HaloShape& hs, const SPlane& sp, const float* 
         const int tr = ii >> 7, tc = cc >> 7;  // floor: neighbour tile row / column
         const float* src = nb[3 * (tr - ti + 1) + (tc - tj + 1)];
         if (src)
-          v[q] = __ldcg(reinterpret_cast<const float4*>(src + (ii - (tr << 7)) * kTile +
+          v[q] = __ldcg(reinterpret_cast<const float4*>(src + off + (ii - (tr << 7)) * kTile +
                                                          (cc - (tc << 7))));
       }
     }
@@ -233,10 +233,14 @@ __device__ void prefetch_item(const Shape& s, const FusedArgs& a, const HaloShap
       prefetch_rect(a.x + (long long)phi * g.plane, g.P, i0 + s.hc, hs.rows, j0 + s.hc, hs.cols,
                     lane);
     prefetch_rect(a.u + (long long)t * g.plane, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
+    if (a.nu > 0.f)
+      prefetch_rect(a.y + (long long)t * g.plane, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
   } else {
     for (int phi = 0; phi < s.R2; ++phi) {
       const long long pb = (long long)phi * g.plane;
       if (e > 0) prefetch_rect(a.Den + pb, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
+      if (e > 0 && a.nu > 0.f)
+        prefetch_rect(a.Nw + pb, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
       if (e + 1 == ne) {
         prefetch_rect(a.x + pb, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
         prefetch_rect(a.N + pb, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
@@ -245,6 +249,11 @@ __device__ void prefetch_item(const Shape& s, const FusedArgs& a, const HaloShap
   }
 }
 
+// STUDENT: heavy-tailed weights u' = u (nu+1) / (nu + u (y - z)^2); each
+// forward item then stores two tiles per slot, w = u' z and w2 = u' y, and
+// each adjoint item correlates both: Den and the numerator N' (a.Nw) of the
+// generalised EM step, in one launch per iteration.
+template <bool STUDENT>
 __global__ void __launch_bounds__(kThreads, 1)
     halo_kernel(const Shape s, const HaloLaunch h, const HaloPlan pl) {
   extern __shared__ __align__(128) float smem[];
@@ -262,6 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const long long NT = pl.NT, L = pl.L, RS = pl.R;
   const int ne = a.t1 - a.t0;
   const int kq = hs.ks >> 2;
+  constexpr long long kSlot = STUDENT ? 2LL * kTileFloats : kTileFloats;  // floats per ring slot
   bool timed_out = false;
 
   // Each CTA claims one item ahead: warp 0 takes the next position and
@@ -334,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();  // also orders the slot check above before the stores below
         corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
       }
-      float* wt = h.ring + slot * kTileFloats;
+      float* wt = h.ring + slot * kSlot;
       const float* up = a.u + (long long)t * g.plane;
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
@@ -342,15 +352,38 @@ __global__ void __launch_bounds__(kThreads, 1)
         const long long grow = (long long)(g.B + i0 + 4 * my + p) * g.P + g.B + j0 + 16 * mx;
         const float2* u2 = reinterpret_cast<const float2*>(up + grow);
         float4* dst = reinterpret_cast<float4*>(wt + (4 * my + p) * kTile + 16 * mx);
+        if (STUDENT) {
+          const float2* y2 = reinterpret_cast<const float2*>(a.y + (long long)t * g.plane + grow);
+          float4* dst2 = reinterpret_cast<float4*>(wt + kTileFloats + (4 * my + p) * kTile + 16 * mx);
+          const float nu1 = a.nu + 1.f;
 #pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) {
-          const float2 ua = __ldg(u2 + 2 * c4), ub = __ldg(u2 + 2 * c4 + 1);
-          float4 w;
-          w.x = ua.x * acc[p][4 * c4 + 0];
-          w.y = ua.y * acc[p][4 * c4 + 1];
-          w.z = ub.x * acc[p][4 * c4 + 2];
-          w.w = ub.y * acc[p][4 * c4 + 3];
-          dst[c4] = w;
+          for (int c4 = 0; c4 < 4; ++c4) {
+            const float2 ua = __ldg(u2 + 2 * c4), ub = __ldg(u2 + 2 * c4 + 1);
+            const float2 ya = __ldg(y2 + 2 * c4), yb = __ldg(y2 + 2 * c4 + 1);
+            const float uv[4] = {ua.x, ua.y, ub.x, ub.y}, yv[4] = {ya.x, ya.y, yb.x, yb.y};
+            float w[4], w2[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float z = acc[p][4 * c4 + q];
+              const float d = yv[q] - z;
+              const float us = uv[q] > 0.f ? uv[q] * nu1 / fmaf(uv[q] * d, d, a.nu) : 0.f;
+              w[q] = us * z;
+              w2[q] = us * yv[q];
+            }
+            dst[c4] = make_float4(w[0], w[1], w[2], w[3]);
+            dst2[c4] = make_float4(w2[0], w2[1], w2[2], w2[3]);
+          }
+        } else {
+#pragma unroll
+          for (int c4 = 0; c4 < 4; ++c4) {
+            const float2 ua = __ldg(u2 + 2 * c4), ub = __ldg(u2 + 2 * c4 + 1);
+            float4 w;
+            w.x = ua.x * acc[p][4 * c4 + 0];
+            w.y = ua.y * acc[p][4 * c4 + 1];
+            w.z = ub.x * acc[p][4 * c4 + 2];
+            w.w = ub.y * acc[p][4 * c4 + 3];
+            dst[c4] = w;
+          }
         }
       }
       if (__syncthreads_or(!ok)) timed_out = true;  // every w store of the CTA is issued
@@ -367,63 +400,71 @@ __global__ void __launch_bounds__(kThreads, 1)
           const long long fid = (long long)e * T + nti * s.gx + ntj;
           const long long slot = fid % RS;
           ok = wait_geq(h.fflag + slot, (int)(fid + 1), h.ctrl);
-          src = h.ring + slot * kTileFloats;
+          src = h.ring + slot * kSlot;
         }
         nb_s[tid] = src;
       } else if (tid == 9 && e > 0) {
         ok = wait_geq(h.adone + k, e, h.ctrl);  // adjoint (e - 1, k) has written Den
       }
       __syncthreads();
-      gather_ring(hs, sp, nb_s, s.hc, i0, j0);
-      claim_next();
-      for (int phi = 0; phi < s.R2; ++phi) {
-        if (phi > 0) {
-          __syncthreads();  // readers of the previous phase's kernel are done
+      // pass 0: Den from w (= u z, or u' z); heavy-tailed pass 1: N' from w2 = u' y
+      for (int pass = 0; pass < (STUDENT ? 2 : 1); ++pass) {
+        if (pass > 0) __syncthreads();  // readers of pass 0's window are done
+        gather_ring(hs, sp, nb_s, pass * kTileFloats, s.hc, i0, j0);
+        if (pass == 0) claim_next();
+        float* run = pass == 0 ? a.Den : a.Nw;  // running sum over the exposures
+        for (int phi = 0; phi < s.R2; ++phi) {
+          if (phi > 0 || pass > 0) {
+            if (phi > 0) __syncthreads();  // readers of the previous phase's kernel are done
 #pragma unroll
-          for (int p = 0; p < 4; ++p)
+            for (int p = 0; p < 4; ++p)
 #pragma unroll
-            for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
-        }
-        const float4* kg =
-            reinterpret_cast<const float4*>(a.ka + ((long long)t * s.R2 + phi) * hs.ks);
-        for (int q = tid; q < kq; q += kThreads) reinterpret_cast<float4*>(ks)[q] = kg[q];
-        __syncthreads();
-        // each exposure's adjoint is summed from zero, then added to Den
-        corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
-        const long long pbase = (long long)phi * g.plane;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const int i = i0 + 4 * my + p;
-          const long long grow = pbase + (long long)(g.B + i) * g.P + g.B + j0 + 16 * mx;
-          float2* den2 = reinterpret_cast<float2*>(a.Den + grow);
-          if (e > 0) {
-#pragma unroll
-            for (int c2 = 0; c2 < 8; ++c2) {
-              const float2 dv = __ldcg(den2 + c2);
-              acc[p][2 * c2] = dv.x + acc[p][2 * c2];
-              acc[p][2 * c2 + 1] = dv.y + acc[p][2 * c2 + 1];
-            }
+              for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
           }
-          if (e + 1 < ne) {
+          const float4* kg =
+              reinterpret_cast<const float4*>(a.ka + ((long long)t * s.R2 + phi) * hs.ks);
+          for (int q = tid; q < kq; q += kThreads) reinterpret_cast<float4*>(ks)[q] = kg[q];
+          __syncthreads();
+          // each exposure's adjoint is summed from zero, then added to the running sum
+          corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
+          const long long pbase = (long long)phi * g.plane;
 #pragma unroll
-            for (int c2 = 0; c2 < 8; ++c2) den2[c2] = make_float2(acc[p][2 * c2], acc[p][2 * c2 + 1]);
-            continue;
-          }
+          for (int p = 0; p < 4; ++p) {
+            const int i = i0 + 4 * my + p;
+            const long long grow = pbase + (long long)(g.B + i) * g.P + g.B + j0 + 16 * mx;
+            float2* run2 = reinterpret_cast<float2*>(run + grow);
+            if (e > 0) {
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int j = j0 + 16 * mx + c;
-            if (i < g.H && j < g.W) {
-              const float d = acc[p][c];
-              const float xo = a.x[grow + c];
-              float xv = xo;
-              if (d > 0.f) {
-                const float nv = fmaxf(a.N[grow + c], 0.f);
-                if (d < 1e-30f)  // denominator near zero: guarded ratio in FP64
-                  xv = (float)((double)xo * (double)nv / (double)d);
-                else
-                  xv = xo * nv / d;
+              for (int c2 = 0; c2 < 8; ++c2) {
+                const float2 dv = __ldcg(run2 + c2);
+                acc[p][2 * c2] = dv.x + acc[p][2 * c2];
+                acc[p][2 * c2 + 1] = dv.y + acc[p][2 * c2 + 1];
               }
-              a.xn[grow + c] = xv;
+            }
+            // not the last exposure; or the heavy-tailed Den, kept for pass 1
+            // (read back below by the thread that wrote it)
+            if (e + 1 < ne || (STUDENT && pass == 0)) {
+#pragma unroll
+              for (int c2 = 0; c2 < 8; ++c2)
+                run2[c2] = make_float2(acc[p][2 * c2], acc[p][2 * c2 + 1]);
+              continue;
+            }
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const int j = j0 + 16 * mx + c;
+              if (i < g.H && j < g.W) {
+                const float d = STUDENT ? __ldcg(a.Den + grow + c) : acc[p][c];
+                const float xo = a.x[grow + c];
+                float xv = xo;
+                if (d > 0.f) {
+                  const float nv = fmaxf(STUDENT ? acc[p][c] : a.N[grow + c], 0.f);
+                  if (d < 1e-30f)  // denominator near zero: guarded ratio in FP64
+                    xv = (float)((double)xo * (double)nv / (double)d);
+                  else
+                    xv = xo * nv / d;
+                }
+                a.xn[grow + c] = xv;
+              }
             }
           }
         }
@@ -474,18 +515,20 @@ HaloPlan halo_plan(const Shape& s, int ne) {
   return p;
 }
 
-size_t halo_buffer_bytes(const Shape& s) {
+size_t halo_buffer_bytes(const Shape& s, bool student) {
   const HaloPlan p = halo_plan(s, s.n);
   if (2 * p.NT + 2LL * kHaloCtasMax >= (1LL << 31)) return 0;  // 32-bit item ids
-  return align256((size_t)p.R * kTileFloats * sizeof(float)) +
-         align256((size_t)p.R * sizeof(int)) + align256((size_t)p.T * sizeof(int)) + 256;
+  const size_t slot = (student ? 2 : 1) * (size_t)kTileFloats * sizeof(float);
+  return align256((size_t)p.R * slot) + align256((size_t)p.R * sizeof(int)) +
+         align256((size_t)p.T * sizeof(int)) + 256;
 }
 
-void halo_bind(const Shape& s, void* buf, HaloLaunch* h) {
+void halo_bind(const Shape& s, bool student, void* buf, HaloLaunch* h) {
   const HaloPlan p = halo_plan(s, s.n);
+  const size_t slot = (student ? 2 : 1) * (size_t)kTileFloats * sizeof(float);
   char* b = static_cast<char*>(buf);
   h->ring = reinterpret_cast<float*>(b);
-  b += align256((size_t)p.R * kTileFloats * sizeof(float));
+  b += align256((size_t)p.R * slot);
   h->fflag = reinterpret_cast<int*>(b);
   b += align256((size_t)p.R * sizeof(int));
   h->adone = reinterpret_cast<int*>(b);
@@ -493,26 +536,32 @@ void halo_bind(const Shape& s, void* buf, HaloLaunch* h) {
   h->ctrl = reinterpret_cast<unsigned long long*>(b);
 }
 
-cudaError_t launch_halo_iter(const Shape& s, const HaloLaunch& h, cudaStream_t st) {
-  const int ne = h.a.t1 - h.a.t0;
-  if (ne <= 0 || ne > s.n) return cudaErrorInvalidValue;
-  const HaloPlan pl = halo_plan(s, ne);
+template <bool STUDENT>
+cudaError_t launch_halo_t(const Shape& s, const HaloLaunch& h, const HaloPlan& pl,
+                          cudaStream_t st) {
   const size_t smem = halo_smem_bytes(s);
-  cudaError_t e =
-      cudaFuncSetAttribute(halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(halo_kernel<STUDENT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, occ = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_kernel, kThreads, smem)) !=
-      cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_kernel<STUDENT>, kThreads,
+                                                         smem)) != cudaSuccess)
     return e;
   long long grid = (long long)sms * (occ > 0 ? occ : 1);
   if (grid > kHaloCtasMax) grid = kHaloCtasMax;
   if (grid > 2 * pl.NT) grid = 2 * pl.NT;
-  halo_kernel<<<(int)grid, kThreads, smem, st>>>(s, h, pl);
+  halo_kernel<STUDENT><<<(int)grid, kThreads, smem, st>>>(s, h, pl);
   return cudaGetLastError();
+}
+
+cudaError_t launch_halo_iter(const Shape& s, const HaloLaunch& h, cudaStream_t st) {
+  const int ne = h.a.t1 - h.a.t0;
+  if (ne <= 0 || ne > s.n) return cudaErrorInvalidValue;
+  const HaloPlan pl = halo_plan(s, ne);
+  return h.a.nu > 0.f ? launch_halo_t<true>(s, h, pl, st) : launch_halo_t<false>(s, h, pl, st);
 }
 
 }  // namespace emd

@@ -18,22 +18,25 @@ struct HaloPlan {
 
 HaloPlan halo_plan(const Shape& s, int ne);
 // device bytes of the ring, its flags and the work counters for up to n
-// exposures per launch (0 when the shape is too large for 32-bit item ids)
-size_t halo_buffer_bytes(const Shape& s);
+// exposures per launch (0 when the shape is too large for 32-bit item ids);
+// student: two tiles per slot (w = u' z and w2 = u' y)
+size_t halo_buffer_bytes(const Shape& s, bool student);
 
 struct HaloLaunch {
-  FusedArgs a;                 // x, xn, u, kf, ka, N, Den, err, t0, t1 (Gaussian noise)
-  float* ring;                 // R slots of kTile * kTile floats
+  FusedArgs a;                 // x, xn, u, kf, ka, N, Den, err, t0, t1; heavy-tailed
+                               // (a.nu > 0): also y, and a.Nw holds the running N'
+  float* ring;                 // R slots of kTile * kTile floats (two tiles if heavy-tailed)
   int* fflag;                  // R: forward item id + 1 last published in each slot
   int* adone;                  // T: adjoint items finished per tile in this launch
   unsigned long long* ctrl;    // [0] claim counter, [1] CTAs finished, [2] abort flag
 };
 
 // carves the ring, flags and counters out of a zeroed buffer of
-// halo_buffer_bytes(s) bytes
-void halo_bind(const Shape& s, void* buf, HaloLaunch* h);
-// one EM iteration of the exposures [a.t0, a.t1) (mode 0 of the fused
-// kernel): a.x -> a.xn, Den scratch in a.Den
+// halo_buffer_bytes(s, student) bytes
+void halo_bind(const Shape& s, bool student, void* buf, HaloLaunch* h);
+// one EM iteration of the exposures [a.t0, a.t1): a.x -> a.xn, Den scratch in
+// a.Den; the Gaussian update of Eq. (2) with numerator a.N, or (a.nu > 0) the
+// heavy-tailed step with N' accumulated in a.Nw
 cudaError_t launch_halo_iter(const Shape& s, const HaloLaunch& h, cudaStream_t st);
 
 }  // namespace emd

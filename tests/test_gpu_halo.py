@@ -102,3 +102,61 @@ def test_alternating_with_the_pair_kernel_and_streaming(emd):
             d.close()
 
     assert np.array_equal(seq(emd.EMD_PREC_FP32), seq(emd.EMD_PREC_FP32_PAIR))
+
+
+STUDENT_CASES = [(300, 257, 5, 43, 1), (200, 330, 4, 9, 2), (700, 650, 40, 15, 1)]
+
+
+@pytest.mark.parametrize("H,W,n,K,r", STUDENT_CASES)
+def test_heavy_tailed_bit_identical_to_cta_pair_kernel(emd, H, W, n, K, r):
+    """Student-t noise (nu = 3): the halo kernel's one-launch step (forward
+    once, adjoints of u'z and u'y) against the CTA-pair kernel's two launches
+    (N' with its own forward pass, then Den' and the update)."""
+    p = synth.make_problem("hsc", H=H, W=W, n=n, K=K, r=r, mask_frac=0.05,
+                           fwhm=(2.0 * r, 5.0 * r), n_points=60, n_gal=4, seed_offset=7 * H + K)
+    x0 = start(p, seed=n + 1)
+
+    def go(prec):
+        d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+        try:
+            d.set_frames(p.y, p.v, p.f, p.mask)
+            d.set_noise(emd.EMD_NOISE_STUDENT_T, 3.0)
+            d.set_precision(prec)
+            d.set_x(x0)
+            out = []
+            for _ in range(3):
+                d.iterate(1)
+                out.append(d.x())
+            return out
+        finally:
+            d.close()
+
+    a, b = go(emd.EMD_PREC_FP32), go(emd.EMD_PREC_FP32_PAIR)
+    for it in range(3):
+        assert np.array_equal(a[it], b[it]), (it, np.abs(a[it] - b[it]).max())
+
+
+def test_switching_noise_models_in_one_context(emd):
+    """Gaussian, then Student-t, then Gaussian again in one context: the ring
+    is re-laid out (two tiles per slot and back) and its counters restart
+    from zero; the iterates equal the CTA-pair kernel's."""
+    p = synth.make_problem("hsc", H=520, W=400, n=6, K=15, r=1, mask_frac=0.05,
+                           fwhm=(2.0, 4.0), n_points=40, n_gal=3, seed_offset=21)
+    x0 = start(p, seed=3)
+
+    def go(prec):
+        d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+        try:
+            d.set_frames(p.y, p.v, p.f, p.mask)
+            d.set_precision(prec)
+            d.set_x(x0)
+            d.iterate(2)
+            d.set_noise(emd.EMD_NOISE_STUDENT_T, 4.0)
+            d.iterate(2)
+            d.set_noise(emd.EMD_NOISE_GAUSSIAN)
+            d.iterate(2)
+            return d.x()
+        finally:
+            d.close()
+
+    assert np.array_equal(go(emd.EMD_PREC_FP32), go(emd.EMD_PREC_FP32_PAIR))
