@@ -180,17 +180,20 @@ int emd_set_precision(emd_ctx *ctx, int mode);
  * (the expected precision scale of the Gaussian scale mixture),
  *   x <- x . max(sum_t F_t^T(u'_t y_t), 0) / sum_t F_t^T(u'_t z_t)
  * (x unchanged where the denominator is 0); it never lowers the Student-t
- * likelihood, and tends to Eq. (2) as nu grows. It costs two forward and
- * two adjoint passes per iteration (Eq. (2): one each). emd_loglik then
+ * likelihood, and tends to Eq. (2) as nu grows. It costs one forward and
+ * two adjoint passes per iteration (Eq. (2): one each; under
+ * EMD_PREC_FP32_PAIR two of each). emd_loglik then
  * returns the Student-t log-likelihood
  *   sum_valid [lgamma((nu+1)/2) - lgamma(nu/2) - 1/2 log(nu pi v)
  *              - (nu+1)/2 log(1 + u (y - z)^2 / nu)]
  * and *chi2 = sum_valid (nu+1) log(1 + u (y - z)^2 / nu).
  * nu: finite, in (0, 1e30] (ignored for the Gaussian model). The heavy-tailed
- * model runs on the FP32 direct kernel and the FFT form (which then keeps n
- * more exposure planes, of u'y, and a larger per-tile scratch, allocated at
- * the next emd_set_precision or emd_iterate): EMD_EUNSUPPORTED with a
- * tensor-core precision, in emd_iterate_streaming and in emd_batch_add.
+ * model runs on the FP32 direct forms (EMD_PREC_FP32: its w ring then holds
+ * two tiles per slot, re-allocated at the next emd_iterate) and the FFT form
+ * (which then keeps n more exposure planes, of u'y, and a larger per-tile
+ * scratch, allocated at the next emd_set_precision or emd_iterate):
+ * EMD_EUNSUPPORTED with a tensor-core precision, in emd_iterate_streaming
+ * and in emd_batch_add.
  */
 enum emd_noise {
     EMD_NOISE_GAUSSIAN = 0,
