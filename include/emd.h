@@ -204,9 +204,13 @@ int emd_set_noise(emd_ctx *ctx, int model, double nu);
 /* Self-test of failure detection: launches, on ctx's stream, one CTA that
  * waits on an mbarrier nothing ever arrives on, with the same bounded-wait
  * code the kernels use but a limit of `spins` polls. The wait gives up, the
- * kernel records the timeout in the context's device error word and exits;
- * the call returns EMD_ETIMEOUT (the expected outcome) and clears the word,
- * leaving the context usable. EMD_OK would mean the wait did not give up. */
+ * kernel records the timeout in the context's device error word and exits.
+ * Then one thread waits, the same way as the halo-exchange kernel's
+ * dependency waits, for a counter nothing increments (`spins` polls), and
+ * once more after giving up: that second wait must return at once because
+ * the first raised the kernel's abort flag. The call returns EMD_ETIMEOUT
+ * (the expected outcome) when both behave, and clears the word, leaving the
+ * context usable. EMD_OK would mean a wait did not give up. */
 int emd_selftest_wait_timeout(emd_ctx *ctx, int spins);
 
 /* Inspection: the numerator N ((rH) x (rW)) and the weights u (n x H x W)

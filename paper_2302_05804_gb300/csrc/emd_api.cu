@@ -819,7 +819,12 @@ int emd_selftest_wait_timeout(emd_ctx* c, int spins) {
     return EMD_EINVAL;
   }
   DeviceGuard dg(c->device);
+  // the mbarrier wait of the staging copies
   CK(emd::launch_wait_selftest((uint32_t)spins, c->err, c->st));
+  const int rc = check_device_error(c);
+  if (rc != EMD_ETIMEOUT) return rc;
+  // the flag waits of the halo-exchange kernel, and their abort flag
+  CK(emd::launch_flag_wait_selftest((uint32_t)spins, c->part, c->err, c->st));
   return check_device_error(c);
 }
 

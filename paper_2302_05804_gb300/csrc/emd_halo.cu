@@ -86,11 +86,12 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Bounded wait for *p >= v. Gives up after kPollLimit polls (raising the
+// Bounded wait for *p >= v. Gives up after `limit` polls (raising the
 // abort flag ctrl[2]) or at once when another CTA has already given up.
-__device__ bool wait_geq(const int* p, int v, unsigned long long* ctrl) {
+__device__ bool wait_geq(const int* p, int v, unsigned long long* ctrl,
+                         uint32_t limit = kPollLimit) {
   const volatile unsigned long long* abort_flag = ctrl + 2;
-  for (uint32_t i = 0; i < kPollLimit; ++i) {
+  for (uint32_t i = 0; i < limit; ++i) {
     if (ld_acquire(p) >= v) return true;
     if (*abort_flag) return false;
     __nanosleep(200);
@@ -500,7 +501,30 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Self-test of the flag waits (no fault, no hang): the first wait is for a
+// counter nothing increments and must give up after `limit` polls, raising
+// the abort flag; the second, with the kernel's own poll limit, must then
+// return at once. Only if both behave is the timeout recorded in *err.
+__global__ void flag_wait_selftest_kernel(uint32_t limit, int* flags, unsigned long long* ctrl,
+                                          int* err) {
+  if (threadIdx.x != 0) return;
+  const bool first = wait_geq(flags, 1, ctrl, limit);
+  const bool second = wait_geq(flags + 1, 1, ctrl);
+  if (!first && !second && *reinterpret_cast<volatile unsigned long long*>(ctrl + 2) != 0ull)
+    atomicOr(err, kErrTimeout);
+}
+
 }  // namespace
+
+cudaError_t launch_flag_wait_selftest(uint32_t limit, void* scratch, int* err, cudaStream_t st) {
+  // scratch: 64 zeroed bytes: two counters, then the three control words
+  int* flags = static_cast<int*>(scratch);
+  unsigned long long* ctrl = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + 8);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 64, st);
+  if (e != cudaSuccess) return e;
+  flag_wait_selftest_kernel<<<1, 32, 0, st>>>(limit, flags, ctrl, err);
+  return cudaGetLastError();
+}
 
 HaloPlan halo_plan(const Shape& s, int ne) {
   HaloPlan p;

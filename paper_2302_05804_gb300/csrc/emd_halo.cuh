@@ -38,5 +38,9 @@ void halo_bind(const Shape& s, bool student, void* buf, HaloLaunch* h);
 // a.Den; the Gaussian update of Eq. (2) with numerator a.N, or (a.nu > 0) the
 // heavy-tailed step with N' accumulated in a.Nw
 cudaError_t launch_halo_iter(const Shape& s, const HaloLaunch& h, cudaStream_t st);
+// one thread waits on a counter nothing increments (bounded by `limit`
+// polls), then once more after its abort flag is up; records the timeout in
+// *err only if both waits gave up. scratch: 64 bytes of device memory.
+cudaError_t launch_flag_wait_selftest(uint32_t limit, void* scratch, int* err, cudaStream_t st);
 
 }  // namespace emd

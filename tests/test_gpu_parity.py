@@ -244,9 +244,14 @@ def test_invalid_data_and_state_errors(emd):
 def test_bounded_wait_gives_up_and_context_stays_usable(emd):
     # failure detection without a fault: a wait on a barrier nothing arrives
     # on must give up, report EMD_ETIMEOUT, and leave the context working
+    # (an mbarrier wait, then the halo kernel's flag waits: the second flag
+    # wait must end at once on the abort flag, not after its own ~2 s limit)
+    import time
     p = make("hsc", H=48, W=40, n=2, K=7, n_points=10, n_gal=1)
     d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    t0 = time.perf_counter()
     rc = emd.emd_selftest_wait_timeout(d.ctx, 2000)
+    assert time.perf_counter() - t0 < 1.0
     assert rc == emd.EMD_ETIMEOUT, rc
     assert "wait" in emd.emd_last_error()
     d.set_frames(p.y, p.v, p.f, p.mask)
