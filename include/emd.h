@@ -220,18 +220,23 @@ int emd_get_weights(emd_ctx *ctx, float *out);
 
 /* ---------------------------------------------------------------------------
  * Batching: many deconvolution jobs (contexts of any shapes) advance one EM
- * iteration per emd_batch_step, all in ONE persistent kernel launch (CUDA
- * pairs of CTAs claim (job, 128x128 tile) work items from a device counter;
- * items of finished jobs are skipped). The step (counter reset, persistent
- * kernel, per-job advance) is captured once as a CUDA graph and replayed.
+ * iteration per emd_batch_step. FP32 direct jobs run in ONE persistent
+ * launch of the halo-exchange kernel whose work list merges every job's
+ * (forward, adjoint) x (exposure, tile) items, each job keeping its own
+ * order and w ring (EMD_PREC_FP32), or of the CTA-pair kernel, whose pairs
+ * claim (job, 128 x 128 tile) items (EMD_PREC_FP32_PAIR); FFT-form jobs
+ * run in persistent FFT forward and adjoint launches. The step (persistent
+ * kernels, per-job advance) is captured once as a CUDA graph and replayed.
  * Jobs may join or leave between steps (continuous batching); a job gives
  * bit-for-bit the same iterates in a batch as with emd_iterate alone.
  *
- * Work-list order and the number of resident CTA pairs are chosen by an
- * online autotuner: the first steps of each new job mix (a signature of the
- * active jobs' size class, Kc, r and exposure count) each run one candidate
- * configuration, timed with CUDA events; the fastest is kept for that mix.
- * Batched jobs use the FP32 kernel (EMD_PREC_FP32).
+ * An online autotuner picks, per job mix (a signature of the active jobs'
+ * size class, Kc, r, exposure count and mode), the FP32 jobs' kernel form
+ * and work order and the resident CTA count: the first steps of a new mix
+ * each run one candidate (halo-exchange kernel with jobs interleaved
+ * round-robin or most expensive first; CTA pairs, all or 3/4 resident),
+ * timed with CUDA events, and the fastest is kept. Heavy-tailed noise is
+ * not batched.
  * -------------------------------------------------------------------------*/
 typedef struct emd_batch emd_batch;
 
@@ -263,8 +268,10 @@ int emd_batch_remaining(emd_batch *b, int slot);
 int emd_batch_sync(emd_batch *b);
 
 /* The autotuner's current choice: resident CTA pairs, work order (0 =
- * job-major, 1 = most expensive jobs first) and the maximum pairs. */
-int emd_batch_config(emd_batch *b, int *clusters, int *order, int *max_clusters);
+ * job-major, or round-robin over jobs in the halo-exchange form; 1 = most
+ * expensive jobs first), the maximum pairs, and the FP32 jobs' form (0 =
+ * halo-exchange kernel, 1 = CTA-pair kernel). Any pointer may be NULL. */
+int emd_batch_config(emd_batch *b, int *clusters, int *order, int *max_clusters, int *form);
 
 /*
  * emd_frame_stats_noalloc -- per-exposure FP64 frame statistics without any

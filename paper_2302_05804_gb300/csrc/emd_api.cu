@@ -883,10 +883,12 @@ int emd_loglik(emd_ctx* c, double* out, double* chi2) {
 namespace {
 
 constexpr int kBatchItemCap = 1 << 20;  // (job, tile) work items per step
+constexpr int kHaloItemCap = 1 << 22;   // (job, position) items of the halo kernel per step
 
 struct TuneChoice {
   int clusters = 0;
-  int order = 1;  // 0: job-major, 1: most expensive jobs first
+  int order = 1;  // 0: job-major (halo form: round-robin over jobs), 1: most expensive jobs first
+  int form = 0;   // FP32 jobs: 0 = halo-exchange kernel, 1 = CTA-pair kernel (same iterates)
 };
 
 }  // namespace
@@ -914,7 +916,14 @@ struct emd_batch {
   int* d_fnitems = nullptr;
   int* d_fcounters = nullptr;
   int fft_ctas = 0;
-  bool has_direct = false, has_fft = false;
+  // FP32 jobs on the halo-exchange kernel: table, (job, position) list, claim counters
+  emd::HaloBatchJob* d_hjobs = nullptr;
+  int2* d_hitems = nullptr;
+  int* d_hnitems = nullptr;
+  unsigned long long* d_hctrl = nullptr;
+  char* harena = nullptr;
+  int halo_ctas = 0;
+  bool has_direct = false, has_fft = false, has_halo = false;
   // captured step graphs, one per (cluster count, parts present)
   std::map<int, cudaGraphExec_t> graphs;
   // autotuner: decision per composition, and the candidates still to try
@@ -949,6 +958,9 @@ std::string composition_signature(emd_batch* b) {
 int upload_table(emd_batch* b) {
   std::vector<emd::BatchJob> tab(b->job.size());
   std::vector<emd::FftBatchJob> ftab(b->job.size());
+  std::vector<emd::HaloBatchJob> htab(b->job.size());
+  struct Hj { long long cost; int job; long long len; };
+  std::vector<Hj> hjobs;
   struct It { long long cost; int job, tile; };
   std::vector<It> its;
   std::vector<int2> fitems;
@@ -957,6 +969,7 @@ int upload_table(emd_batch* b) {
     emd::BatchJob& J = tab[i];
     memset(&J, 0, sizeof(J));
     memset(&ftab[i], 0, sizeof(ftab[i]));
+    memset(&htab[i], 0, sizeof(htab[i]));
     if (!c) continue;
     if (c->prec == EMD_PREC_FFT_FP32) {
       emd::FftBatchJob& F = ftab[i];
@@ -977,6 +990,23 @@ int upload_table(emd_batch* b) {
       if (F.remaining > 0)
         for (int t = 0; t < emd::fft_tiles_total(c->s); ++t) fitems.push_back(make_int2((int)i, t));
       continue;  // not in the direct table (remaining 0 there)
+    }
+    if (c->prec == EMD_PREC_FP32 && b->cur.form == 0 && c->halo_arena && b->remaining[i] > 0) {
+      emd::HaloBatchJob& Hj = htab[i];
+      Hj.s = c->s;
+      for (int k = 0; k < 2; ++k) {
+        const int save = c->cur;
+        c->cur = k;
+        Hj.h[k] = c->halo;
+        Hj.h[k].a = fused_args(c);
+        c->cur = save;
+      }
+      Hj.pl = emd::halo_plan(c->s, c->s.n);
+      Hj.cur = c->cur;
+      Hj.remaining = b->remaining[i];
+      hjobs.push_back({(long long)c->s.n * c->s.R2 * c->s.Kc * c->s.Kc * Hj.pl.T, (int)i,
+                       2 * Hj.pl.NT});
+      continue;  // not in the CTA-pair table (remaining 0 there)
     }
     J.s = c->s;
     for (int k = 0; k < 2; ++k) {
@@ -1000,6 +1030,29 @@ int upload_table(emd_batch* b) {
   std::vector<int2> items(its.size());
   for (size_t k = 0; k < its.size(); ++k) items[k] = make_int2(its[k].job, its[k].tile);
   const int n = (int)items.size();
+  // halo-exchange jobs: each job's claim sequence in its own order, merged
+  // round-robin (order 0) or job after job, most expensive first (order 1)
+  std::vector<int2> hitems;
+  {
+    long long tot = 0;
+    for (auto& j : hjobs) tot += j.len;
+    if (tot > kHaloItemCap) {
+      set_err("emd_batch_step: more than %d halo work items in one step", kHaloItemCap);
+      return EMD_EINVAL;
+    }
+    hitems.reserve((size_t)tot);
+    if (b->cur.order == 1) {
+      std::stable_sort(hjobs.begin(), hjobs.end(),
+                       [](const Hj& x, const Hj& y) { return x.cost > y.cost; });
+      for (auto& j : hjobs)
+        for (long long q = 0; q < j.len; ++q) hitems.push_back(make_int2(j.job, (int)q));
+    } else {
+      for (long long q = 0; (long long)hitems.size() < tot; ++q)
+        for (auto& j : hjobs)
+          if (q < j.len) hitems.push_back(make_int2(j.job, (int)q));
+    }
+  }
+  const int nh = (int)hitems.size();
   CK(cudaMemcpyAsync(b->d_jobs, tab.data(), tab.size() * sizeof(emd::BatchJob),
                      cudaMemcpyHostToDevice, b->st));
   if (n) CK(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int2),
@@ -1011,17 +1064,24 @@ int upload_table(emd_batch* b) {
   if (nf) CK(cudaMemcpyAsync(b->d_fitems, fitems.data(), fitems.size() * sizeof(int2),
                              cudaMemcpyHostToDevice, b->st));
   CK(cudaMemcpyAsync(b->d_fnitems, &nf, sizeof(int), cudaMemcpyHostToDevice, b->st));
+  CK(cudaMemcpyAsync(b->d_hjobs, htab.data(), htab.size() * sizeof(emd::HaloBatchJob),
+                     cudaMemcpyHostToDevice, b->st));
+  if (nh) CK(cudaMemcpyAsync(b->d_hitems, hitems.data(), hitems.size() * sizeof(int2),
+                             cudaMemcpyHostToDevice, b->st));
+  CK(cudaMemcpyAsync(b->d_hnitems, &nh, sizeof(int), cudaMemcpyHostToDevice, b->st));
   CK(cudaStreamSynchronize(b->st));
   b->njobs_table = (int)tab.size();
   b->has_direct = n > 0;
   b->has_fft = nf > 0;
+  b->has_halo = nh > 0;
   return EMD_OK;
 }
 
 int get_graph(emd_batch* b, int clusters, cudaGraphExec_t* out) {
   // a step: the persistent direct kernel over the FP32 jobs' tiles, then the
   // persistent FFT forward and adjoint kernels over the FFT jobs' tiles
-  const int key = clusters | (b->has_direct ? 1 << 20 : 0) | (b->has_fft ? 1 << 21 : 0);
+  const int key = clusters | (b->has_direct ? 1 << 20 : 0) | (b->has_fft ? 1 << 21 : 0) |
+                  (b->has_halo ? 1 << 22 : 0);
   auto it = b->graphs.find(key);
   if (it != b->graphs.end()) {
     *out = it->second;
@@ -1033,6 +1093,13 @@ int get_graph(emd_batch* b, int clusters, cudaGraphExec_t* out) {
   if (b->has_direct)
     e = emd::launch_batch(b->d_jobs, b->max_jobs, b->d_items, b->d_nitems, b->d_counter, b->d_err,
                           clusters, b->smem, b->st);
+  if (e == cudaSuccess && b->has_halo) {
+    // the halo kernel's share of the CTAs follows the tuned cluster count
+    int ctas = b->halo_ctas * clusters / (b->max_clusters > 0 ? b->max_clusters : 1);
+    if (ctas < 1) ctas = 1;
+    e = emd::launch_halo_batch(b->d_hjobs, b->max_jobs, b->d_hitems, b->d_hnitems, b->d_hctrl,
+                               b->d_err, ctas, b->st);
+  }
   if (e == cudaSuccess && b->has_fft)
     e = emd::launch_fft_batch(b->d_fjobs, b->max_jobs, b->d_fitems, b->d_fnitems, b->d_fcounters,
                               b->fft_ctas, b->st);
@@ -1106,11 +1173,30 @@ emd_batch* emd_batch_create(int max_jobs) {
   }
   b->smem = emd::batch_smem_bytes();
   b->max_clusters = emd::batch_max_clusters(b->smem);
-  if (b->max_clusters <= 0) {
-    set_err("emd_batch_create: the persistent kernel cannot be resident");
+  b->halo_ctas = emd::halo_batch_ctas();
+  if (b->max_clusters <= 0 || b->halo_ctas <= 0) {
+    set_err("emd_batch_create: the persistent kernels cannot be resident");
     cudaFree(b->arena);
     delete b;
     return nullptr;
+  }
+  {
+    // halo-exchange jobs: table, work list, item count, claim counters
+    const size_t hjb = (sizeof(emd::HaloBatchJob) * max_jobs + 255) & ~(size_t)255;
+    const size_t hib = sizeof(int2) * (size_t)kHaloItemCap;
+    void* hp = nullptr;
+    if (cudaMalloc(&hp, hjb + hib + 512) != cudaSuccess) {
+      cudaGetLastError();
+      set_err("emd_batch_create: out of device memory");
+      cudaFree(b->arena);
+      delete b;
+      return nullptr;
+    }
+    b->harena = static_cast<char*>(hp);
+    b->d_hjobs = reinterpret_cast<emd::HaloBatchJob*>(b->harena);
+    b->d_hitems = reinterpret_cast<int2*>(b->harena + hjb);
+    b->d_hnitems = reinterpret_cast<int*>(b->harena + hjb + hib);
+    b->d_hctrl = reinterpret_cast<unsigned long long*>(b->harena + hjb + hib + 256);
   }
   b->cur.clusters = b->max_clusters;
   if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1121,11 +1207,15 @@ emd_batch* emd_batch_create(int max_jobs) {
   }
   b->own_stream = true;
   // zeroed on the batch's own stream, ahead of every table upload and step
-  if (cudaMemsetAsync(b->arena, 0, total, b->st) != cudaSuccess) {
+  if (cudaMemsetAsync(b->arena, 0, total, b->st) != cudaSuccess ||
+      cudaMemsetAsync(b->harena, 0, (size_t)(reinterpret_cast<char*>(b->d_hitems) - b->harena),
+                      b->st) != cudaSuccess ||
+      cudaMemsetAsync(b->d_hnitems, 0, 512, b->st) != cudaSuccess) {
     cudaGetLastError();
     set_err("emd_batch_create: memset failed");
     cudaStreamDestroy(b->st);
     cudaFree(b->arena);
+    cudaFree(b->harena);
     delete b;
     return nullptr;
   }
@@ -1143,6 +1233,7 @@ void emd_batch_destroy(emd_batch* b) {
   cudaEventDestroy(b->e0);
   cudaEventDestroy(b->e1);
   cudaFree(b->arena);
+  cudaFree(b->harena);
   delete b;
 }
 
@@ -1176,6 +1267,10 @@ int emd_batch_add(emd_batch* b, emd_ctx* c, int iterations) {
       if (c->prec == EMD_PREC_FFT_FP32 && !c->fft_ready) {
         CK(emd::launch_fft_spectra(c->s, c->ka, c->fft_spec, c->st));
         c->fft_ready = true;
+      }
+      if (c->prec == EMD_PREC_FP32) {
+        bool ok = false;  // without a ring (too many items) the job runs the CTA-pair form
+        if (int rc = ensure_halo_arena(c, &ok)) return rc;
       }
       CK(cudaStreamSynchronize(c->st));
       b->job[i] = c;
@@ -1228,18 +1323,22 @@ int emd_batch_step(emd_batch* b, int* finished) {
     b->trial_ms.clear();
     auto it = b->tuned.find(sig);
     if (it != b->tuned.end()) {
-      if (it->second.order != b->cur.order) b->dirty = true;
+      if (it->second.order != b->cur.order || it->second.form != b->cur.form) b->dirty = true;
       b->cur = it->second;
     } else {
+      // candidates: the FP32 jobs' form (halo-exchange: round-robin or most
+      // expensive job first; CTA pairs: all or 3/4 of the resident pairs)
       const int full = b->max_clusters, part = b->max_clusters - b->max_clusters / 4;
-      for (int order = 0; order < 2; ++order)
-        for (int cl : {full, part}) b->trying.push_back({cl, order});
+      b->trying.push_back({full, 0, 0});
+      b->trying.push_back({full, 1, 0});
+      b->trying.push_back({full, 1, 1});
+      b->trying.push_back({part, 1, 1});
       b->dirty = true;
     }
   }
   if (!b->trying.empty()) {
     const TuneChoice next = b->trying[b->trial_ms.size()];
-    if (next.order != b->cur.order) b->dirty = true;
+    if (next.order != b->cur.order || next.form != b->cur.form) b->dirty = true;
     b->cur = next;
     timing = true;
   }
@@ -1261,7 +1360,8 @@ int emd_batch_step(emd_batch* b, int* finished) {
       size_t best = 0;
       for (size_t k = 1; k < b->trial_ms.size(); ++k)
         if (b->trial_ms[k] < b->trial_ms[best]) best = k;
-      if (b->trying[best].order != b->cur.order) b->dirty = true;
+      if (b->trying[best].order != b->cur.order || b->trying[best].form != b->cur.form)
+        b->dirty = true;
       b->cur = b->trying[best];
       b->tuned[b->sig] = b->cur;
       b->trying.clear();
@@ -1296,11 +1396,12 @@ int emd_batch_sync(emd_batch* b) {
   return EMD_OK;
 }
 
-int emd_batch_config(emd_batch* b, int* clusters, int* order, int* max_clusters) {
+int emd_batch_config(emd_batch* b, int* clusters, int* order, int* max_clusters, int* form) {
   if (int rc = batch_check(b)) return rc;
   if (clusters) *clusters = b->cur.clusters;
   if (order) *order = b->cur.order;
   if (max_clusters) *max_clusters = b->max_clusters;
+  if (form) *form = b->cur.form;
   return EMD_OK;
 }
 

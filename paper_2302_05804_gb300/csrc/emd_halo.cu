@@ -254,13 +254,15 @@ __device__ void prefetch_item(const Shape& s, const FusedArgs& a, const HaloShap
 // forward item then stores two tiles per slot, w = u' z and w2 = u' y, and
 // each adjoint item correlates both: Den and the numerator N' (a.Nw) of the
 // generalised EM step, in one launch per iteration.
-template <bool STUDENT>
-__global__ void __launch_bounds__(kThreads, 1)
-    halo_kernel(const Shape s, const HaloLaunch h, const HaloPlan pl) {
-  extern __shared__ __align__(128) float smem[];
-  __shared__ long long item_s;
-  __shared__ const float* nb_s[9];
-  __shared__ int last_s;
+//
+// One work item: position sq of a job's claim sequence, run by the whole
+// CTA. claim_next() is called once, after the item's window is staged (the
+// caller takes its next claim there and prefetches for it). nb_s: 9 shared
+// pointers. A wait that gives up sets timed_out.
+template <bool STUDENT, class ClaimNext>
+__device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, const HaloPlan& pl,
+                                          long long sq, float* smem, const float** nb_s,
+                                          bool& timed_out, ClaimNext&& claim_next) {
   const FusedArgs& a = h.a;
   const Geom& g = s.g;
   const HaloShape hs = halo_shape(s);
@@ -273,6 +275,199 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int ne = a.t1 - a.t0;
   const int kq = hs.ks >> 2;
   constexpr long long kSlot = STUDENT ? 2LL * kTileFloats : kTileFloats;  // floats per ring slot
+  long long id;
+  const bool fwd = decode_item(sq, NT, L, &id);
+  const int e = (int)(id / T), k = (int)(id - (long long)e * T);
+  const int ti = k / s.gx, tj = k - ti * s.gx;
+  const int i0 = ti * kTile, j0 = tj * kTile;
+  const int t = a.t0 + e;
+  bool ok = true;
+  float acc[4][16];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
+
+  if (fwd) {
+    // ---------------- forward item: w_t = u_t . F_t x on the tile ----------------
+    const long long slot = id % RS;
+    // The slot's previous tile (forward id - R) must have been read by its
+    // adjoint readers before this item's w is stored: probe their counters
+    // now (relaxed), settle after staging (a fence, or a bounded wait).
+    const int* probe = nullptr;
+    int need = 0, seen = 0;
+    if (id >= RS && tid < 9) {
+      const long long prev = id - RS;
+      const int pe = (int)(prev / T), pk = (int)(prev - (long long)pe * T);
+      const int nti = pk / s.gx + tid / 3 - 1, ntj = pk % s.gx + tid % 3 - 1;
+      if (nti >= 0 && nti < s.gy && ntj >= 0 && ntj < s.gx) {
+        probe = h.adone + nti * s.gx + ntj;
+        need = pe + 1;
+        seen = ld_relaxed(probe);
+      }
+    }
+    for (int phi = 0; phi < s.R2; ++phi) {
+      if (phi > 0) __syncthreads();  // readers of the previous phase's window are done
+      gather_plane(s, hs, sp, a.x + (long long)phi * g.plane, i0, j0);
+      const float4* kg =
+          reinterpret_cast<const float4*>(a.kf + ((long long)t * s.R2 + phi) * hs.ks);
+      for (int q = tid; q < kq; q += kThreads) reinterpret_cast<float4*>(ks)[q] = kg[q];
+      if (phi == 0) {
+        claim_next();
+        if (probe) {
+          if (seen >= need)
+            __threadfence();  // acquire: the readers' loads precede our stores
+          else
+            ok = wait_geq(probe, need, h.ctrl);
+        }
+      }
+      __syncthreads();  // also orders the slot check above before the stores below
+      corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
+    }
+    float* wt = h.ring + slot * kSlot;
+    const float* up = a.u + (long long)t * g.plane;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      // B and P are even: each row of the tile starts 8-byte aligned
+      const long long grow = (long long)(g.B + i0 + 4 * my + p) * g.P + g.B + j0 + 16 * mx;
+      const float2* u2 = reinterpret_cast<const float2*>(up + grow);
+      float4* dst = reinterpret_cast<float4*>(wt + (4 * my + p) * kTile + 16 * mx);
+      if (STUDENT) {
+        const float2* y2 = reinterpret_cast<const float2*>(a.y + (long long)t * g.plane + grow);
+        float4* dst2 = reinterpret_cast<float4*>(wt + kTileFloats + (4 * my + p) * kTile + 16 * mx);
+        const float nu1 = a.nu + 1.f;
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) {
+          const float2 ua = __ldg(u2 + 2 * c4), ub = __ldg(u2 + 2 * c4 + 1);
+          const float2 ya = __ldg(y2 + 2 * c4), yb = __ldg(y2 + 2 * c4 + 1);
+          const float uv[4] = {ua.x, ua.y, ub.x, ub.y}, yv[4] = {ya.x, ya.y, yb.x, yb.y};
+          float w[4], w2[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float z = acc[p][4 * c4 + q];
+            const float d = yv[q] - z;
+            const float us = uv[q] > 0.f ? uv[q] * nu1 / fmaf(uv[q] * d, d, a.nu) : 0.f;
+            w[q] = us * z;
+            w2[q] = us * yv[q];
+          }
+          dst[c4] = make_float4(w[0], w[1], w[2], w[3]);
+          dst2[c4] = make_float4(w2[0], w2[1], w2[2], w2[3]);
+        }
+      } else {
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) {
+          const float2 ua = __ldg(u2 + 2 * c4), ub = __ldg(u2 + 2 * c4 + 1);
+          float4 w;
+          w.x = ua.x * acc[p][4 * c4 + 0];
+          w.y = ua.y * acc[p][4 * c4 + 1];
+          w.z = ub.x * acc[p][4 * c4 + 2];
+          w.w = ub.y * acc[p][4 * c4 + 3];
+          dst[c4] = w;
+        }
+      }
+    }
+    if (__syncthreads_or(!ok)) timed_out = true;  // every w store of the CTA is issued
+    if (tid == 0) {
+      __threadfence();
+      st_release(h.fflag + slot, (int)(id + 1));
+    }
+  } else {
+    // ---------------- adjoint item: Den (+)= F_t^T w_t on the tile ----------------
+    if (tid < 9) {
+      const int nti = ti + tid / 3 - 1, ntj = tj + tid % 3 - 1;
+      const float* src = nullptr;
+      if (nti >= 0 && nti < s.gy && ntj >= 0 && ntj < s.gx) {
+        const long long fid = (long long)e * T + nti * s.gx + ntj;
+        const long long slot = fid % RS;
+        ok = wait_geq(h.fflag + slot, (int)(fid + 1), h.ctrl);
+        src = h.ring + slot * kSlot;
+      }
+      nb_s[tid] = src;
+    } else if (tid == 9 && e > 0) {
+      ok = wait_geq(h.adone + k, e, h.ctrl);  // adjoint (e - 1, k) has written Den
+    }
+    __syncthreads();
+    // pass 0: Den from w (= u z, or u' z); heavy-tailed pass 1: N' from w2 = u' y
+    for (int pass = 0; pass < (STUDENT ? 2 : 1); ++pass) {
+      if (pass > 0) __syncthreads();  // readers of pass 0's window are done
+      gather_ring(hs, sp, nb_s, pass * kTileFloats, s.hc, i0, j0);
+      if (pass == 0) claim_next();
+      float* run = pass == 0 ? a.Den : a.Nw;  // running sum over the exposures
+      for (int phi = 0; phi < s.R2; ++phi) {
+        if (phi > 0 || pass > 0) {
+          if (phi > 0) __syncthreads();  // readers of the previous phase's kernel are done
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
+        }
+        const float4* kg =
+            reinterpret_cast<const float4*>(a.ka + ((long long)t * s.R2 + phi) * hs.ks);
+        for (int q = tid; q < kq; q += kThreads) reinterpret_cast<float4*>(ks)[q] = kg[q];
+        __syncthreads();
+        // each exposure's adjoint is summed from zero, then added to the running sum
+        corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
+        const long long pbase = (long long)phi * g.plane;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const int i = i0 + 4 * my + p;
+          const long long grow = pbase + (long long)(g.B + i) * g.P + g.B + j0 + 16 * mx;
+          float2* run2 = reinterpret_cast<float2*>(run + grow);
+          if (e > 0) {
+#pragma unroll
+            for (int c2 = 0; c2 < 8; ++c2) {
+              const float2 dv = __ldcg(run2 + c2);
+              acc[p][2 * c2] = dv.x + acc[p][2 * c2];
+              acc[p][2 * c2 + 1] = dv.y + acc[p][2 * c2 + 1];
+            }
+          }
+          // not the last exposure; or the heavy-tailed Den, kept for pass 1
+          // (read back below by the thread that wrote it)
+          if (e + 1 < ne || (STUDENT && pass == 0)) {
+#pragma unroll
+            for (int c2 = 0; c2 < 8; ++c2)
+              run2[c2] = make_float2(acc[p][2 * c2], acc[p][2 * c2 + 1]);
+            continue;
+          }
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int j = j0 + 16 * mx + c;
+            if (i < g.H && j < g.W) {
+              const float d = STUDENT ? __ldcg(a.Den + grow + c) : acc[p][c];
+              const float xo = a.x[grow + c];
+              float xv = xo;
+              if (d > 0.f) {
+                const float nv = fmaxf(STUDENT ? acc[p][c] : a.N[grow + c], 0.f);
+                if (d < 1e-30f)  // denominator near zero: guarded ratio in FP64
+                  xv = (float)((double)xo * (double)nv / (double)d);
+                else
+                  xv = xo * nv / d;
+              }
+              a.xn[grow + c] = xv;
+            }
+          }
+        }
+      }
+    }
+    if (__syncthreads_or(!ok)) timed_out = true;  // all reads of the ring and Den are done
+    if (tid == 0) {
+      __threadfence();
+      st_release(h.adone + k, e + 1);
+    }
+  }
+}
+
+// One launch per EM iteration of one context (exposures [a.t0, a.t1)).
+template <bool STUDENT>
+__global__ void __launch_bounds__(kThreads, 1)
+    halo_kernel(const Shape s, const HaloLaunch h, const HaloPlan pl) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ long long item_s;
+  __shared__ const float* nb_s[9];
+  __shared__ int last_s;
+  const HaloShape hs = halo_shape(s);
+  const int tid = threadIdx.x;
+  const long long total = 2 * pl.NT;
   bool timed_out = false;
 
   // Each CTA claims one item ahead: warp 0 takes the next position and
@@ -283,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0) item_s = (long long)atomicAdd(&h.ctrl[0], 1ull);
   __syncthreads();
   long long sq = item_s;
-  while (sq < 2 * NT) {
+  while (sq < total) {
     __syncthreads();  // every thread has read item_s
     // the next claim is taken now and used after this item's window is staged,
     // so the atomic's round trip overlaps the staging loads
@@ -293,189 +488,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (tid < 32) {
         const long long nx = (long long)__shfl_sync(0xffffffffu, nx_raw, 0);
         if (tid == 0) item_s = nx;
-        if (nx < 2 * NT) prefetch_item(s, a, hs, pl, nx, tid);
+        if (nx < total) prefetch_item(s, h.a, hs, pl, nx, tid);
       }
     };
-    long long id;
-    const bool fwd = decode_item(sq, NT, L, &id);
-    const int e = (int)(id / T), k = (int)(id - (long long)e * T);
-    const int ti = k / s.gx, tj = k - ti * s.gx;
-    const int i0 = ti * kTile, j0 = tj * kTile;
-    const int t = a.t0 + e;
-    bool ok = true;
-    float acc[4][16];
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
-
-    if (fwd) {
-      // ---------------- forward item: w_t = u_t . F_t x on the tile ----------------
-      const long long slot = id % RS;
-      // The slot's previous tile (forward id - R) must have been read by its
-      // adjoint readers before this item's w is stored: probe their counters
-      // now (relaxed), settle after staging (a fence, or a bounded wait).
-      const int* probe = nullptr;
-      int need = 0, seen = 0;
-      if (id >= RS && tid < 9) {
-        const long long prev = id - RS;
-        const int pe = (int)(prev / T), pk = (int)(prev - (long long)pe * T);
-        const int nti = pk / s.gx + tid / 3 - 1, ntj = pk % s.gx + tid % 3 - 1;
-        if (nti >= 0 && nti < s.gy && ntj >= 0 && ntj < s.gx) {
-          probe = h.adone + nti * s.gx + ntj;
-          need = pe + 1;
-          seen = ld_relaxed(probe);
-        }
-      }
-      for (int phi = 0; phi < s.R2; ++phi) {
-        if (phi > 0) __syncthreads();  // readers of the previous phase's window are done
-        gather_plane(s, hs, sp, a.x + (long long)phi * g.plane, i0, j0);
-        const float4* kg =
-            reinterpret_cast<const float4*>(a.kf + ((long long)t * s.R2 + phi) * hs.ks);
-        for (int q = tid; q < kq; q += kThreads) reinterpret_cast<float4*>(ks)[q] = kg[q];
-        if (phi == 0) {
-          claim_next();
-          if (probe) {
-            if (seen >= need)
-              __threadfence();  // acquire: the readers' loads precede our stores
-            else
-              ok = wait_geq(probe, need, h.ctrl);
-          }
-        }
-        __syncthreads();  // also orders the slot check above before the stores below
-        corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
-      }
-      float* wt = h.ring + slot * kSlot;
-      const float* up = a.u + (long long)t * g.plane;
-#pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        // B and P are even: each row of the tile starts 8-byte aligned
-        const long long grow = (long long)(g.B + i0 + 4 * my + p) * g.P + g.B + j0 + 16 * mx;
-        const float2* u2 = reinterpret_cast<const float2*>(up + grow);
-        float4* dst = reinterpret_cast<float4*>(wt + (4 * my + p) * kTile + 16 * mx);
-        if (STUDENT) {
-          const float2* y2 = reinterpret_cast<const float2*>(a.y + (long long)t * g.plane + grow);
-          float4* dst2 = reinterpret_cast<float4*>(wt + kTileFloats + (4 * my + p) * kTile + 16 * mx);
-          const float nu1 = a.nu + 1.f;
-#pragma unroll
-          for (int c4 = 0; c4 < 4; ++c4) {
-            const float2 ua = __ldg(u2 + 2 * c4), ub = __ldg(u2 + 2 * c4 + 1);
-            const float2 ya = __ldg(y2 + 2 * c4), yb = __ldg(y2 + 2 * c4 + 1);
-            const float uv[4] = {ua.x, ua.y, ub.x, ub.y}, yv[4] = {ya.x, ya.y, yb.x, yb.y};
-            float w[4], w2[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float z = acc[p][4 * c4 + q];
-              const float d = yv[q] - z;
-              const float us = uv[q] > 0.f ? uv[q] * nu1 / fmaf(uv[q] * d, d, a.nu) : 0.f;
-              w[q] = us * z;
-              w2[q] = us * yv[q];
-            }
-            dst[c4] = make_float4(w[0], w[1], w[2], w[3]);
-            dst2[c4] = make_float4(w2[0], w2[1], w2[2], w2[3]);
-          }
-        } else {
-#pragma unroll
-          for (int c4 = 0; c4 < 4; ++c4) {
-            const float2 ua = __ldg(u2 + 2 * c4), ub = __ldg(u2 + 2 * c4 + 1);
-            float4 w;
-            w.x = ua.x * acc[p][4 * c4 + 0];
-            w.y = ua.y * acc[p][4 * c4 + 1];
-            w.z = ub.x * acc[p][4 * c4 + 2];
-            w.w = ub.y * acc[p][4 * c4 + 3];
-            dst[c4] = w;
-          }
-        }
-      }
-      if (__syncthreads_or(!ok)) timed_out = true;  // every w store of the CTA is issued
-      if (tid == 0) {
-        __threadfence();
-        st_release(h.fflag + slot, (int)(id + 1));
-      }
-    } else {
-      // ---------------- adjoint item: Den (+)= F_t^T w_t on the tile ----------------
-      if (tid < 9) {
-        const int nti = ti + tid / 3 - 1, ntj = tj + tid % 3 - 1;
-        const float* src = nullptr;
-        if (nti >= 0 && nti < s.gy && ntj >= 0 && ntj < s.gx) {
-          const long long fid = (long long)e * T + nti * s.gx + ntj;
-          const long long slot = fid % RS;
-          ok = wait_geq(h.fflag + slot, (int)(fid + 1), h.ctrl);
-          src = h.ring + slot * kSlot;
-        }
-        nb_s[tid] = src;
-      } else if (tid == 9 && e > 0) {
-        ok = wait_geq(h.adone + k, e, h.ctrl);  // adjoint (e - 1, k) has written Den
-      }
-      __syncthreads();
-      // pass 0: Den from w (= u z, or u' z); heavy-tailed pass 1: N' from w2 = u' y
-      for (int pass = 0; pass < (STUDENT ? 2 : 1); ++pass) {
-        if (pass > 0) __syncthreads();  // readers of pass 0's window are done
-        gather_ring(hs, sp, nb_s, pass * kTileFloats, s.hc, i0, j0);
-        if (pass == 0) claim_next();
-        float* run = pass == 0 ? a.Den : a.Nw;  // running sum over the exposures
-        for (int phi = 0; phi < s.R2; ++phi) {
-          if (phi > 0 || pass > 0) {
-            if (phi > 0) __syncthreads();  // readers of the previous phase's kernel are done
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-#pragma unroll
-              for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
-          }
-          const float4* kg =
-              reinterpret_cast<const float4*>(a.ka + ((long long)t * s.R2 + phi) * hs.ks);
-          for (int q = tid; q < kq; q += kThreads) reinterpret_cast<float4*>(ks)[q] = kg[q];
-          __syncthreads();
-          // each exposure's adjoint is summed from zero, then added to the running sum
-          corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
-          const long long pbase = (long long)phi * g.plane;
-#pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const int i = i0 + 4 * my + p;
-            const long long grow = pbase + (long long)(g.B + i) * g.P + g.B + j0 + 16 * mx;
-            float2* run2 = reinterpret_cast<float2*>(run + grow);
-            if (e > 0) {
-#pragma unroll
-              for (int c2 = 0; c2 < 8; ++c2) {
-                const float2 dv = __ldcg(run2 + c2);
-                acc[p][2 * c2] = dv.x + acc[p][2 * c2];
-                acc[p][2 * c2 + 1] = dv.y + acc[p][2 * c2 + 1];
-              }
-            }
-            // not the last exposure; or the heavy-tailed Den, kept for pass 1
-            // (read back below by the thread that wrote it)
-            if (e + 1 < ne || (STUDENT && pass == 0)) {
-#pragma unroll
-              for (int c2 = 0; c2 < 8; ++c2)
-                run2[c2] = make_float2(acc[p][2 * c2], acc[p][2 * c2 + 1]);
-              continue;
-            }
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              const int j = j0 + 16 * mx + c;
-              if (i < g.H && j < g.W) {
-                const float d = STUDENT ? __ldcg(a.Den + grow + c) : acc[p][c];
-                const float xo = a.x[grow + c];
-                float xv = xo;
-                if (d > 0.f) {
-                  const float nv = fmaxf(STUDENT ? acc[p][c] : a.N[grow + c], 0.f);
-                  if (d < 1e-30f)  // denominator near zero: guarded ratio in FP64
-                    xv = (float)((double)xo * (double)nv / (double)d);
-                  else
-                    xv = xo * nv / d;
-                }
-                a.xn[grow + c] = xv;
-              }
-            }
-          }
-        }
-      }
-      if (__syncthreads_or(!ok)) timed_out = true;  // all reads of the ring and Den are done
-      if (tid == 0) {
-        __threadfence();
-        st_release(h.adone + k, e + 1);
-      }
-    }
+    halo_item<STUDENT>(s, h, pl, sq, smem, nb_s, timed_out, claim_next);
     __syncthreads();  // readers of this item's window and kernel are done; item_s is set
     sq = item_s;
   }
@@ -484,19 +500,88 @@ __global__ void __launch_bounds__(kThreads, 1)
   // (stream order makes the reset visible to it).
   __syncthreads();
   if (tid == 0) {
-    if (timed_out) atomicOr(a.err, kErrTimeout);
+    if (timed_out) atomicOr(h.a.err, kErrTimeout);
     __threadfence();
     last_s = atomicAdd(&h.ctrl[1], 1ull) == (unsigned long long)(gridDim.x - 1);
   }
   __syncthreads();
   if (last_s) {
     __threadfence();
-    for (long long i = tid; i < RS; i += kThreads) h.fflag[i] = 0;
-    for (int i = tid; i < T; i += kThreads) h.adone[i] = 0;
+    for (long long i = tid; i < pl.R; i += kThreads) h.fflag[i] = 0;
+    for (int i = tid; i < pl.T; i += kThreads) h.adone[i] = 0;
     if (tid == 0) {
       h.ctrl[0] = 0ull;
       h.ctrl[1] = 0ull;
       h.ctrl[2] = 0ull;
+    }
+  }
+}
+
+// A batch step: the claim sequences of several contexts (one EM iteration
+// each), merged into one work list of (job, position) entries that keeps
+// each job's own order, so every wait is still on an earlier entry. Each
+// job has its own ring, flags and abort flag; the list's claim counter and
+// the finished-CTA count are the batch's. The last CTA resets the flags of
+// every job that ran.
+__global__ void __launch_bounds__(kThreads, 1)
+    halo_batch_kernel(const HaloBatchJob* __restrict__ jobs, int njobs,
+                      const int2* __restrict__ items, const int* __restrict__ n_items,
+                      unsigned long long* ctrl, int* err) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ long long item_s;
+  __shared__ const float* nb_s[9];
+  __shared__ int last_s;
+  const int tid = threadIdx.x;
+  const long long total = *n_items;
+  bool timed_out = false;
+  if (tid == 0) item_s = (long long)atomicAdd(&ctrl[0], 1ull);
+  __syncthreads();
+  long long q = item_s;
+  while (q < total) {
+    __syncthreads();  // every thread has read item_s
+    unsigned long long nx_raw = 0;
+    if (tid == 0) nx_raw = atomicAdd(&ctrl[0], 1ull);
+    const int2 it = items[q];
+    const HaloBatchJob& J = jobs[it.x];
+    const Shape s = J.s;
+    const HaloLaunch h = J.h[J.cur];
+    const HaloPlan pl = J.pl;
+    auto claim_next = [&]() {
+      if (tid < 32) {
+        const long long nx = (long long)__shfl_sync(0xffffffffu, nx_raw, 0);
+        if (tid == 0) item_s = nx;
+        if (nx < total) {
+          const int2 nit = items[nx];
+          const HaloBatchJob& NJ = jobs[nit.x];
+          prefetch_item(NJ.s, NJ.h[NJ.cur].a, halo_shape(NJ.s), NJ.pl, nit.y, tid);
+        }
+      }
+    };
+    if (J.remaining > 0) halo_item<false>(s, h, pl, it.y, smem, nb_s, timed_out, claim_next);
+    else claim_next();
+    __syncthreads();
+    q = item_s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (timed_out) atomicOr(err, kErrTimeout);
+    __threadfence();
+    last_s = atomicAdd(&ctrl[1], 1ull) == (unsigned long long)(gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last_s) {
+    __threadfence();
+    for (int j = 0; j < njobs; ++j) {
+      const HaloBatchJob& J = jobs[j];
+      if (J.remaining <= 0) continue;
+      const HaloLaunch& h = J.h[0];  // ring, flags and counters are shared by h[0], h[1]
+      for (long long i = tid; i < J.pl.R; i += kThreads) h.fflag[i] = 0;
+      for (int i = tid; i < J.pl.T; i += kThreads) h.adone[i] = 0;
+      if (tid == 0) h.ctrl[2] = 0ull;
+    }
+    if (tid == 0) {
+      ctrl[0] = 0ull;
+      ctrl[1] = 0ull;
     }
   }
 }
@@ -578,6 +663,59 @@ cudaError_t launch_halo_t(const Shape& s, const HaloLaunch& h, const HaloPlan& p
   if (grid > kHaloCtasMax) grid = kHaloCtasMax;
   if (grid > 2 * pl.NT) grid = 2 * pl.NT;
   halo_kernel<STUDENT><<<(int)grid, kThreads, smem, st>>>(s, h, pl);
+  return cudaGetLastError();
+}
+
+size_t halo_batch_smem_bytes() {
+  size_t m = 0;
+  for (int hc = 0; hc <= EMD_MAX_HC; ++hc) {
+    Shape s{};
+    s.hc = hc;
+    s.Kc = 2 * hc + 1;
+    s.KP = (s.Kc + 3) / 4 * 4;
+    const size_t b = halo_smem_bytes(s);
+    if (b > m) m = b;
+  }
+  return m;
+}
+
+namespace {
+__global__ void halo_batch_advance_kernel(HaloBatchJob* __restrict__ jobs, int njobs) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < njobs && jobs[j].remaining > 0) {
+    jobs[j].remaining -= 1;
+    jobs[j].cur ^= 1;
+  }
+}
+}  // namespace
+
+int halo_batch_ctas() {
+  const size_t smem = halo_batch_smem_bytes();
+  if (cudaFuncSetAttribute(halo_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return 0;
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_batch_kernel, kThreads, smem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms * (occ > 0 ? occ : 1);
+}
+
+cudaError_t launch_halo_batch(const HaloBatchJob* jobs, int njobs, const int2* items,
+                              const int* n_items, unsigned long long* ctrl, int* err, int ctas,
+                              cudaStream_t st) {
+  const size_t smem = halo_batch_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(halo_batch_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  halo_batch_kernel<<<ctas, kThreads, smem, st>>>(jobs, njobs, items, n_items, ctrl, err);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  halo_batch_advance_kernel<<<(njobs + 127) / 128, 128, 0, st>>>(const_cast<HaloBatchJob*>(jobs),
+                                                                 njobs);
   return cudaGetLastError();
 }
 

@@ -38,6 +38,27 @@ void halo_bind(const Shape& s, bool student, void* buf, HaloLaunch* h);
 // a.Den; the Gaussian update of Eq. (2) with numerator a.N, or (a.nu > 0) the
 // heavy-tailed step with N' accumulated in a.Nw
 cudaError_t launch_halo_iter(const Shape& s, const HaloLaunch& h, cudaStream_t st);
+// one job of a batch step (device table entry): h[c] has x = buffer c and
+// xn = buffer c^1 of the job's context; ring, flags and counters are the
+// context's own, sized for n exposures
+struct HaloBatchJob {
+  Shape s;
+  HaloLaunch h[2];
+  HaloPlan pl;     // halo_plan(s, s.n)
+  int cur;         // current x buffer
+  int remaining;   // iterations still to run (0: skipped)
+};
+// dynamic shared memory of the halo kernels for any accepted shape
+size_t halo_batch_smem_bytes();
+// CTAs of the persistent batch kernel that fit the device (0 on error)
+int halo_batch_ctas();
+// a batch step over items (job, position in the job's claim sequence):
+// persistent kernel, then the advance kernel of the jobs; on st,
+// graph-capturable (ctrl: 2 words, zero before the first launch, left zero)
+cudaError_t launch_halo_batch(const HaloBatchJob* jobs, int njobs, const int2* items,
+                              const int* n_items, unsigned long long* ctrl, int* err, int ctas,
+                              cudaStream_t st);
+
 // one thread waits on a counter nothing increments (bounded by `limit`
 // polls), then once more after its abort flag is up; records the timeout in
 // *err only if both waits gave up. scratch: 64 bytes of device memory.

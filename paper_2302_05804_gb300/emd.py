@@ -110,7 +110,7 @@ def load(build_if_missing: bool = False):
         lib.emd_batch_step.argtypes = [vp, ip]
         lib.emd_batch_remaining.argtypes = [vp, i]
         lib.emd_batch_sync.argtypes = [vp]
-        lib.emd_batch_config.argtypes = [vp, ip, ip, ip]
+        lib.emd_batch_config.argtypes = [vp, ip, ip, ip, ip]
         lib.emd_fit_psf.argtypes = [vp, i, i, i, vp, i, vp, C.c_float, C.c_float, i, vp, vp]
         lib.emd_fit_psf.restype = i
         lib.emd_set_noise.argtypes = [vp, i, C.c_double]
@@ -325,9 +325,9 @@ def emd_batch_sync(b) -> None:
 
 
 def emd_batch_config(b):
-    c, o, m = C.c_int(), C.c_int(), C.c_int()
-    _check(load().emd_batch_config(b, C.byref(c), C.byref(o), C.byref(m)))
-    return {"clusters": c.value, "order": o.value, "max_clusters": m.value}
+    c, o, m, f = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(load().emd_batch_config(b, C.byref(c), C.byref(o), C.byref(m), C.byref(f)))
+    return {"clusters": c.value, "order": o.value, "max_clusters": m.value, "form": f.value}
 
 
 # -- convenience wrapper --------------------------------------------------------

@@ -57,6 +57,7 @@ def test_batch_matches_solo_runs_bitwise():
         np.testing.assert_array_equal(ds[i].x(), solo[i])
     cfg = emd.emd_batch_config(b)
     assert 1 <= cfg["clusters"] <= cfg["max_clusters"] and cfg["order"] in (0, 1)
+    assert cfg["form"] in (0, 1)  # halo-exchange or CTA-pair kernel (tried in turn above)
     for i in range(len(probs)):
         emd.emd_batch_remove(b, slots[i])
         ds[i].close()
@@ -84,13 +85,15 @@ def test_batch_remove_midway_keeps_reached_iterate():
 
 def test_mixed_direct_and_fft_batch_matches_solo_runs_bitwise():
     """FFT-form jobs run in the persistent FFT kernels of the same step (one
-    forward launch and one adjoint launch over all their tiles); each job's
-    iterate equals its solo run (direct or FFT) bit for bit, including r = 2
-    and a job that joins mid-run."""
+    forward launch and one adjoint launch over all their tiles), FP32 jobs in
+    the halo-exchange kernel's merged work list (or, while the tuner tries
+    it, the CTA-pair kernel), an EMD_PREC_FP32_PAIR job always in the
+    CTA-pair kernel; each job's iterate equals its solo run bit for bit,
+    including r = 2 and a job that joins mid-run."""
     from paper_2302_05804_gb300 import emd
     iters = [5, 4, 6, 3, 4]
     forms = [emd.EMD_PREC_FFT_FP32, emd.EMD_PREC_FP32, emd.EMD_PREC_FFT_FP32,
-             emd.EMD_PREC_FFT_FP32, emd.EMD_PREC_FP32]
+             emd.EMD_PREC_FP32_PAIR, emd.EMD_PREC_FP32]
     probs = [make(i) for i in range(len(JOBS))]
 
     def ctx(i):
