@@ -854,8 +854,19 @@ int emd_loglik(emd_ctx* c, double* out, double* chi2) {
   }
   DeviceGuard dg(c->device);
   emd::FusedArgs a = fused_args(c);
-  CK(emd::launch_fused(c->s, a, 2, c->part, c->st));
-  CK(emd::launch_reduce_final(c->part, emd::fused_blocks(c->s), 1, c->sums + 4, c->st));
+  // the forward model once per pixel (the CTA-pair kernel's halo form under
+  // EMD_PREC_FP32_PAIR); FP64 partial sums added in a fixed order
+  const int max_parts = (int)((c->L.sums - c->L.part) / sizeof(double));
+  int nparts = 0;
+  if (c->prec != EMD_PREC_FP32_PAIR && max_parts >= c->s.gx * c->s.gy) {
+    cudaError_t e = cudaSuccess;
+    nparts = emd::launch_halo_chi2(c->s, a, c->part, max_parts, c->st, &e);
+    CK(e);
+  } else {
+    CK(emd::launch_fused(c->s, a, 2, c->part, c->st));
+    nparts = emd::fused_blocks(c->s);
+  }
+  CK(emd::launch_reduce_final(c->part, nparts, 1, c->sums + 4, c->st));
   double h = 0.0;
   CK(cudaMemcpyAsync(&h, c->sums + 4, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   if (int rc = check_device_error(c)) return rc;

@@ -1,6 +1,7 @@
-// emd_corr.cuh -- the register-blocked FP32 correlation shared by the
-// direct-form kernels (the fused CTA-pair kernel and the halo-exchange
-// kernel): a thread accumulates an RY x RX block of outputs
+// emd_corr.cuh -- device code shared by the direct-form kernels (the fused
+// CTA-pair kernel and the halo-exchange kernel): an FP64 block sum, and the
+// register-blocked FP32 correlation, where a thread accumulates an RY x RX
+// block of outputs
 //     acc[p][c] += sum_{a < Kc, b < KP} k[a][b] src[oy + p + a][ox + c + b]
 // from a shared-memory plane, one 16-byte kernel quad and a (RX + 4)-float
 // window of the source row at a time.
@@ -67,6 +68,20 @@ __device__ __forceinline__ void corr_tile(float (&acc)[RY][RX], const SPlane& sr
     else
       corr_row<RY, RX, true>(acc, row, ks, KP, Kc, s);
   }
+}
+
+// Sum of v over the CTA, in FP64 (warp shuffles, then the warps in order).
+__device__ __forceinline__ double block_sum_f64(double v, double* red /* >= 8 */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  return s;  // valid in thread 0
 }
 
 }  // namespace emd

@@ -586,6 +586,78 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// The data term of the log-likelihood (Eq. (1); the Student-t term with
+// STUDENT): sum over valid pixels of u (y - z)^2, z = F_t x, in FP64 -- the
+// forward model alone, each pixel once. Items (tile, group of exposures)
+// are taken in a fixed stride by a persistent grid and each writes its own
+// partial sum, so the total (a fixed-order sum of the partials) does not
+// depend on scheduling. For r = 1 the x window is staged once per item.
+template <bool STUDENT>
+__global__ void __launch_bounds__(kThreads, 1)
+    halo_chi2_kernel(const Shape s, const FusedArgs a, const int groups,
+                     double* __restrict__ part) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ double red[kThreads / 32];
+  const Geom& g = s.g;
+  const HaloShape hs = halo_shape(s);
+  const SPlane sp{smem, hs.pitch, 2};
+  float* ks = smem + hs.buf;
+  const int tid = threadIdx.x;
+  const int my = tid & 31, mx = tid >> 5;
+  const int kq = hs.ks >> 2;
+  const int nitems = s.gx * s.gy * groups;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int k = item / groups, grp = item - k * groups;
+    const int ti = k / s.gx, tj = k - ti * s.gx;
+    const int i0 = ti * kTile, j0 = tj * kTile;
+    const int t0 = (int)((long long)s.n * grp / groups);
+    const int t1 = (int)((long long)s.n * (grp + 1) / groups);
+    double chi = 0.0;
+    for (int t = t0; t < t1; ++t) {
+      float acc[4][16];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
+      for (int phi = 0; phi < s.R2; ++phi) {
+        __syncthreads();  // readers of the previous window and kernel are done
+        if (s.R2 > 1 || t == t0) gather_plane(s, hs, sp, a.x + (long long)phi * g.plane, i0, j0);
+        const float4* kg =
+            reinterpret_cast<const float4*>(a.kf + ((long long)t * s.R2 + phi) * hs.ks);
+        for (int q = tid; q < kq; q += kThreads) reinterpret_cast<float4*>(ks)[q] = kg[q];
+        if (tid < 32 && phi == 0 && t + 1 < t1) {  // the next exposure's u and y into L2
+          prefetch_rect(a.u + (long long)(t + 1) * g.plane, g.P, g.B + i0, kTile, g.B + j0,
+                        kTile, tid);
+          prefetch_rect(a.y + (long long)(t + 1) * g.plane, g.P, g.B + i0, kTile, g.B + j0,
+                        kTile, tid);
+        }
+        __syncthreads();
+        corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
+      }
+      const long long tp = (long long)t * g.plane;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int i = i0 + 4 * my + p;
+        const long long grow = tp + (long long)(g.B + i) * g.P + g.B + j0 + 16 * mx;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int j = j0 + 16 * mx + c;
+          const float uv = a.u[grow + c];
+          if (i < g.H && j < g.W && uv != 0.f) {
+            const double d = (double)a.y[grow + c] - (double)acc[p][c];
+            if (STUDENT)
+              chi += ((double)a.nu + 1.0) * log1p((double)uv * d * d / (double)a.nu);
+            else
+              chi += (double)uv * d * d;
+          }
+        }
+      }
+    }
+    const double tot = block_sum_f64(chi, red);
+    if (tid == 0) part[item] = tot;
+  }
+}
+
 // Self-test of the flag waits (no fault, no hang): the first wait is for a
 // counter nothing increments and must give up after `limit` polls, raising
 // the abort flag; the second, with the kernel's own poll limit, must then
@@ -717,6 +789,33 @@ cudaError_t launch_halo_batch(const HaloBatchJob* jobs, int njobs, const int2* i
   halo_batch_advance_kernel<<<(njobs + 127) / 128, 128, 0, st>>>(const_cast<HaloBatchJob*>(jobs),
                                                                  njobs);
   return cudaGetLastError();
+}
+
+int launch_halo_chi2(const Shape& s, const FusedArgs& a, double* part, int max_parts,
+                     cudaStream_t st, cudaError_t* err) {
+  const int T = s.gx * s.gy;
+  int groups = max_parts / T;
+  if (groups > s.n) groups = s.n;
+  if (groups < 1) {
+    *err = cudaErrorInvalidValue;
+    return 0;
+  }
+  const size_t smem = halo_smem_bytes(s);
+  auto kern = a.nu > 0.f ? halo_chi2_kernel<true> : halo_chi2_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, sms = 0, occ = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+  if (e != cudaSuccess) {
+    *err = e;
+    return 0;
+  }
+  long long grid = (long long)sms * (occ > 0 ? occ : 1);
+  if (grid > (long long)T * groups) grid = (long long)T * groups;
+  kern<<<(int)grid, kThreads, smem, st>>>(s, a, groups, part);
+  *err = cudaGetLastError();
+  return T * groups;
 }
 
 cudaError_t launch_halo_iter(const Shape& s, const HaloLaunch& h, cudaStream_t st) {

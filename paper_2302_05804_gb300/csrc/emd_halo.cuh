@@ -59,6 +59,12 @@ cudaError_t launch_halo_batch(const HaloBatchJob* jobs, int njobs, const int2* i
                               const int* n_items, unsigned long long* ctrl, int* err, int ctas,
                               cudaStream_t st);
 
+// The log-likelihood's data term (mode 2 of the fused kernel) with each
+// forward pixel computed once: partial sums into part[0 .. returned count),
+// to be added in index order (at most max_parts; needs max_parts >= gx*gy).
+int launch_halo_chi2(const Shape& s, const FusedArgs& a, double* part, int max_parts,
+                     cudaStream_t st, cudaError_t* err);
+
 // one thread waits on a counter nothing increments (bounded by `limit`
 // polls), then once more after its abort flag is up; records the timeout in
 // *err only if both waits gave up. scratch: 64 bytes of device memory.

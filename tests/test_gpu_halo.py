@@ -160,3 +160,32 @@ def test_switching_noise_models_in_one_context(emd):
             d.close()
 
     assert np.array_equal(go(emd.EMD_PREC_FP32), go(emd.EMD_PREC_FP32_PAIR))
+
+
+@pytest.mark.parametrize("H,W,n,K,r,nu", [(300, 257, 5, 43, 1, 0.0), (200, 330, 4, 9, 2, 0.0),
+                                          (520, 400, 6, 15, 1, 3.0), (1024, 1024, 12, 43, 1, 0.0)])
+def test_loglik_against_cta_pair_kernel(emd, H, W, n, K, r, nu):
+    """emd_loglik's data term from the forward-only halo kernel (each pixel
+    once, FP64 partial sums per (tile, exposure group) added in a fixed
+    order) against the CTA-pair kernel's: the same FP32 model values summed
+    in another order, so equal to FP64 rounding; and repeatable bit for bit."""
+    p = synth.make_problem("hsc", H=H, W=W, n=n, K=K, r=r, mask_frac=0.05,
+                           fwhm=(2.0 * r, 5.0 * r), n_points=60, n_gal=4, seed_offset=H + n)
+    x0 = start(p, seed=5)
+    out = {}
+    for prec in (emd.EMD_PREC_FP32, emd.EMD_PREC_FP32_PAIR):
+        d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+        try:
+            d.set_frames(p.y, p.v, p.f, p.mask)
+            if nu > 0:
+                d.set_noise(emd.EMD_NOISE_STUDENT_T, nu)
+            d.set_precision(prec)
+            d.set_x(x0)
+            out[prec] = [d.loglik(), d.loglik()]
+        finally:
+            d.close()
+    (ll_a, chi_a), (ll_a2, chi_a2) = out[emd.EMD_PREC_FP32]
+    (ll_b, chi_b), _ = out[emd.EMD_PREC_FP32_PAIR]
+    assert ll_a == ll_a2 and chi_a == chi_a2
+    assert abs(chi_a - chi_b) <= 1e-12 * abs(chi_b)
+    assert abs(ll_a - ll_b) <= 1e-12 * abs(ll_b)
