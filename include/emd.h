@@ -165,9 +165,9 @@ int emd_loglik(emd_ctx *ctx, double *out, double *chi2);
  * first such iteration. EMD_PREC_FP32_PAIR gives the same iterates bit for
  * bit from the kernel that keeps u_t z_t in the shared memory of a CTA
  * pair per tile and recomputes the forward model on a 2 hc halo around it
- * (no extra memory, 1.48x the multiply-adds at K = 43); the heavy-tailed
- * model and batched jobs run that kernel in the FP32 modes, and emd_loglik
- * in every mode. */
+ * (no extra memory, 1.48x the multiply-adds at K = 43). emd_loglik
+ * computes the forward model once per pixel in every mode except
+ * EMD_PREC_FP32_PAIR. */
 int emd_set_precision(emd_ctx *ctx, int mode);
 
 /*
