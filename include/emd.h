@@ -159,8 +159,8 @@ int emd_loglik(emd_ctx *ctx, double *out, double *chi2);
  * scratch of r^2 spectra (66.5 KB each), allocated on first selection.
  * EMD_PREC_FP32 (Gaussian noise) runs one persistent kernel per iteration
  * that computes each pixel's forward model once and passes the weighted
- * model images u_t z_t between 128 x 128 tiles through a ring of tile
- * buffers in device memory (about 550 tiles of 64 KB at 4096^2, fewer for
+ * model images u_t z_t between 64 x 128 tiles through a ring of tile
+ * buffers in device memory (about 1030 tiles of 32 KB at 4096^2, fewer for
  * smaller images; emd_ctx_bytes_precision counts them), allocated at the
  * first such iteration. EMD_PREC_FP32_PAIR gives the same iterates bit for
  * bit from the kernel that keeps u_t z_t in the shared memory of a CTA

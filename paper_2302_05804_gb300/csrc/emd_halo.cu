@@ -1,7 +1,7 @@
 // emd_halo.cu -- the FP32 direct EM iteration of Sec. 2, Eq. (2) (Eq. (3)
 // for r > 1) as one persistent kernel over two kinds of work items:
 //
-//   forward item (t, tile)   w_t = u_t . (F_t x) on the 128 x 128 tile,
+//   forward item (t, tile)   w_t = u_t . (F_t x) on the 64 x 128 tile,
 //                            stored in one slot of a ring of tile buffers
 //   adjoint item (t, tile)   Den += F_t^T w_t on the tile, reading w_t of the
 //                            tile and of its 8 neighbours from the ring; the
@@ -11,9 +11,13 @@
 // emd_direct.cu keeps w in shared memory instead and so recomputes a 2*hc
 // halo around each tile (176^2 forward outputs per 128^2 tile at K = 43:
 // 1.48x the algorithmic FMAs overall against 1.0x here). What this costs is
-// w passing through global memory: a ring of R tile buffers (about 550 at
-// 4096^2, 36 MB), written and read again within a few hundred items, so it
+// w passing through global memory: a ring of R tile buffers (about 1030 at
+// 4096^2, 34 MB), written and read again within a few hundred items, so it
 // stays in L2; no per-exposure image is kept.
+//
+// Tiles are 64 rows x 128 columns, one per CTA of 128 threads (a 4 x 16
+// block of outputs per thread), two CTAs per SM: when one waits at a
+// barrier or on its staging loads, the other keeps the FMA pipes busy.
 //
 // Item order. One atomic counter hands out a fixed sequence: the first L
 // forward items, then adjoint and forward items alternately, then the last
@@ -39,8 +43,10 @@ namespace emd {
 
 namespace {
 
-constexpr int kTileFloats = kTile * kTile;
-constexpr int kHaloCtasMax = 160;      // grid cap (>= SMs of one GB300); sizes the ring
+constexpr int kHT = 128;   // threads per CTA (two CTAs per SM)
+constexpr int kTH = 64;    // tile rows (columns: kTile = 128)
+constexpr int kTileFloats = kTH * kTile;
+constexpr int kHaloCtasMax = 320;      // grid cap (>= 2 x SMs of one GB300); sizes the ring
 constexpr uint32_t kPollLimit = 1u << 23;  // x ~0.3 us per poll: seconds, not a hang
 constexpr int kGather = 8;             // 16-byte loads in flight per thread while staging
 
@@ -56,7 +62,7 @@ struct HaloShape {
 
 __host__ __device__ inline HaloShape halo_shape(const Shape& s) {
   HaloShape h;
-  h.rows = kTile + 2 * s.hc;
+  h.rows = kTH + 2 * s.hc;
   h.cols = kTile + s.KP;
   h.pitch = h.cols;  // a multiple of 4: rows start 16-byte aligned; even: the
                      // 8 lanes of a load phase (rows 4 apart) hit distinct bank groups
@@ -126,11 +132,11 @@ __device__ void gather_plane(const Shape& s, const HaloShape& hs, const SPlane& 
   const int nq = ((c0 + hs.cols - 1) >> 2) - q0 + 1;
   const int total = hs.rows * nq;
   const float* base = plane + (long long)(i0 + s.hc) * s.g.P;
-  for (int e0 = threadIdx.x; e0 < total; e0 += kThreads * kGather) {
+  for (int e0 = threadIdx.x; e0 < total; e0 += kHT * kGather) {
     float4 v[kGather];
 #pragma unroll
     for (int q = 0; q < kGather; ++q) {
-      const int e = e0 + q * kThreads;
+      const int e = e0 + q * kHT;
       if (e < total) {
         const int R = e / nq, m = e - R * nq;
         v[q] = __ldg(reinterpret_cast<const float4*>(base + (long long)R * s.g.P + ((q0 + m) << 2)));
@@ -138,7 +144,7 @@ __device__ void gather_plane(const Shape& s, const HaloShape& hs, const SPlane& 
     }
 #pragma unroll
     for (int q = 0; q < kGather; ++q) {
-      const int e = e0 + q * kThreads;
+      const int e = e0 + q * kHT;
       if (e < total) {
         const int R = e / nq, m = e - R * nq;
         put4(srow(sp, R), ((q0 + m) << 2) - c0, hs.cols, v[q]);
@@ -159,26 +165,26 @@ __device__ void gather_ring(const HaloShape& hs, const SPlane& sp, const float* 
   const int q0 = c0 >> 2;   // floor
   const int nq = ((c0 + hs.cols - 1) >> 2) - q0 + 1;
   const int total = hs.rows * nq;
-  const int ti = i0 >> 7, tj = j0 >> 7;
-  for (int e0 = threadIdx.x; e0 < total; e0 += kThreads * kGather) {
+  const int ti = i0 / kTH, tj = j0 >> 7;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kHT * kGather) {
     float4 v[kGather];
 #pragma unroll
     for (int q = 0; q < kGather; ++q) {
-      const int e = e0 + q * kThreads;
+      const int e = e0 + q * kHT;
       v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (e < total) {
         const int R = e / nq, m = e - R * nq;
         const int ii = i0 - hc + R, cc = (q0 + m) << 2;
-        const int tr = ii >> 7, tc = cc >> 7;  // floor: neighbour tile row / column
+        const int tr = ii >= 0 ? ii / kTH : -1, tc = cc >> 7;  // floor: neighbour tile row / column
         const float* src = nb[3 * (tr - ti + 1) + (tc - tj + 1)];
         if (src)
-          v[q] = __ldcg(reinterpret_cast<const float4*>(src + off + (ii - (tr << 7)) * kTile +
+          v[q] = __ldcg(reinterpret_cast<const float4*>(src + off + (ii - tr * kTH) * kTile +
                                                          (cc - (tc << 7))));
       }
     }
 #pragma unroll
     for (int q = 0; q < kGather; ++q) {
-      const int e = e0 + q * kThreads;
+      const int e = e0 + q * kHT;
       if (e < total) {
         const int R = e / nq, m = e - R * nq;
         put4(srow(sp, R), ((q0 + m) << 2) - c0, hs.cols, v[q]);
@@ -226,25 +232,25 @@ __device__ void prefetch_item(const Shape& s, const FusedArgs& a, const HaloShap
   long long id;
   const bool fwd = decode_item(sq, pl.NT, pl.L, &id);
   const int e = (int)(id / pl.T), k = (int)(id - (long long)e * pl.T);
-  const int i0 = (k / s.gx) * kTile, j0 = (k % s.gx) * kTile;
+  const int i0 = (k / s.gx) * kTH, j0 = (k % s.gx) * kTile;
   const Geom& g = s.g;
   const int t = a.t0 + e, ne = a.t1 - a.t0;
   if (fwd) {
     for (int phi = 0; phi < s.R2; ++phi)
       prefetch_rect(a.x + (long long)phi * g.plane, g.P, i0 + s.hc, hs.rows, j0 + s.hc, hs.cols,
                     lane);
-    prefetch_rect(a.u + (long long)t * g.plane, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
+    prefetch_rect(a.u + (long long)t * g.plane, g.P, g.B + i0, kTH, g.B + j0, kTile, lane);
     if (a.nu > 0.f)
-      prefetch_rect(a.y + (long long)t * g.plane, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
+      prefetch_rect(a.y + (long long)t * g.plane, g.P, g.B + i0, kTH, g.B + j0, kTile, lane);
   } else {
     for (int phi = 0; phi < s.R2; ++phi) {
       const long long pb = (long long)phi * g.plane;
-      if (e > 0) prefetch_rect(a.Den + pb, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
+      if (e > 0) prefetch_rect(a.Den + pb, g.P, g.B + i0, kTH, g.B + j0, kTile, lane);
       if (e > 0 && a.nu > 0.f)
-        prefetch_rect(a.Nw + pb, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
+        prefetch_rect(a.Nw + pb, g.P, g.B + i0, kTH, g.B + j0, kTile, lane);
       if (e + 1 == ne) {
-        prefetch_rect(a.x + pb, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
-        prefetch_rect(a.N + pb, g.P, g.B + i0, kTile, g.B + j0, kTile, lane);
+        prefetch_rect(a.x + pb, g.P, g.B + i0, kTH, g.B + j0, kTile, lane);
+        prefetch_rect(a.N + pb, g.P, g.B + i0, kTH, g.B + j0, kTile, lane);
       }
     }
   }
@@ -269,7 +275,7 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
   const SPlane sp{smem, hs.pitch, 2};
   float* ks = smem + hs.buf;
   const int tid = threadIdx.x;
-  const int my = tid & 31, mx = tid >> 5;  // this thread's 4 x 16 outputs: rows 4 my, cols 16 mx
+  const int my = tid & 15, mx = tid >> 4;  // this thread's 4 x 16 outputs: rows 4 my, cols 16 mx
   const int T = pl.T;
   const long long NT = pl.NT, L = pl.L, RS = pl.R;
   const int ne = a.t1 - a.t0;
@@ -279,7 +285,7 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
   const bool fwd = decode_item(sq, NT, L, &id);
   const int e = (int)(id / T), k = (int)(id - (long long)e * T);
   const int ti = k / s.gx, tj = k - ti * s.gx;
-  const int i0 = ti * kTile, j0 = tj * kTile;
+  const int i0 = ti * kTH, j0 = tj * kTile;
   const int t = a.t0 + e;
   bool ok = true;
   float acc[4][16];
@@ -300,7 +306,7 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
       const long long prev = id - RS;
       const int pe = (int)(prev / T), pk = (int)(prev - (long long)pe * T);
       const int nti = pk / s.gx + tid / 3 - 1, ntj = pk % s.gx + tid % 3 - 1;
-      if (nti >= 0 && nti < s.gy && ntj >= 0 && ntj < s.gx) {
+      if (nti >= 0 && nti < pl.T / s.gx && ntj >= 0 && ntj < s.gx) {
         probe = h.adone + nti * s.gx + ntj;
         need = pe + 1;
         seen = ld_relaxed(probe);
@@ -311,7 +317,7 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
       gather_plane(s, hs, sp, a.x + (long long)phi * g.plane, i0, j0);
       const float4* kg =
           reinterpret_cast<const float4*>(a.kf + ((long long)t * s.R2 + phi) * hs.ks);
-      for (int q = tid; q < kq; q += kThreads) reinterpret_cast<float4*>(ks)[q] = kg[q];
+      for (int q = tid; q < kq; q += kHT) reinterpret_cast<float4*>(ks)[q] = kg[q];
       if (phi == 0) {
         claim_next();
         if (probe) {
@@ -376,7 +382,7 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
     if (tid < 9) {
       const int nti = ti + tid / 3 - 1, ntj = tj + tid % 3 - 1;
       const float* src = nullptr;
-      if (nti >= 0 && nti < s.gy && ntj >= 0 && ntj < s.gx) {
+      if (nti >= 0 && nti < pl.T / s.gx && ntj >= 0 && ntj < s.gx) {
         const long long fid = (long long)e * T + nti * s.gx + ntj;
         const long long slot = fid % RS;
         ok = wait_geq(h.fflag + slot, (int)(fid + 1), h.ctrl);
@@ -403,7 +409,7 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
         }
         const float4* kg =
             reinterpret_cast<const float4*>(a.ka + ((long long)t * s.R2 + phi) * hs.ks);
-        for (int q = tid; q < kq; q += kThreads) reinterpret_cast<float4*>(ks)[q] = kg[q];
+        for (int q = tid; q < kq; q += kHT) reinterpret_cast<float4*>(ks)[q] = kg[q];
         __syncthreads();
         // each exposure's adjoint is summed from zero, then added to the running sum
         corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
@@ -459,7 +465,7 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
 
 // One launch per EM iteration of one context (exposures [a.t0, a.t1)).
 template <bool STUDENT>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kHT, 2)
     halo_kernel(const Shape s, const HaloLaunch h, const HaloPlan pl) {
   extern __shared__ __align__(128) float smem[];
   __shared__ long long item_s;
@@ -507,8 +513,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (last_s) {
     __threadfence();
-    for (long long i = tid; i < pl.R; i += kThreads) h.fflag[i] = 0;
-    for (int i = tid; i < pl.T; i += kThreads) h.adone[i] = 0;
+    for (long long i = tid; i < pl.R; i += kHT) h.fflag[i] = 0;
+    for (int i = tid; i < pl.T; i += kHT) h.adone[i] = 0;
     if (tid == 0) {
       h.ctrl[0] = 0ull;
       h.ctrl[1] = 0ull;
@@ -523,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // job has its own ring, flags and abort flag; the list's claim counter and
 // the finished-CTA count are the batch's. The last CTA resets the flags of
 // every job that ran.
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kHT, 2)
     halo_batch_kernel(const HaloBatchJob* __restrict__ jobs, int njobs,
                       const int2* __restrict__ items, const int* __restrict__ n_items,
                       unsigned long long* ctrl, int* err) {
@@ -575,8 +581,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const HaloBatchJob& J = jobs[j];
       if (J.remaining <= 0) continue;
       const HaloLaunch& h = J.h[0];  // ring, flags and counters are shared by h[0], h[1]
-      for (long long i = tid; i < J.pl.R; i += kThreads) h.fflag[i] = 0;
-      for (int i = tid; i < J.pl.T; i += kThreads) h.adone[i] = 0;
+      for (long long i = tid; i < J.pl.R; i += kHT) h.fflag[i] = 0;
+      for (int i = tid; i < J.pl.T; i += kHT) h.adone[i] = 0;
       if (tid == 0) h.ctrl[2] = 0ull;
     }
     if (tid == 0) {
@@ -593,23 +599,23 @@ __global__ void __launch_bounds__(kThreads, 1)
 // partial sum, so the total (a fixed-order sum of the partials) does not
 // depend on scheduling. For r = 1 the x window is staged once per item.
 template <bool STUDENT>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kHT, 2)
     halo_chi2_kernel(const Shape s, const FusedArgs a, const int groups,
                      double* __restrict__ part) {
   extern __shared__ __align__(128) float smem[];
-  __shared__ double red[kThreads / 32];
+  __shared__ double red[kHT / 32];
   const Geom& g = s.g;
   const HaloShape hs = halo_shape(s);
   const SPlane sp{smem, hs.pitch, 2};
   float* ks = smem + hs.buf;
   const int tid = threadIdx.x;
-  const int my = tid & 31, mx = tid >> 5;
+  const int my = tid & 15, mx = tid >> 4;
   const int kq = hs.ks >> 2;
-  const int nitems = s.gx * s.gy * groups;
+  const int nitems = s.gx * ((s.H + kTH - 1) / kTH) * groups;
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int k = item / groups, grp = item - k * groups;
     const int ti = k / s.gx, tj = k - ti * s.gx;
-    const int i0 = ti * kTile, j0 = tj * kTile;
+    const int i0 = ti * kTH, j0 = tj * kTile;
     const int t0 = (int)((long long)s.n * grp / groups);
     const int t1 = (int)((long long)s.n * (grp + 1) / groups);
     double chi = 0.0;
@@ -624,11 +630,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (s.R2 > 1 || t == t0) gather_plane(s, hs, sp, a.x + (long long)phi * g.plane, i0, j0);
         const float4* kg =
             reinterpret_cast<const float4*>(a.kf + ((long long)t * s.R2 + phi) * hs.ks);
-        for (int q = tid; q < kq; q += kThreads) reinterpret_cast<float4*>(ks)[q] = kg[q];
+        for (int q = tid; q < kq; q += kHT) reinterpret_cast<float4*>(ks)[q] = kg[q];
         if (tid < 32 && phi == 0 && t + 1 < t1) {  // the next exposure's u and y into L2
-          prefetch_rect(a.u + (long long)(t + 1) * g.plane, g.P, g.B + i0, kTile, g.B + j0,
+          prefetch_rect(a.u + (long long)(t + 1) * g.plane, g.P, g.B + i0, kTH, g.B + j0,
                         kTile, tid);
-          prefetch_rect(a.y + (long long)(t + 1) * g.plane, g.P, g.B + i0, kTile, g.B + j0,
+          prefetch_rect(a.y + (long long)(t + 1) * g.plane, g.P, g.B + i0, kTH, g.B + j0,
                         kTile, tid);
         }
         __syncthreads();
@@ -685,9 +691,9 @@ cudaError_t launch_flag_wait_selftest(uint32_t limit, void* scratch, int* err, c
 
 HaloPlan halo_plan(const Shape& s, int ne) {
   HaloPlan p;
-  p.T = s.gx * s.gy;
-  // neighbour ids differ by up to gx + 1 (a row of tiles plus one column)
-  p.dmax = (s.gy > 1 ? s.gx : 0) + (s.gx > 1 ? 1 : 0);
+  const int gyh = (s.H + kTH - 1) / kTH;
+  p.T = s.gx * gyh;
+  p.dmax = (gyh > 1 ? s.gx : 0) + (s.gx > 1 ? 1 : 0);
   p.NT = (long long)ne * p.T;
   p.L = p.dmax + 2LL * kHaloCtasMax;
   if (p.L > p.NT) p.L = p.NT;
@@ -728,13 +734,13 @@ cudaError_t launch_halo_t(const Shape& s, const HaloLaunch& h, const HaloPlan& p
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_kernel<STUDENT>, kThreads,
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_kernel<STUDENT>, kHT,
                                                          smem)) != cudaSuccess)
     return e;
   long long grid = (long long)sms * (occ > 0 ? occ : 1);
   if (grid > kHaloCtasMax) grid = kHaloCtasMax;
   if (grid > 2 * pl.NT) grid = 2 * pl.NT;
-  halo_kernel<STUDENT><<<(int)grid, kThreads, smem, st>>>(s, h, pl);
+  halo_kernel<STUDENT><<<(int)grid, kHT, smem, st>>>(s, h, pl);
   return cudaGetLastError();
 }
 
@@ -769,7 +775,7 @@ int halo_batch_ctas() {
   int dev = 0, sms = 0, occ = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_batch_kernel, kThreads, smem) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_batch_kernel, kHT, smem) !=
           cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -784,7 +790,7 @@ cudaError_t launch_halo_batch(const HaloBatchJob* jobs, int njobs, const int2* i
   cudaError_t e = cudaFuncSetAttribute(halo_batch_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  halo_batch_kernel<<<ctas, kThreads, smem, st>>>(jobs, njobs, items, n_items, ctrl, err);
+  halo_batch_kernel<<<ctas, kHT, smem, st>>>(jobs, njobs, items, n_items, ctrl, err);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   halo_batch_advance_kernel<<<(njobs + 127) / 128, 128, 0, st>>>(const_cast<HaloBatchJob*>(jobs),
                                                                  njobs);
@@ -793,7 +799,7 @@ cudaError_t launch_halo_batch(const HaloBatchJob* jobs, int njobs, const int2* i
 
 int launch_halo_chi2(const Shape& s, const FusedArgs& a, double* part, int max_parts,
                      cudaStream_t st, cudaError_t* err) {
-  const int T = s.gx * s.gy;
+  const int T = s.gx * ((s.H + kTH - 1) / kTH);
   int groups = max_parts / T;
   if (groups > s.n) groups = s.n;
   if (groups < 1) {
@@ -806,14 +812,14 @@ int launch_halo_chi2(const Shape& s, const FusedArgs& a, double* part, int max_p
   int dev = 0, sms = 0, occ = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kHT, smem);
   if (e != cudaSuccess) {
     *err = e;
     return 0;
   }
   long long grid = (long long)sms * (occ > 0 ? occ : 1);
   if (grid > (long long)T * groups) grid = (long long)T * groups;
-  kern<<<(int)grid, kThreads, smem, st>>>(s, a, groups, part);
+  kern<<<(int)grid, kHT, smem, st>>>(s, a, groups, part);
   *err = cudaGetLastError();
   return T * groups;
 }

@@ -25,7 +25,7 @@ size_t halo_buffer_bytes(const Shape& s, bool student);
 struct HaloLaunch {
   FusedArgs a;                 // x, xn, u, kf, ka, N, Den, err, t0, t1; heavy-tailed
                                // (a.nu > 0): also y, and a.Nw holds the running N'
-  float* ring;                 // R slots of kTile * kTile floats (two tiles if heavy-tailed)
+  float* ring;                 // R slots of 64 x 128 floats (two tiles if heavy-tailed)
   int* fflag;                  // R: forward item id + 1 last published in each slot
   int* adone;                  // T: adjoint items finished per tile in this launch
   unsigned long long* ctrl;    // [0] claim counter, [1] CTAs finished, [2] abort flag

@@ -88,15 +88,16 @@ def test_fit_psf_rejects_bad_arguments_before_touching_the_gpu(lib):
 def test_ctx_bytes_precision_host_only(lib):
     from paper_2302_05804_gb300 import emd
     base = emd.emd_ctx_bytes(4096, 4096, 33, 43, 1)
-    # FP32: the halo-exchange kernel's ring of 128^2 tiles: R = L + dmax + 1 + 160
-    # slots, L = dmax + 320 (adjoint lag), dmax = 32 + 1 tile ids, plus the flags
-    ring = 547 * 128 * 128 * 4 + 2304 + 4096 + 256
+    # FP32: the halo-exchange kernel's ring of 64 x 128 tiles: R = L + dmax + 1 + 320
+    # slots, L = dmax + 640 (adjoint lag), dmax = 32 + 1 tile ids, plus the flags
+    # (1027 slots, 2048 tile counters)
+    ring = 1027 * 64 * 128 * 4 + 4352 + 8192 + 256
     assert emd.emd_ctx_bytes_precision(4096, 4096, 33, 43, 1, emd.EMD_PREC_FP32) == base + ring
     assert emd.emd_ctx_bytes_precision(4096, 4096, 33, 43, 1, emd.EMD_PREC_FP32_PAIR) == base
-    # small problems: the ring holds all n * T tiles (4 exposures x 4 tiles)
+    # small problems: the ring holds all n * T tiles (4 exposures x 8 tiles)
     small = emd.emd_ctx_bytes(256, 256, 4, 15, 1)
     assert (emd.emd_ctx_bytes_precision(256, 256, 4, 15, 1, emd.EMD_PREC_FP32)
-            == small + 16 * 128 * 128 * 4 + 256 + 256 + 256)
+            == small + 32 * 64 * 128 * 4 + 256 + 256 + 256)
     fft = emd.emd_ctx_bytes_precision(4096, 4096, 33, 43, 1, emd.EMD_PREC_FFT_FP32)
     assert base + 33 * 4096 * 4096 * 4 < fft < base + 33 * 4300 * 4300 * 4 + 10e6
     assert emd.emd_ctx_bytes_precision(4096, 4096, 33, 43, 1, emd.EMD_PREC_SPLIT_BF16) > base

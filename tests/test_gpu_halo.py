@@ -44,9 +44,9 @@ def start(p, seed=0):
     return (g.uniform(0.5, 1.5, (p.r * p.H, p.r * p.W)) * 10.0).astype(np.float32)
 
 
-# (H, W, n, K, r): one tile; ragged 3 x 3 tiles; one row of tiles; one column;
-# K = 1; r = 2 with a ragged grid; 8 x 8 tiles x 12 exposures (NT = 768 >
-# ring slots 499: slots reused within the launch)
+# (H, W, n, K, r) with 64 x 128 tiles: two tiles; ragged 5 x 3 tiles; two
+# rows of tiles; one column; K = 1; r = 2 with a ragged grid; 16 x 8 tiles x 12
+# exposures (1536 forward items > 979 ring slots: slots reused in the launch)
 CASES = [(96, 80, 3, 15, 1), (300, 257, 5, 43, 1), (100, 1500, 3, 21, 1),
          (1400, 90, 3, 21, 1), (260, 300, 4, 1, 1), (200, 330, 4, 9, 2),
          (1024, 1024, 12, 43, 1)]
@@ -64,9 +64,10 @@ def test_bit_identical_to_cta_pair_kernel(emd, H, W, n, K, r):
 
 
 def test_oracle_parity_with_ring_reuse(emd):
-    """A ragged 6 x 6 tile grid with 40 exposures: 1440 forward items through
-    a ring of 495 slots, so slots are rewritten within every launch; one and
-    five iterations against the oracle at the FP32 path's tolerances."""
+    """A ragged 11 x 6 grid of 64 x 128 tiles with 40 exposures: 2640 forward
+    items through a ring of 975 slots, so slots are rewritten within every
+    launch; one and five iterations against the oracle at the FP32 path's
+    tolerances."""
     p = synth.make_problem("hsc", H=700, W=650, n=40, K=15, r=1, mask_frac=0.05,
                            fwhm=(2.0, 4.0), n_points=80, n_gal=5, seed_offset=3)
     x0 = start(p, seed=1)
