@@ -8,7 +8,9 @@ asserts that every dependency of an item comes earlier in the claim sequence
 (so no wait can deadlock with any number of CTAs), that the simulation never
 stalls, that every adjoint item reads the w tiles of its own exposure and
 neighbours, that no forward item overwrites a slot while a reader still
-needs it, and that adjoint items of one tile run in exposure order."""
+needs it, and that adjoint items of one tile run in exposure order. The
+batch kernel's work list (several jobs' sequences merged round-robin or job
+after job) is checked the same way."""
 import random
 
 import pytest
@@ -149,3 +151,82 @@ def simulate(gx, gy, ne, cap, ctas, seed, ahead=True):
 def test_simulated_execution(gx, gy, ne, cap, ctas, ahead):
     for seed in range(3):
         simulate(gx, gy, ne, cap, ctas, seed, ahead)
+
+
+def merged(jobs, order):
+    """The batch step's work list: each job's claim positions in its own
+    order, merged round-robin (order 0) or job after job (order 1)."""
+    seqs = [[(j, sq) for sq in range(2 * plan(*jb)[2])] for j, jb in enumerate(jobs)]
+    if order == 1:
+        return [e for s in seqs for e in s]
+    out, q = [], 0
+    while len(out) < sum(len(s) for s in seqs):
+        out += [s[q] for s in seqs if q < len(s)]
+        q += 1
+    return out
+
+
+JOB_MIXES = [[(2, 2, 3, 2), (1, 1, 4, 2), (5, 3, 2, 1)],
+             [(8, 8, 2, 3), (3, 1, 5, 2)],
+             [(1, 3, 1, 1), (4, 4, 3, 2), (2, 1, 6, 1), (3, 3, 2, 3)]]
+
+
+@pytest.mark.parametrize("jobs", JOB_MIXES)
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("ctas", [1, 3, 17])
+def test_merged_batch_work_list(jobs, order, ctas):
+    """Every dependency of an entry (same job) comes earlier in the merged
+    list, and a simulated run with claim-ahead finishes, each adjoint item
+    reading the ring slots its job's forward items filled."""
+    lst = merged(jobs, order)
+    pos = {}
+    for p_, (j, sq) in enumerate(lst):
+        NT, L = plan(*jobs[j])[2], plan(*jobs[j])[3]
+        fwd, i = decode(sq, NT, L)
+        pos[(j, "F" if fwd else "A", i)] = p_
+    for (j, kind, i), p_ in pos.items():
+        gx, gy = jobs[j][0], jobs[j][1]
+        T, _, _, _, R = plan(*jobs[j])
+        for d in deps(kind == "F", i, gx, gy, T, R):
+            assert pos[(j,) + d] < p_
+    rng = random.Random(len(lst) + ctas)
+    done, ring = set(), {}
+    workers, pending, nxt = [None] * ctas, [None] * ctas, 0
+    steps = 0
+    while len(done) < len(lst):
+        progressed = False
+        for w in range(ctas):
+            if workers[w] is None:
+                p_ = pending[w]
+                if p_ is None:
+                    p_, nxt = nxt, nxt + 1
+                pending[w] = None
+                if p_ < len(lst):
+                    j, sq = lst[p_]
+                    NT, L = plan(*jobs[j])[2], plan(*jobs[j])[3]
+                    fwd, i = decode(sq, NT, L)
+                    workers[w] = [j, "F" if fwd else "A", i, "wait", rng.randint(1, 4)]
+                    pending[w], nxt = nxt, nxt + 1
+                    progressed = True
+                continue
+            j, kind, i, state, rem = workers[w]
+            gx, gy = jobs[j][0], jobs[j][1]
+            T, _, _, _, R = plan(*jobs[j])
+            if state == "wait":
+                if all((j,) + d in done for d in deps(kind == "F", i, gx, gy, T, R)):
+                    workers[w][3] = "run"
+                    progressed = True
+                    if kind == "A":
+                        e, k = divmod(i, T)
+                        for k2 in neighbours(k, gx, gy):
+                            assert ring[(j, (e * T + k2) % R)] == e * T + k2
+                continue
+            workers[w][4] -= 1
+            progressed = True
+            if workers[w][4] == 0:
+                if kind == "F":
+                    ring[(j, i % R)] = i
+                done.add((j, kind, i))
+                workers[w] = None
+        steps += 1
+        assert progressed, "merged schedule stalled"
