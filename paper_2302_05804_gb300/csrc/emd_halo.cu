@@ -53,7 +53,7 @@ constexpr int kGather = 8;             // 16-byte loads in flight per thread whi
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct HaloShape {
-  int rows;   // staged rows: kTile + 2 hc
+  int rows;   // staged rows: kTH + 2 hc
   int cols;   // staged columns: kTile + KP
   int pitch;  // floats per staged row; rows also carry a skew of 4 floats every 4 rows
   int buf;    // floats of the staged window
@@ -106,8 +106,8 @@ __device__ bool wait_geq(const int* p, int v, unsigned long long* ctrl,
   return false;
 }
 
-// Writes the four floats of v (image/plane columns col0 .. col0+3) into the
-// staged row, skipping columns outside [0, cols).
+// Writes the four floats of v into the staged row at columns C .. C+3,
+// skipping columns outside [0, cols).
 __device__ __forceinline__ void put4(float* row, int C, int cols, const float4 v) {
   if (C >= 0 && C + 3 < cols) {
     row[C] = v.x;
@@ -122,7 +122,7 @@ __device__ __forceinline__ void put4(float* row, int C, int cols, const float4 v
   }
 }
 
-// Forward item: the x window of rows [i0 - hc, i0 + 128 + hc) and columns
+// Forward item: the x window of rows [i0 - hc, i0 + kTH + hc) and columns
 // [j0 - hc, j0 - hc + cols) of one padded latent plane (read-only during
 // the launch), through 16-byte loads on the plane's 16-byte grid.
 __device__ void gather_plane(const Shape& s, const HaloShape& hs, const SPlane& sp,
@@ -153,12 +153,12 @@ __device__ void gather_plane(const Shape& s, const HaloShape& hs, const SPlane& 
   }
 }
 
-// Adjoint item: the w window of rows [i0 - hc, i0 + 128 + hc) and columns
+// Adjoint item: the w window of rows [i0 - hc, i0 + kTH + hc) and columns
 // [j0 - hc, j0 - hc + cols) from the ring slots of the tile and its
 // neighbours (nb[3 * (dy + 1) + (dx + 1)], null outside the tile grid: w = 0
-// there). Tile origins are multiples of 128, so the 16-byte image-column
-// grid is each slot's own. Loads bypass L1 (the slots are rewritten by
-// other SMs during the launch).
+// there), `off` floats into each slot. Tile column origins are multiples of
+// 128, so the 16-byte image-column grid is each slot's own. Loads bypass L1
+// (the slots are rewritten by other SMs during the launch).
 __device__ void gather_ring(const HaloShape& hs, const SPlane& sp, const float* const* nb,
                             int off, int hc, int i0, int j0) {
   const int c0 = j0 - hc;   // image column of window column 0
