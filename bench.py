@@ -455,11 +455,13 @@ def run_ours(args):
     elif prec in (0, 6):
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
         kern = "halo" if prec == 0 else "fused"
-        traffic = committed_traffic(kern, args.workload)
+        # the committed DRAM records are of the Gaussian instances
+        traffic = committed_traffic(kern, args.workload) if args.nu == 0 else None
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": traffic,
                     "kernel": {"halo": "halo_kernel (FP32 FMA, persistent, w ring in L2)",
-                               "fused": "fused_kernel (FP32 FMA, CTA pairs)"}[kern],
+                               "fused": "fused_kernel (FP32 FMA, CTA pairs)"}[kern] +
+                              (" heavy-tailed instance" if args.nu > 0 else ""),
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
         if traffic:
             hbm_peak, hsrc = 6800.0, "fallback 6.8 TB/s"
