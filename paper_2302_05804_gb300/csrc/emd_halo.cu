@@ -294,14 +294,20 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
 #pragma unroll
     for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
 
+  // Both kinds of item run one loop of steps, each staging a window and a
+  // kernel and correlating them at ONE call site: the two CTAs of an SM may
+  // be in different kinds of item, and one copy of the unrolled loop keeps
+  // both in the instruction cache. Forward: R2 steps (the phases of x,
+  // accumulated into z); adjoint: passes x R2 steps, each summed from zero
+  // and then added into its running sum (pass 0: Den from w; heavy-tailed
+  // pass 1: N' from w2 = u' y).
+  const long long slot = fwd ? id % RS : 0;
+  // Forward: the slot's previous tile (forward id - R) must have been read by
+  // its adjoint readers before this item's w is stored: probe their counters
+  // now (relaxed), settle after staging (a fence, or a bounded wait).
+  const int* probe = nullptr;
+  int need = 0, seen = 0;
   if (fwd) {
-    // ---------------- forward item: w_t = u_t . F_t x on the tile ----------------
-    const long long slot = id % RS;
-    // The slot's previous tile (forward id - R) must have been read by its
-    // adjoint readers before this item's w is stored: probe their counters
-    // now (relaxed), settle after staging (a fence, or a bounded wait).
-    const int* probe = nullptr;
-    int need = 0, seen = 0;
     if (id >= RS && tid < 9) {
       const long long prev = id - RS;
       const int pe = (int)(prev / T), pk = (int)(prev - (long long)pe * T);
@@ -312,24 +318,98 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
         seen = ld_relaxed(probe);
       }
     }
-    for (int phi = 0; phi < s.R2; ++phi) {
-      if (phi > 0) __syncthreads();  // readers of the previous phase's window are done
+  } else {
+    // adjoint: the forward items of the 3 x 3 neighbours, and adjoint (e - 1, k)
+    if (tid < 9) {
+      const int nti = ti + tid / 3 - 1, ntj = tj + tid % 3 - 1;
+      const float* src = nullptr;
+      if (nti >= 0 && nti < pl.T / s.gx && ntj >= 0 && ntj < s.gx) {
+        const long long fid = (long long)e * T + nti * s.gx + ntj;
+        const long long fslot = fid % RS;
+        ok = wait_geq(h.fflag + fslot, (int)(fid + 1), h.ctrl);
+        src = h.ring + fslot * kSlot;
+      }
+      nb_s[tid] = src;
+    } else if (tid == 9 && e > 0) {
+      ok = wait_geq(h.adone + k, e, h.ctrl);  // adjoint (e - 1, k) has written Den
+    }
+    __syncthreads();
+  }
+  const int nsteps = fwd ? s.R2 : (STUDENT ? 2 : 1) * s.R2;
+  for (int step = 0; step < nsteps; ++step) {
+    const int pass = step / s.R2, phi = step - pass * s.R2;
+    if (step > 0) __syncthreads();  // readers of the previous step's window and kernel are done
+    if (fwd) {
       gather_plane(s, hs, sp, a.x + (long long)phi * g.plane, i0, j0);
-      const float4* kg =
-          reinterpret_cast<const float4*>(a.kf + ((long long)t * s.R2 + phi) * hs.ks);
-      for (int q = tid; q < kq; q += kHT) reinterpret_cast<float4*>(ks)[q] = kg[q];
-      if (phi == 0) {
-        claim_next();
-        if (probe) {
-          if (seen >= need)
-            __threadfence();  // acquire: the readers' loads precede our stores
-          else
-            ok = wait_geq(probe, need, h.ctrl);
+    } else {
+      if (phi == 0) gather_ring(hs, sp, nb_s, pass * kTileFloats, s.hc, i0, j0);
+      if (step > 0) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
+      }
+    }
+    const float4* kg = reinterpret_cast<const float4*>((fwd ? a.kf : a.ka) +
+                                                       ((long long)t * s.R2 + phi) * hs.ks);
+    for (int q = tid; q < kq; q += kHT) reinterpret_cast<float4*>(ks)[q] = kg[q];
+    if (step == 0) {
+      claim_next();
+      if (probe) {
+        if (seen >= need)
+          __threadfence();  // acquire: the readers' loads precede our stores
+        else
+          ok = wait_geq(probe, need, h.ctrl);
+      }
+    }
+    __syncthreads();  // also orders the slot check above before the stores below
+    corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
+    if (fwd) continue;
+    // ---------------- adjoint epilogue: running sum, or the update ----------------
+    float* run = pass == 0 ? a.Den : a.Nw;  // running sum over the exposures
+    const long long pbase = (long long)phi * g.plane;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int i = i0 + 4 * my + p;
+      const long long grow = pbase + (long long)(g.B + i) * g.P + g.B + j0 + 16 * mx;
+      float2* run2 = reinterpret_cast<float2*>(run + grow);
+      if (e > 0) {
+#pragma unroll
+        for (int c2 = 0; c2 < 8; ++c2) {
+          const float2 dv = __ldcg(run2 + c2);
+          acc[p][2 * c2] = dv.x + acc[p][2 * c2];
+          acc[p][2 * c2 + 1] = dv.y + acc[p][2 * c2 + 1];
         }
       }
-      __syncthreads();  // also orders the slot check above before the stores below
-      corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
+      // not the last exposure; or the heavy-tailed Den, kept for pass 1
+      // (read back below by the thread that wrote it)
+      if (e + 1 < ne || (STUDENT && pass == 0)) {
+#pragma unroll
+        for (int c2 = 0; c2 < 8; ++c2)
+          run2[c2] = make_float2(acc[p][2 * c2], acc[p][2 * c2 + 1]);
+        continue;
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int j = j0 + 16 * mx + c;
+        if (i < g.H && j < g.W) {
+          const float d = STUDENT ? __ldcg(a.Den + grow + c) : acc[p][c];
+          const float xo = a.x[grow + c];
+          float xv = xo;
+          if (d > 0.f) {
+            const float nv = fmaxf(STUDENT ? acc[p][c] : a.N[grow + c], 0.f);
+            if (d < 1e-30f)  // denominator near zero: guarded ratio in FP64
+              xv = (float)((double)xo * (double)nv / (double)d);
+            else
+              xv = xo * nv / d;
+          }
+          a.xn[grow + c] = xv;
+        }
+      }
     }
+  }
+  if (fwd) {
+    // ---------------- forward epilogue: w_t = u_t . z into the ring slot ----------------
     float* wt = h.ring + slot * kSlot;
     const float* up = a.u + (long long)t * g.plane;
 #pragma unroll
@@ -378,83 +458,6 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
       st_release(h.fflag + slot, (int)(id + 1));
     }
   } else {
-    // ---------------- adjoint item: Den (+)= F_t^T w_t on the tile ----------------
-    if (tid < 9) {
-      const int nti = ti + tid / 3 - 1, ntj = tj + tid % 3 - 1;
-      const float* src = nullptr;
-      if (nti >= 0 && nti < pl.T / s.gx && ntj >= 0 && ntj < s.gx) {
-        const long long fid = (long long)e * T + nti * s.gx + ntj;
-        const long long slot = fid % RS;
-        ok = wait_geq(h.fflag + slot, (int)(fid + 1), h.ctrl);
-        src = h.ring + slot * kSlot;
-      }
-      nb_s[tid] = src;
-    } else if (tid == 9 && e > 0) {
-      ok = wait_geq(h.adone + k, e, h.ctrl);  // adjoint (e - 1, k) has written Den
-    }
-    __syncthreads();
-    // pass 0: Den from w (= u z, or u' z); heavy-tailed pass 1: N' from w2 = u' y
-    for (int pass = 0; pass < (STUDENT ? 2 : 1); ++pass) {
-      if (pass > 0) __syncthreads();  // readers of pass 0's window are done
-      gather_ring(hs, sp, nb_s, pass * kTileFloats, s.hc, i0, j0);
-      if (pass == 0) claim_next();
-      float* run = pass == 0 ? a.Den : a.Nw;  // running sum over the exposures
-      for (int phi = 0; phi < s.R2; ++phi) {
-        if (phi > 0 || pass > 0) {
-          if (phi > 0) __syncthreads();  // readers of the previous phase's kernel are done
-#pragma unroll
-          for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
-        }
-        const float4* kg =
-            reinterpret_cast<const float4*>(a.ka + ((long long)t * s.R2 + phi) * hs.ks);
-        for (int q = tid; q < kq; q += kHT) reinterpret_cast<float4*>(ks)[q] = kg[q];
-        __syncthreads();
-        // each exposure's adjoint is summed from zero, then added to the running sum
-        corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
-        const long long pbase = (long long)phi * g.plane;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const int i = i0 + 4 * my + p;
-          const long long grow = pbase + (long long)(g.B + i) * g.P + g.B + j0 + 16 * mx;
-          float2* run2 = reinterpret_cast<float2*>(run + grow);
-          if (e > 0) {
-#pragma unroll
-            for (int c2 = 0; c2 < 8; ++c2) {
-              const float2 dv = __ldcg(run2 + c2);
-              acc[p][2 * c2] = dv.x + acc[p][2 * c2];
-              acc[p][2 * c2 + 1] = dv.y + acc[p][2 * c2 + 1];
-            }
-          }
-          // not the last exposure; or the heavy-tailed Den, kept for pass 1
-          // (read back below by the thread that wrote it)
-          if (e + 1 < ne || (STUDENT && pass == 0)) {
-#pragma unroll
-            for (int c2 = 0; c2 < 8; ++c2)
-              run2[c2] = make_float2(acc[p][2 * c2], acc[p][2 * c2 + 1]);
-            continue;
-          }
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int j = j0 + 16 * mx + c;
-            if (i < g.H && j < g.W) {
-              const float d = STUDENT ? __ldcg(a.Den + grow + c) : acc[p][c];
-              const float xo = a.x[grow + c];
-              float xv = xo;
-              if (d > 0.f) {
-                const float nv = fmaxf(STUDENT ? acc[p][c] : a.N[grow + c], 0.f);
-                if (d < 1e-30f)  // denominator near zero: guarded ratio in FP64
-                  xv = (float)((double)xo * (double)nv / (double)d);
-                else
-                  xv = xo * nv / d;
-              }
-              a.xn[grow + c] = xv;
-            }
-          }
-        }
-      }
-    }
     if (__syncthreads_or(!ok)) timed_out = true;  // all reads of the ring and Den are done
     if (tid == 0) {
       __threadfence();
