@@ -1213,6 +1213,7 @@ emd_batch* emd_batch_create(int max_jobs) {
   if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
     set_err("emd_batch_create: stream creation failed");
     cudaFree(b->arena);
+    cudaFree(b->harena);
     delete b;
     return nullptr;
   }
