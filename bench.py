@@ -35,9 +35,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "EM Gpix·exposure-iters/s"
 UNIT = "Gpix·exposure-iters/s"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (Blackwell)
 # kernels one emd_iterate(ctx, 1) call launches: the fused kernel (FP32); the
 # x split + tensor-core kernel (BF16 modes); the x maximum, the power-of-two
 # scales, the split and the tensor-core kernel (FP16 modes)
@@ -58,6 +56,26 @@ KERNEL_SOURCES = {
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     return int(os.environ.get("RANK", "0")), ws, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def fp32_peak(device_index):
+    """Derived FP32 FMA peak of the device in TFLOP/s: SMs (queried) x 128
+    lanes x 2 flop x the maximum SM clock (nvidia-smi clocks.max.sm; the
+    GB300's 2070 MHz when nvidia-smi cannot be asked). Returns (peak,
+    description, sms, max_mhz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(device_index).multi_processor_count
+    mhz, src = 2070.0, "2070 MHz (nvidia-smi unavailable)"
+    try:
+        out = subprocess.run(["nvidia-smi", f"--id={device_index}", "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=30).stdout.strip()
+        mhz, src = float(out.splitlines()[0]), "nvidia-smi clocks.max.sm"
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        pass
+    peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    return peak, (f"derived: {sms} SMs (queried) x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                  f"{mhz:.0f} MHz ({src})"), sms, mhz
 
 
 def workload_shape(name):
@@ -240,17 +258,18 @@ def run_reference(args):
     return 0
 
 
-def run_serving(p, args, precision=0):
-    """Continuous-batching sample: jobs with sides log-uniform in [128, 2048],
-    4-40 exposures, odd PSF sides 15-43, 50 iterations each, cut from the
-    resident frame set; an 80 GB budget. First all jobs at t=0 (saturated
-    jobs/s), then Poisson streams at 0.5x, 0.7x and 0.9x that rate for
-    p50/p99 latency (the top-level figures are the 0.7x stream's)."""
+def run_serving(p, args, precision=0, jobs=2000):
+    """Continuous-batching run: `jobs` jobs with sides log-uniform in
+    [128, 2048], 4-40 exposures, odd PSF sides 15-43, 50 iterations each, cut
+    from the resident frame set; an 80 GB budget. First all jobs at t=0
+    (saturated jobs/s, seed 4004), then Poisson streams of `jobs` jobs (seed
+    4005) at 0.5x, 0.7x and 0.9x that rate for p50/p99 latency (the
+    top-level figures are the 0.7x stream's)."""
     from paper_2302_05804_gb300 import serve
     pool = serve.DataPool(p)
     kw = dict(s_range=(128, min(2048, p.H)), n_range=(4, 40), k_range=(15, min(43, p.K)),
               iters=50)
-    sat_trace = serve.poisson_trace(args.serve_jobs, rate=1e9, seed=4004, **kw)
+    sat_trace = serve.poisson_trace(jobs, rate=1e9, seed=4004, **kw)
     srv = serve.Server(hbm_budget=80e9, max_slots=64, precision=precision)
     try:
         res = srv.run(sat_trace, pool.make, realtime=False)
@@ -260,7 +279,7 @@ def run_serving(p, args, precision=0):
     per_rate = {}
     for frac in (0.5, 0.7, 0.9):
         rate_f = frac * sat["jobs_per_s"]
-        trace_f = serve.poisson_trace(args.serve_jobs, rate=rate_f, seed=4005, **kw)
+        trace_f = serve.poisson_trace(jobs, rate=rate_f, seed=4005, **kw)
         srv = serve.Server(hbm_budget=80e9, max_slots=64, precision=precision)
         try:
             res_f = srv.run(trace_f, pool.make, realtime=True)
@@ -271,8 +290,11 @@ def run_serving(p, args, precision=0):
     fma = sum(2.0 * s.n * s.H * s.W * s.K ** 2 * s.iters for s in trace)
     return {"form": "fft" if precision == 5 else "direct fp32",
             "jobs": len(res), "saturated_jobs_per_s": sat["jobs_per_s"],
-            "by_load": {f"{frac}x": {"arrival_rate_jobs_per_s": v[0], "p50_latency_s": v[3]["p50_s"],
-                                     "p99_latency_s": v[3]["p99_s"], "jobs_per_s": v[3]["jobs_per_s"]}
+            "saturated_jobs": sat["jobs"],
+            "by_load": {f"{frac}x": {"jobs": v[3]["jobs"], "arrival_rate_jobs_per_s": v[0],
+                                     "p50_latency_s": v[3]["p50_s"],
+                                     "p99_latency_s": v[3]["p99_s"], "jobs_per_s": v[3]["jobs_per_s"],
+                                     "span_s": v[3]["span_s"]}
                         for frac, v in per_rate.items()},
             "arrival_rate_jobs_per_s": rate, "jobs_per_s": live["jobs_per_s"],
             "p50_latency_s": live["p50_s"], "p99_latency_s": live["p99_s"],
@@ -348,7 +370,7 @@ def run_psf_fit(p, iters):
     hg = (Kg - 1) // 2
     taps1d = sum(sum(1 for a in range(Kg) if 0 <= P + hg - a < Kh) for P in range(Kh))
     flops = 2.0 * 2.0 * taps1d ** 2 * n * iters
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = fp32_peak(torch.cuda.current_device())[0]
     tf = flops / (ms / 1e3) / 1e12
     return {"workload": f"{n} coarse {K}x{K} PSFs -> {Kh}x{Kh} (r = {r}), Kg = {Kg}, "
                         f"{iters} projected Adam iterations",
@@ -432,11 +454,12 @@ def run_ours(args):
     flops = algorithmic_flops(p.H, p.W, p.n, p.K, p.r) * (1.5 if args.nu > 0 else 1)
     launch_s = statistics.mean(per) / 1e3
     achieved = flops / launch_s / 1e12
+    peak32, peak32_src, _, sm_max_mhz = fp32_peak(local)
     if prec == 5:
         # FFT form: flops of the transforms it runs (a real 128^2 transform
         # = 2.5 N log2 N, N = 128^2) and of the spectrum products, against
         # the FP32 peak; the direct-form flops it replaces are reported beside
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        peak = peak32
         hc = ((p.K - 1) // 2 + p.r - 1) // p.r
         B = 128 - 2 * hc
         tiles = -(-p.H // B) * -(-p.W // B)
@@ -449,11 +472,11 @@ def run_ours(args):
         roofline = {"bound": "alu", "achieved": ex, "peak": peak, "unit": "TFLOP/s",
                     "frac": ex / peak, "traffic": None,
                     "kernel": "fft_forward_kernel + fft_adjoint_kernel (FP32 FFT)",
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                    "peak_source": peak32_src,
                     "direct_equivalent_tflops": achieved,
                     "fft_tflop_per_iteration": fl / 1e12}
     elif prec in (0, 6):
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        peak = peak32
         kern = "halo" if prec == 0 else "fused"
         # the committed DRAM records are of the Gaussian instances
         traffic = committed_traffic(kern, args.workload) if args.nu == 0 else None
@@ -462,7 +485,7 @@ def run_ours(args):
                     "kernel": {"halo": "halo_kernel (FP32 FMA, persistent, w ring in L2)",
                                "fused": "fused_kernel (FP32 FMA, CTA pairs)"}[kern] +
                               (" heavy-tailed instance" if args.nu > 0 else ""),
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+                    "peak_source": peak32_src}
         if traffic:
             hbm_peak, hsrc = 6800.0, "fallback 6.8 TB/s"
             try:
@@ -474,7 +497,7 @@ def run_ours(args):
             roofline["hbm_frac"] = roofline["hbm_gbs"] / hbm_peak
             roofline["hbm_peak_source"] = hsrc
         if clocks.get("sm_mhz"):
-            roofline["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ)
+            roofline["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / sm_max_mhz)
         fma = emd.emd_measure_fma_rate()
         roofline["fma_chain_measured_tflops"] = fma
         roofline["frac_of_measured_fma"] = achieved / fma
@@ -524,8 +547,9 @@ def run_ours(args):
 
     serving = serving_direct = None
     if args.serve_jobs > 0 and prec == 0:
-        serving = run_serving(p, args, precision=5)
-        serving_direct = run_serving(p, args, precision=0)
+        serving = run_serving(p, args, precision=5, jobs=args.serve_jobs)
+    if args.serve_jobs_direct > 0 and prec == 0:
+        serving_direct = run_serving(p, args, precision=0, jobs=args.serve_jobs_direct)
     psf_fit = None
     if args.psf_iters > 0 and prec == 0:
         psf_fit = run_psf_fit(p, args.psf_iters)
@@ -576,8 +600,11 @@ def main():
     ap.add_argument("--e2e-iters", type=int, default=10)
     ap.add_argument("--e2e-jobs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-jobs", type=int, default=40,
-                    help="jobs in the serving sample (0 disables it)")
+    ap.add_argument("--serve-jobs", type=int, default=2000,
+                    help="jobs of each serving run in the FFT form (0 disables it)")
+    ap.add_argument("--serve-jobs-direct", type=int, default=200,
+                    help="jobs of each serving run in the direct FP32 form (0 disables it; "
+                         "2000 would take about 20 minutes at its 10 jobs/s)")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip timing the FFT, tensor-core and heavy-tailed forms")
     ap.add_argument("--nu", type=float, default=0.0,

@@ -144,10 +144,12 @@ int emd_get_x(emd_ctx *ctx, float *out);
 /*
  * emd_loglik -- log-likelihood of the current iterate under Eq. (1)/(3):
  *   l = -1/2 sum_{t,i valid} [ u (y - z)^2 + log(2 pi v) ],  z = D^r(f_t * x),
- * accumulated in FP64. chi2 (the data term sum u (y-z)^2) is returned in
- * *chi2 when chi2 is not NULL. Synchronises the stream.
+ * accumulated in FP64, into *out. Synchronises the stream.
+ * emd_loglik_chi2 does the same and also returns the data term
+ * sum u (y-z)^2 in *chi2 (when chi2 is not NULL).
  */
-int emd_loglik(emd_ctx *ctx, double *out, double *chi2);
+int emd_loglik(emd_ctx *ctx, double *out);
+int emd_loglik_chi2(emd_ctx *ctx, double *out, double *chi2);
 
 /* Select the convolution arithmetic (enum emd_precision). Modes not built
  * into this library return EMD_EUNSUPPORTED and leave the mode unchanged.
@@ -295,7 +297,10 @@ int emd_batch_config(emd_batch *b, int *clusters, int *order, int *max_clusters,
  * fixed-size array inside the library's device image (room for
  * EMD_NOALLOC_MAX_EXPOSURES exposures; every GPU that loads the library
  * holds it until the process exits). n > EMD_NOALLOC_MAX_EXPOSURES is
- * rejected with EMD_EINVAL, as are NULL or host pointers and sizes < 1.
+ * rejected with EMD_EINVAL, as are NULL or host pointers, device memory of a
+ * GPU other than the current one, and sizes < 1. The C side cannot check
+ * buffer sizes: y and v must hold n*H*W floats, mask n*H*W bytes and out
+ * 4*n doubles.
  * The first call on a device looks up the scratch array's device address;
  * make that first call before any stream capture. All calls share the one
  * scratch array, so calls that overlap on the GPU (concurrent streams or

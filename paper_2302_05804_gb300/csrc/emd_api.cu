@@ -846,7 +846,9 @@ int emd_get_weights(emd_ctx* c, float* out) {
   return EMD_OK;
 }
 
-int emd_loglik(emd_ctx* c, double* out, double* chi2) {
+int emd_loglik(emd_ctx* c, double* out) { return emd_loglik_chi2(c, out, nullptr); }
+
+int emd_loglik_chi2(emd_ctx* c, double* out, double* chi2) {
   if (int rc = check_ctx(c, true)) return rc;
   if (!out) {
     set_err("null output pointer");

@@ -101,13 +101,17 @@ int na_fail(int code, const char* msg) {
   return code;
 }
 
-bool device_accessible(const void* p) {
+// True for device memory of the current device `dev` and for managed
+// memory. Device memory of another GPU is refused: the kernels would read it
+// through peer addressing, which may not be enabled.
+bool device_accessible(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -122,12 +126,12 @@ extern "C" int emd_frame_stats_noalloc(const float* y, const float* v, const uin
              EMD_NOALLOC_MAX_EXPOSURES);
     return na_fail(EMD_EINVAL, m);
   }
-  if (!device_accessible(y) || !device_accessible(v) || !device_accessible(out) ||
-      (mask && !device_accessible(mask)))
-    return na_fail(EMD_EINVAL, "y, v, mask and out must be device pointers");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
     return na_fail(EMD_ECUDA, "no usable current device");
+  if (!device_accessible(y, dev) || !device_accessible(v, dev) || !device_accessible(out, dev) ||
+      (mask && !device_accessible(mask, dev)))
+    return na_fail(EMD_EINVAL, "y, v, mask and out must be device pointers of the current device");
   double* part = nullptr;
   {
     // set-up, once per device with that device current: the host-side name

@@ -37,7 +37,7 @@ EMD_NOISE_STUDENT_T = 1
 
 EXPORTS = [
     "emd_create", "emd_ctx_bytes", "emd_destroy", "emd_last_error", "emd_set_stream",
-    "emd_set_frames", "emd_set_x", "emd_iterate", "emd_get_x", "emd_loglik",
+    "emd_set_frames", "emd_set_x", "emd_iterate", "emd_get_x", "emd_loglik", "emd_loglik_chi2",
     "emd_set_precision", "emd_get_numerator", "emd_get_weights", "emd_frame_stats_noalloc",
     "emd_batch_create", "emd_batch_destroy", "emd_batch_add", "emd_batch_remove",
     "emd_batch_step", "emd_batch_remaining", "emd_batch_sync", "emd_batch_config",
@@ -90,7 +90,8 @@ def load(build_if_missing: bool = False):
         lib.emd_set_x.argtypes = [vp, vp]
         lib.emd_iterate.argtypes = [vp, i]
         lib.emd_get_x.argtypes = [vp, vp]
-        lib.emd_loglik.argtypes = [vp, dp, dp]
+        lib.emd_loglik.argtypes = [vp, dp]
+        lib.emd_loglik_chi2.argtypes = [vp, dp, dp]
         lib.emd_set_precision.argtypes = [vp, i]
         lib.emd_get_numerator.argtypes = [vp, vp]
         lib.emd_get_weights.argtypes = [vp, vp]
@@ -121,7 +122,8 @@ def load(build_if_missing: bool = False):
                      "emd_batch_remaining", "emd_batch_sync", "emd_batch_config"):
             getattr(lib, name).restype = i
         for name in ("emd_set_stream", "emd_set_frames", "emd_set_x", "emd_iterate",
-                     "emd_get_x", "emd_loglik", "emd_set_precision", "emd_get_numerator",
+                     "emd_get_x", "emd_loglik", "emd_loglik_chi2", "emd_set_precision",
+                     "emd_get_numerator",
                      "emd_get_weights"):
             getattr(lib, name).restype = i
         _lib = lib
@@ -219,22 +221,49 @@ def emd_get_weights(ctx, out) -> None:
     _check(load().emd_get_weights(ctx, _ptr(out, np.float32, "out")))
 
 
-def emd_loglik(ctx):
+def emd_loglik(ctx) -> float:
+    """The log-likelihood of the current iterate (FP64)."""
+    ll = C.c_double()
+    _check(load().emd_loglik(ctx, C.byref(ll)))
+    return ll.value
+
+
+def emd_loglik_chi2(ctx):
     """Returns (loglik, chi2), both FP64."""
     ll, chi = C.c_double(), C.c_double()
-    _check(load().emd_loglik(ctx, C.byref(ll), C.byref(chi)))
+    _check(load().emd_loglik_chi2(ctx, C.byref(ll), C.byref(chi)))
     return ll.value, chi.value
 
 
 def emd_frame_stats_noalloc(y, v, mask, H: int, W: int, n: int, out, stream=None) -> None:
     """Per-exposure FP64 statistics (n x 4 doubles into the device tensor
-    ``out``) from device tensors y, v, mask; allocates no device memory."""
+    ``out``) from device tensors y, v, mask; allocates no device memory.
+
+    The C side cannot see buffer sizes, so they are checked here: y and v
+    must be float32 CUDA tensors of at least n*H*W elements, mask (optional)
+    a uint8 CUDA tensor of at least n*H*W, out a contiguous float64 CUDA
+    tensor of at least 4*n, all on the current device."""
+    import torch
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
-    if out is None:
-        raise TypeError("out: need a device tensor of n*4 float64")
-    _check(load().emd_frame_stats_noalloc(_ptr(y, np.float32, "y"), _ptr(v, np.float32, "v"),
-                                          _ptr(mask, np.uint8, "mask"), H, W, n,
+    H, W, n = int(H), int(W), int(n)
+    need = max(n, 0) * max(H, 0) * max(W, 0)
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else None
+    for name, t, dt, cnt in (("y", y, torch.float32, need), ("v", v, torch.float32, need),
+                             ("mask", mask, torch.uint8, need),
+                             ("out", out, torch.float64, 4 * max(n, 0))):
+        if t is None and name == "mask":
+            continue
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name}: need a CUDA tensor")
+        if t.dtype != dt or not t.is_contiguous():
+            raise TypeError(f"{name}: need a contiguous {dt} tensor")
+        if t.device.index != dev:
+            raise ValueError(f"{name}: on cuda:{t.device.index}, the current device is cuda:{dev}")
+        if t.numel() < cnt:
+            raise ValueError(f"{name}: {t.numel()} elements, need at least {cnt}")
+    _check(load().emd_frame_stats_noalloc(y.data_ptr(), v.data_ptr(),
+                                          None if mask is None else mask.data_ptr(), H, W, n,
                                           out.data_ptr(), stream))
 
 
@@ -388,4 +417,5 @@ class Deconvolver:
         return out
 
     def loglik(self):
-        return emd_loglik(self.ctx)
+        """(loglik, chi2) of the current iterate."""
+        return emd_loglik_chi2(self.ctx)

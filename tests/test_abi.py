@@ -103,3 +103,36 @@ def test_ctx_bytes_precision_host_only(lib):
     assert emd.emd_ctx_bytes_precision(4096, 4096, 33, 43, 1, emd.EMD_PREC_SPLIT_BF16) > base
     assert emd.emd_ctx_bytes_precision(256, 256, 4, 14, 1, emd.EMD_PREC_FFT_FP32) == 0
     assert emd.emd_ctx_bytes_precision(256, 256, 4, 15, 1, 99) == 0
+
+
+def test_frame_stats_noalloc_binding_checks_before_the_call(lib):
+    """The C side of emd_frame_stats_noalloc cannot see buffer sizes; the
+    binding refuses host tensors, wrong dtypes and short buffers before the
+    library is called."""
+    import torch
+    from paper_2302_05804_gb300 import emd
+    y = torch.ones((2, 4, 4), dtype=torch.float32)
+    out = torch.zeros(8, dtype=torch.float64)
+    with pytest.raises(TypeError):                    # host (CPU) tensors
+        emd.emd_frame_stats_noalloc(y, y, None, 4, 4, 2, out)
+    with pytest.raises(TypeError):                    # numpy arrays
+        emd.emd_frame_stats_noalloc(y.numpy(), y.numpy(), None, 4, 4, 2, out)
+    if torch.cuda.is_available():
+        yd = y.cuda()
+        with pytest.raises(TypeError):                # float32 out
+            emd.emd_frame_stats_noalloc(yd, yd, None, 4, 4, 2, torch.zeros(8, device="cuda"))
+        with pytest.raises(ValueError):               # out shorter than 4 n
+            emd.emd_frame_stats_noalloc(yd, yd, None, 4, 4, 2,
+                                        torch.zeros(7, dtype=torch.float64, device="cuda"))
+        with pytest.raises(ValueError):               # y shorter than n H W
+            emd.emd_frame_stats_noalloc(yd, yd, None, 4, 4, 3,
+                                        torch.zeros(12, dtype=torch.float64, device="cuda"))
+
+
+def test_loglik_has_the_two_argument_form(lib):
+    """emd_loglik(ctx, out) as the boundary declares it; the data term comes
+    from emd_loglik_chi2."""
+    import ctypes
+    assert lib.emd_loglik.argtypes == [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    assert len(lib.emd_loglik_chi2.argtypes) == 3
+    assert lib.emd_loglik(None, None) == -1           # EMD_EINVAL: no context

@@ -1,9 +1,12 @@
 """Batching: jobs of different shapes advancing together in one persistent
 kernel per step give bit-for-bit the iterates they give alone, including a
-job that joins while others are running (continuous batching)."""
+job that joins while others are running (continuous batching), and each
+job's iterate matches the FP64 oracle's Eq. (2) iterate from the same start
+(1e-5 after one iteration, 1e-4 after several)."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -19,6 +22,16 @@ JOBS = [
 
 def make(i):
     return synth.make_problem("hsc", seed_offset=i, **JOBS[i])
+
+
+def oracle_x(p, k):
+    u, y, N, _ = oracle.prepare(p)
+    return oracle.em_run(np.full((p.r * p.H, p.r * p.W), 5.0), N, u, p.f, k, p.r)
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def ctx_for(emd, p):
@@ -122,7 +135,40 @@ def test_mixed_direct_and_fft_batch_matches_solo_runs_bitwise():
     emd.emd_batch_sync(b)
     for i in range(len(probs)):
         assert emd.emd_batch_remaining(b, slots[i]) == 0
-        np.testing.assert_array_equal(ds[i].x(), solo[i])
+        xb = ds[i].x()
+        np.testing.assert_array_equal(xb, solo[i])
+        err = rel_l2(xb, oracle_x(probs[i], iters[i]))
+        print(f"job {i} (mode {forms[i]}, r = {probs[i].r}): rel L2 vs oracle after "
+              f"{iters[i]} iterations = {err:.2e}")
+        assert err <= 1e-4
+        emd.emd_batch_remove(b, slots[i])
+        ds[i].close()
+    emd.emd_batch_destroy(b)
+
+
+def test_mixed_batch_one_iteration_against_the_oracle():
+    """One iteration of every job in a mixed batch (FFT, halo-exchange and
+    CTA-pair forms, r = 1 and 2, PSFs 7 to 43) against the oracle at the
+    one-iteration bar; one job joins after the others' step."""
+    from paper_2302_05804_gb300 import emd
+    forms = [emd.EMD_PREC_FFT_FP32, emd.EMD_PREC_FP32, emd.EMD_PREC_FP32,
+             emd.EMD_PREC_FP32_PAIR, emd.EMD_PREC_FFT_FP32]
+    probs = [make(i) for i in range(len(JOBS))]
+    ds = []
+    for i, p in enumerate(probs):
+        d = ctx_for(emd, p)
+        d.set_precision(forms[i])
+        ds.append(d)
+    b = emd.emd_batch_create(8)
+    slots = [emd.emd_batch_add(b, ds[i].ctx, 1) for i in range(4)]
+    assert emd.emd_batch_step(b) == 4
+    slots.append(emd.emd_batch_add(b, ds[4].ctx, 1))
+    assert emd.emd_batch_step(b) == 1
+    emd.emd_batch_sync(b)
+    for i, p in enumerate(probs):
+        err = rel_l2(ds[i].x(), oracle_x(p, 1))
+        print(f"job {i} (mode {forms[i]}, r = {p.r}): rel L2 vs oracle after 1 iteration = {err:.2e}")
+        assert err <= 1e-5
         emd.emd_batch_remove(b, slots[i])
         ds[i].close()
     emd.emd_batch_destroy(b)

@@ -26,9 +26,9 @@ def sample_idx(Hf, Wf, k, seed):
 
 
 @pytest.mark.parametrize("recipe,k", [("hsc", 24), ("sr2", 4)])
-def test_full_size_one_iteration_sampled(recipe, k):
+def test_full_size_one_iteration_sampled(recipe, k, request):
     from paper_2302_05804_gb300 import emd
-    p = synth.make_problem(recipe)
+    p = request.getfixturevalue("hsc_problem") if recipe == "hsc" else synth.make_problem(recipe)
     Hf, Wf = p.r * p.H, p.r * p.W
     x0 = (np.random.default_rng(5).uniform(0.5, 1.5, (Hf, Wf)) * 10.0).astype(np.float32)
     d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
@@ -56,13 +56,13 @@ def test_full_size_one_iteration_sampled(recipe, k):
 
 
 @pytest.mark.parametrize("mode,tol", [(1, 5e-3), (2, 2e-3), (3, 1e-4), (4, 1e-4)])
-def test_full_size_tensor_core_forms_sampled(mode, tol):
+def test_full_size_tensor_core_forms_sampled(mode, tol, hsc_problem):
     """The tensor-core forms (BF16, FP16, split BF16, split FP16) at the size
     the bench times them (4096^2 x 33, 43 x 43 PSFs): one iteration against
     the oracle's single-pixel evaluation at sampled pixels, with the bars of
     the smaller tensor-core parity cases (the operand rounding of each form)."""
     from paper_2302_05804_gb300 import emd
-    p = synth.make_problem("hsc")
+    p = hsc_problem
     x0 = (np.random.default_rng(5).uniform(0.5, 1.5, (p.H, p.W)) * 10.0).astype(np.float32)
     d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
     d.set_frames(p.y, p.v, p.f, p.mask)

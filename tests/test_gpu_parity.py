@@ -316,3 +316,61 @@ def test_contexts_order_against_a_busy_legacy_stream(emd):
     ref = run(False)
     got = run(True)
     assert np.array_equal(ref, got)
+
+
+def test_parity_fifty_iterations_k43_with_ring_reuse(emd):
+    """50 iterations of the FP32 halo-exchange kernel with 43 x 43 PSFs on
+    512^2 x 33 exposures: 33 x 32 = 1056 forward items of 64 x 128 tiles
+    against a ring of 971 slots, so slots are reused within every launch
+    (the regime of the full-size workload). Spec bars: 1e-5 after one
+    iteration, 1e-4 after 50."""
+    p = make("hsc", H=512, W=512, seed_offset=7)
+    assert p.n == 33 and p.K == 43
+    ring = (emd.emd_ctx_bytes_precision(512, 512, 33, 43, 1, emd.EMD_PREC_FP32)
+            - emd.emd_ctx_bytes(512, 512, 33, 43, 1))
+    assert ring < 33 * 32 * 64 * 128 * 4                # fewer slots than forward items
+    x0 = start(p, seed=3)
+    u, y, N, _ = oracle.prepare(p)
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    try:
+        d.set_frames(p.y, p.v, p.f, p.mask)
+        d.set_x(x0)
+        d.iterate(1)
+        x1 = d.x()
+        d.iterate(49)
+        x50 = d.x()
+    finally:
+        d.close()
+    xo1 = oracle.em_run(x0, N, u, p.f, 1)
+    assert rel_l2(x1, xo1) <= 1e-5
+    xo50 = oracle.em_run(xo1, N, u, p.f, 49)
+    err = rel_l2(x50, xo50)
+    print(f"512^2 x 33, K = 43: rel L2 after 50 iterations = {err:.2e}")
+    assert err <= 1e-4
+    assert (x50 >= 0).all()
+
+
+def test_default_start_equals_oracle_default_x0(emd):
+    """x^(0) = (sum u y / sum u) / r^2 when positive (Sec. 2 asks only for a
+    strictly positive start): the GPU's FP64 sums against the oracle's, for
+    r = 1 and r = 2, with masks; and 1 when the weighted mean is not
+    positive."""
+    for kw in (dict(), dict(H=96, W=80, n=3, K=15, r=2, fwhm=(3.0, 6.0), mask_frac=0.1,
+                            n_points=30, n_gal=2)):
+        p = make("hsc", **kw) if kw else make(mask_frac=0.05)
+        d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+        d.set_frames(p.y, p.v, p.f, p.mask)
+        x0 = d.x()
+        d.close()
+        u, y, _, c = oracle.prepare(p)
+        assert (x0 == x0.flat[0]).all()
+        assert abs(float(x0.flat[0]) - c) <= 1e-6 * c
+    p = make("hsc", H=40, W=40, n=2, K=5, mask_frac=0.0, n_points=5, n_gal=1)
+    yneg = -np.abs(p.y) - 1.0
+    d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+    d.set_frames(yneg, p.v, p.f, p.mask)
+    x0 = d.x()
+    d.close()
+    u, _ = oracle.weights(p.v, p.mask, yneg)
+    assert oracle.default_x0(yneg.astype(np.float64), u, 1) == 1.0
+    assert (x0 == 1.0).all()

@@ -1,21 +1,24 @@
 """Continuous-batching server: jobs arriving while others run are admitted
 as slots and memory allow, overlap on the device, and each result is
-bit-for-bit the result of running that job alone."""
+bit-for-bit the result of running that job alone and matches the FP64
+oracle's Eq. (2) iterate from the default start (1e-5 after one iteration,
+1e-4 after six)."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("form", ["direct", "fft"])
-def test_served_results_equal_solo_results(form):
+@pytest.mark.parametrize("form,iters", [("direct", 6), ("fft", 6), ("direct", 1), ("fft", 1)])
+def test_served_results_equal_solo_results(form, iters):
     from paper_2302_05804_gb300 import emd, serve
     prec = emd.EMD_PREC_FFT_FP32 if form == "fft" else emd.EMD_PREC_FP32
     pool = serve.DataPool(synth.make_problem("hsc", H=640, W=640, n=6, mask_frac=0.05))
-    trace = serve.poisson_trace(8, rate=200.0, seed=4004, s_range=(64, 300), n_range=(2, 6),
-                                k_range=(15, 43), iters=6)
+    trace = serve.poisson_trace(8, rate=200.0, seed=4004 + iters, s_range=(64, 300),
+                                n_range=(2, 6), k_range=(15, 43), iters=iters)
     # a budget that holds only a few jobs at once forces queueing and reuse
     budget = 3 * max(emd.emd_ctx_bytes_precision(s.H, s.W, s.n, s.K, s.r, prec) for s in trace)
     srv = serve.Server(hbm_budget=budget, max_slots=4, keep_results=True, precision=prec)
@@ -35,3 +38,12 @@ def test_served_results_equal_solo_results(form):
         solo.iterate(spec.iters)
         np.testing.assert_array_equal(by_id[spec.jid].x, solo.x())
         solo.close()
+        # the oracle from its own default start (the iterates of Eq. (2) do
+        # not depend on the scale of a constant start)
+        q = synth.Problem(y=d.y, v=d.v, f=d.f, mask=d.mask, x_true=None, r=spec.r)
+        u, y, N, c = oracle.prepare(q)
+        xo = oracle.em_run(np.full((spec.r * spec.H, spec.r * spec.W), c), N, u, d.f,
+                           spec.iters, spec.r)
+        got = by_id[spec.jid].x.astype(np.float64)
+        err = np.linalg.norm(got - xo) / np.linalg.norm(xo)
+        assert err <= (1e-5 if spec.iters == 1 else 1e-4), (spec, err)

@@ -287,6 +287,48 @@ def test_flux_of_forward_and_adjoint():
         assert abs(oracle.adjoint(w, f, r).sum() - r * r * w.sum()) < 1e-12 * w.sum()
 
 
+def test_flux_conservation_at_the_fixed_point():
+    """Sec. 2: with normalised PSFs the weighted flux is fixed at convergence.
+
+    At a fixed point of Eq. (2) where every x_j > 0, N_j = Den_j for all j.
+    Summing over j, with u_t a constant c_t on exposure t and every source at
+    least 2K pixels from the edges (so that neither F_t nor F_t^T loses flux
+    over the border): sum_t c_t sum_i y_t,i = sum_t c_t sum_j x_j, i.e.
+        sum x = sum_t c_t sum y_t / sum_t c_t.
+    The exposures are scaled by different transparencies s_t, so the data are
+    inconsistent and the identity depends on the weights: weighting by v_t
+    instead of 1/v_t would move the target by 10%. The sky is smooth Gaussian
+    blobs on a tiny positive pedestal, so the fixed point is the unconstrained
+    minimiser (s-bar times the truth, strictly positive) and EM reaches it
+    linearly instead of creeping towards zeros. Data come from scipy's direct
+    convolution, not from the oracle."""
+    g = rng(5)
+    H = W = 32
+    n, K = 3, 5
+    f = np.stack([synth.moffat_psf(K, 1.6, 3.0)] * n)
+    x_true = np.full((H, W), 1e-5)
+    yy, xx = np.mgrid[:H, :W]
+    for _ in range(4):   # centres in [13, 19): >= 2K = 10 pixels from every edge
+        ci, cj = g.uniform(13, 19, 2)
+        x_true += g.lognormal(5, 0.5) * np.exp(-((yy - ci) ** 2 + (xx - cj) ** 2) / 4.5)
+    s = np.array([1.0, 1.3, 0.8])
+    vt = np.array([50.0, 120.0, 300.0])
+    y = np.stack([s[t] * ss.convolve2d(x_true, f[t], mode="same") for t in range(n)])
+    v = np.stack([np.full((H, W), vt[t]) for t in range(n)])
+    u, bad = oracle.weights(v)
+    assert bad == 0
+    c = 1.0 / vt
+    target = (c * y.sum(axis=(1, 2))).sum() / c.sum()
+    wrong = (vt * y.sum(axis=(1, 2))).sum() / vt.sum()
+    assert abs(wrong - target) > 0.05 * target
+    N = oracle.numerator(y, u, f)
+    x = oracle.em_run(np.full((H, W), oracle.default_x0(y, u)), N, u, f, 5000)
+    x_next = oracle.em_step(x, N, u, f)
+    assert np.abs(x_next - x).max() <= 1e-9 * x.max()   # converged
+    assert (x > 0).all()
+    assert abs(x.sum() - target) <= 1e-6 * target
+
+
 def test_em_converges_to_nnls_solution():
     g = rng(17)
     n, H, W = 2, 6, 6
