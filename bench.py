@@ -426,10 +426,18 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    # warm-up
+    # warm-up; the FP32 direct form's autotuner times its tile shapes on the
+    # first iterations of a new problem shape, so warm up until it has decided
     for _ in range(args.warmup):
         d.iterate(1)
     torch.cuda.synchronize()
+    if prec == 0:
+        for _ in range(16):
+            if d.tile_rows()[1]:
+                break
+            d.iterate(1)
+            torch.cuda.synchronize()
+    tile_rows = d.tile_rows() if prec == 0 else None
 
     # timed region: K steps, one fused-kernel launch each, events per step
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -486,6 +494,9 @@ def run_ours(args):
                                "fused": "fused_kernel (FP32 FMA, CTA pairs)"}[kern] +
                               (" heavy-tailed instance" if args.nu > 0 else ""),
                     "peak_source": peak32_src}
+        if prec == 0:
+            roofline["tile"] = (f"{tile_rows[0]} x 128 tiles, {tile_rows[0] // 16} x 16 outputs "
+                                f"per thread ({'autotuned' if tile_rows[1] else 'undecided'})")
         if traffic:
             hbm_peak, hsrc = 6800.0, "fallback 6.8 TB/s"
             try:

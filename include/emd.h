@@ -203,6 +203,23 @@ enum emd_noise {
 };
 int emd_set_noise(emd_ctx *ctx, int model, double nu);
 
+/* Tile shape of the FP32 halo-exchange iteration (EMD_PREC_FP32): the
+ * kernel works on tiles of `rows` x 128 pixels, each of its 128 threads
+ * computing a (rows/16) x 16 block of outputs. rows = 64 (two CTAs per SM),
+ * 48 (three CTAs per SM, at most 168 registers a thread) or 32 (four CTAs
+ * per SM where the shared memory allows); 0 (the default) lets the
+ * autotuner choose: the first iterations of a problem shape (H, W, n, K, r,
+ * noise model) not seen before in this process run each candidate shape
+ * twice, timed with CUDA events on the context's stream and read without
+ * blocking at later calls, and the fastest is kept for every context of
+ * that shape. All shapes give the same iterates bit for bit. EMD_EINVAL for
+ * another value. */
+int emd_set_tile_rows(emd_ctx *ctx, int rows);
+/* The tile rows the next FP32 iteration uses, and *decided = 1 once the
+ * autotuner has decided (or the rows were fixed); either pointer may be
+ * NULL. */
+int emd_get_tile_rows(emd_ctx *ctx, int *rows, int *decided);
+
 /* Self-test of failure detection: launches, on ctx's stream, one CTA that
  * waits on an mbarrier nothing ever arrives on, with the same bounded-wait
  * code the kernels use but a limit of `spins` polls. The wait gives up, the
@@ -233,12 +250,12 @@ int emd_get_weights(emd_ctx *ctx, float *out);
  * bit-for-bit the same iterates in a batch as with emd_iterate alone.
  *
  * An online autotuner picks, per job mix (a signature of the active jobs'
- * size class, Kc, r, exposure count and mode), the FP32 jobs' kernel form
- * and work order and the resident CTA count: the first steps of a new mix
- * each run one candidate (halo-exchange kernel with jobs interleaved
- * round-robin or most expensive first; CTA pairs, all or 3/4 resident),
- * timed with CUDA events, and the fastest is kept. Heavy-tailed noise is
- * not batched.
+ * size class, Kc, r, exposure count and mode), the FP32 jobs' kernel form,
+ * tile shape and work order and the resident CTA count: the first steps of
+ * a new mix each run one candidate (halo-exchange kernel on 64-row tiles
+ * with jobs interleaved round-robin or most expensive first, or on 48-row
+ * tiles; CTA pairs, all or 3/4 resident), timed with CUDA events, and the
+ * fastest is kept. Heavy-tailed noise is not batched.
  * -------------------------------------------------------------------------*/
 typedef struct emd_batch emd_batch;
 
@@ -271,9 +288,11 @@ int emd_batch_sync(emd_batch *b);
 
 /* The autotuner's current choice: resident CTA pairs, work order (0 =
  * job-major, or round-robin over jobs in the halo-exchange form; 1 = most
- * expensive jobs first), the maximum pairs, and the FP32 jobs' form (0 =
- * halo-exchange kernel, 1 = CTA-pair kernel). Any pointer may be NULL. */
-int emd_batch_config(emd_batch *b, int *clusters, int *order, int *max_clusters, int *form);
+ * expensive jobs first), the maximum pairs, the FP32 jobs' form (0 =
+ * halo-exchange kernel, 1 = CTA-pair kernel) and the halo-exchange kernel's
+ * tile rows (64 or 48; see emd_set_tile_rows). Any pointer may be NULL. */
+int emd_batch_config(emd_batch *b, int *clusters, int *order, int *max_clusters, int *form,
+                     int *tile_rows);
 
 /*
  * emd_frame_stats_noalloc -- per-exposure FP64 frame statistics without any

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -126,6 +127,15 @@ struct emd_ctx {
   size_t halo_bytes = 0;
   bool halo_student = false;  // slots hold two tiles (heavy-tailed weights)
   emd::HaloLaunch halo{};
+  // its tile shape: fixed by emd_set_tile_rows (-1: autotuned), and the
+  // autotuner's trials on this context (candidates in launch order, events
+  // around each launch)
+  int tile_forced = -1;
+  int tile_last = 0;
+  std::vector<int> trial_cfg;
+  std::vector<cudaEvent_t> trial_ev;
+  size_t trials_issued = 0;
+  bool trial_student = false;
 };
 
 namespace {
@@ -315,6 +325,7 @@ void emd_destroy(emd_ctx* c) {
   if (!c) return;
   DeviceGuard dg(c->device);
   cudaStreamSynchronize(c->st);  // NULL: the legacy default stream
+  for (cudaEvent_t e : c->trial_ev) cudaEventDestroy(e);
   cudaFree(c->arena);
   if (c->handoff) cudaEventDestroy(c->handoff);
   if (c->tc_arena) cudaFree(c->tc_arena);
@@ -412,6 +423,121 @@ int ensure_halo_arena(emd_ctx* c, bool* ok) {
   c->halo_student = student;
   emd::halo_bind(c->s, student, p, &c->halo);
   *ok = true;
+  return EMD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tile-shape autotuner of the halo-exchange kernel. A process-wide table,
+// keyed by the problem (H, W, n, K, r, noise model), holds the decided tile
+// shape. A context whose key is undecided times the candidate shapes on its
+// own iterations: each candidate runs in turn, twice, with CUDA events
+// around its launch on the context's stream, and the second round's times
+// decide (the first round carries each kernel's first-launch costs). The
+// events are polled without blocking (cudaEventQuery) at later calls, so the
+// iterations stay asynchronous. Every shape gives the same iterates, so
+// trials change nothing but time.
+// ---------------------------------------------------------------------------
+struct TileKey {
+  int H, W, n, K, r, student;
+  bool operator<(const TileKey& o) const {
+    const int a[6] = {H, W, n, K, r, student}, b[6] = {o.H, o.W, o.n, o.K, o.r, o.student};
+    return std::lexicographical_compare(a, a + 6, b, b + 6);
+  }
+};
+std::mutex g_tile_mu;
+std::map<TileKey, int> g_tile_decided;
+
+TileKey tile_key(const emd_ctx* c, bool student) {
+  return TileKey{c->s.H, c->s.W, c->s.n, c->s.K, c->s.r, student ? 1 : 0};
+}
+
+// Candidate shapes for this problem: 64-row tiles always; 48-row tiles when
+// three CTAs fit an SM; 32-row tiles when four do.
+std::vector<int> tile_candidates(const emd_ctx* c) {
+  std::vector<int> v{0};
+  if (emd::halo_tile_ctas_per_sm(c->s, 1) >= 3) v.push_back(1);
+  if (emd::halo_tile_ctas_per_sm(c->s, 2) >= 4) v.push_back(2);
+  return v;
+}
+
+// Reads the trial events if they are all done (no blocking) and records the
+// decision.
+void tile_trials_poll(emd_ctx* c) {
+  if (c->trial_cfg.empty() || c->trials_issued < c->trial_cfg.size()) return;
+  if (cudaEventQuery(c->trial_ev[2 * c->trials_issued - 1]) != cudaSuccess) {
+    cudaGetLastError();  // not ready yet (cudaErrorNotReady is not sticky)
+    return;
+  }
+  const size_t half = c->trial_cfg.size() / 2;
+  int best = c->trial_cfg[half];
+  float best_ms = 0.f;
+  for (size_t i = half; i < c->trial_cfg.size(); ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->trial_ev[2 * i], c->trial_ev[2 * i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (i == half || ms < best_ms) {
+      best_ms = ms;
+      best = c->trial_cfg[i];
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    g_tile_decided[tile_key(c, c->trial_student)] = best;
+  }
+  c->trial_cfg.clear();
+  c->trials_issued = 0;
+}
+
+// Tile shape of the next full-iteration launch; *trial: index of the trial
+// it runs (events to record), or -1.
+int tile_for_launch(emd_ctx* c, bool student, int* trial) {
+  *trial = -1;
+  if (c->tile_forced >= 0) return c->tile_forced;
+  tile_trials_poll(c);
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    auto it = g_tile_decided.find(tile_key(c, student));
+    if (it != g_tile_decided.end()) return it->second;
+  }
+  if (c->trial_cfg.empty() || c->trial_student != student) {
+    const std::vector<int> cand = tile_candidates(c);
+    if (cand.size() < 2) {
+      std::lock_guard<std::mutex> lk(g_tile_mu);
+      g_tile_decided[tile_key(c, student)] = cand[0];
+      return cand[0];
+    }
+    c->trial_cfg.clear();
+    for (int round = 0; round < 2; ++round)
+      for (int cfg : cand) c->trial_cfg.push_back(cfg);
+    c->trials_issued = 0;
+    c->trial_student = student;
+    while (c->trial_ev.size() < 2 * c->trial_cfg.size()) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        c->trial_cfg.clear();
+        return 0;
+      }
+      c->trial_ev.push_back(e);
+    }
+  }
+  if (c->trials_issued < c->trial_cfg.size()) {
+    *trial = (int)c->trials_issued;
+    return c->trial_cfg[c->trials_issued++];
+  }
+  return c->trial_cfg[0];  // all trials issued, not yet read
+}
+
+// One halo-exchange launch of a full iteration, with the autotuner's shape.
+int halo_launch_full(emd_ctx* c, const emd::HaloLaunch& h, bool student) {
+  int trial = -1;
+  const int cfg = tile_for_launch(c, student, &trial);
+  if (trial >= 0) CK(cudaEventRecord(c->trial_ev[2 * trial], c->st));
+  CK(emd::launch_halo_iter(c->s, h, cfg, c->st));
+  if (trial >= 0) CK(cudaEventRecord(c->trial_ev[2 * trial + 1], c->st));
+  c->tile_last = cfg;
   return EMD_OK;
 }
 
@@ -665,7 +791,7 @@ int emd_iterate(emd_ctx* c, int k) {
       emd::HaloLaunch h = c->halo;
       h.a = fused_args(c);
       h.a.Nw = c->Ns;
-      CK(emd::launch_halo_iter(c->s, h, c->st));
+      if (int rc = halo_launch_full(c, h, true)) return rc;
       c->cur ^= 1;
     }
     for (int it = 0; !halo && it < k; ++it) {
@@ -686,7 +812,7 @@ int emd_iterate(emd_ctx* c, int k) {
     if (halo) {
       emd::HaloLaunch h = c->halo;
       h.a = a;
-      CK(emd::launch_halo_iter(c->s, h, c->st));
+      if (int rc = halo_launch_full(c, h, false)) return rc;
     } else {
       CK(emd::launch_fused(c->s, a, 0, c->part, c->st));
     }
@@ -793,15 +919,58 @@ int emd_iterate_streaming(emd_ctx* c, int k, const int* order) {
       a.t0 = t;
       a.t1 = t + 1;
       if (halo) {
+        // one-exposure launches: the shape decided for the full iteration
+        // (or fixed by the caller), without trials of their own
+        int cfg = c->tile_forced;
+        if (cfg < 0) {
+          std::lock_guard<std::mutex> lk(g_tile_mu);
+          auto f = g_tile_decided.find(tile_key(c, false));
+          cfg = f != g_tile_decided.end() ? f->second : 0;
+        }
         emd::HaloLaunch h = c->halo;
         h.a = a;
-        CK(emd::launch_halo_iter(s, h, c->st));
+        CK(emd::launch_halo_iter(s, h, cfg, c->st));
       } else {
         CK(emd::launch_fused(s, a, 0, c->part, c->st));
       }
       c->cur ^= 1;
     }
   }
+  return EMD_OK;
+}
+
+int emd_set_tile_rows(emd_ctx* c, int rows) {
+  if (int rc = check_ctx(c, false)) return rc;
+  if (rows == 0) {
+    c->tile_forced = -1;
+    return EMD_OK;
+  }
+  for (int cfg = 0; cfg < emd::kHaloTileConfigs; ++cfg)
+    if (emd::halo_tile_rows(cfg) == rows) {
+      c->tile_forced = cfg;
+      return EMD_OK;
+    }
+  set_err("emd_set_tile_rows: rows must be 0 (autotuned), 64, 48 or 32");
+  return EMD_EINVAL;
+}
+
+int emd_get_tile_rows(emd_ctx* c, int* rows, int* decided) {
+  if (int rc = check_ctx(c, false)) return rc;
+  DeviceGuard dg(c->device);
+  tile_trials_poll(c);
+  int cfg = c->tile_forced, dec = 1;
+  if (cfg < 0) {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    auto it = g_tile_decided.find(tile_key(c, c->noise == EMD_NOISE_STUDENT_T));
+    if (it != g_tile_decided.end()) {
+      cfg = it->second;
+    } else {
+      cfg = c->tile_last;
+      dec = 0;
+    }
+  }
+  if (rows) *rows = emd::halo_tile_rows(cfg);
+  if (decided) *decided = dec;
   return EMD_OK;
 }
 
@@ -902,6 +1071,10 @@ struct TuneChoice {
   int clusters = 0;
   int order = 1;  // 0: job-major (halo form: round-robin over jobs), 1: most expensive jobs first
   int form = 0;   // FP32 jobs: 0 = halo-exchange kernel, 1 = CTA-pair kernel (same iterates)
+  int tile = 0;   // halo-exchange kernel's tile shape (emd::halo_plan's cfg)
+  bool same_table(const TuneChoice& o) const {
+    return order == o.order && form == o.form && tile == o.tile;
+  }
 };
 
 }  // namespace
@@ -935,7 +1108,7 @@ struct emd_batch {
   int* d_hnitems = nullptr;
   unsigned long long* d_hctrl = nullptr;
   char* harena = nullptr;
-  int halo_ctas = 0;
+  int halo_ctas[emd::kHaloTileConfigs] = {};  // resident CTAs of each tile shape's kernel
   bool has_direct = false, has_fft = false, has_halo = false;
   // captured step graphs, one per (cluster count, parts present)
   std::map<int, cudaGraphExec_t> graphs;
@@ -1014,7 +1187,7 @@ int upload_table(emd_batch* b) {
         Hj.h[k].a = fused_args(c);
         c->cur = save;
       }
-      Hj.pl = emd::halo_plan(c->s, c->s.n);
+      Hj.pl = emd::halo_plan(c->s, c->s.n, b->cur.tile);
       Hj.cur = c->cur;
       Hj.remaining = b->remaining[i];
       hjobs.push_back({(long long)c->s.n * c->s.R2 * c->s.Kc * c->s.Kc * Hj.pl.T, (int)i,
@@ -1094,7 +1267,7 @@ int get_graph(emd_batch* b, int clusters, cudaGraphExec_t* out) {
   // a step: the persistent direct kernel over the FP32 jobs' tiles, then the
   // persistent FFT forward and adjoint kernels over the FFT jobs' tiles
   const int key = clusters | (b->has_direct ? 1 << 20 : 0) | (b->has_fft ? 1 << 21 : 0) |
-                  (b->has_halo ? 1 << 22 : 0);
+                  (b->has_halo ? 1 << 22 : 0) | (b->cur.tile << 23);
   auto it = b->graphs.find(key);
   if (it != b->graphs.end()) {
     *out = it->second;
@@ -1108,10 +1281,10 @@ int get_graph(emd_batch* b, int clusters, cudaGraphExec_t* out) {
                           clusters, b->smem, b->st);
   if (e == cudaSuccess && b->has_halo) {
     // the halo kernel's share of the CTAs follows the tuned cluster count
-    int ctas = b->halo_ctas * clusters / (b->max_clusters > 0 ? b->max_clusters : 1);
+    int ctas = b->halo_ctas[b->cur.tile] * clusters / (b->max_clusters > 0 ? b->max_clusters : 1);
     if (ctas < 1) ctas = 1;
-    e = emd::launch_halo_batch(b->d_hjobs, b->max_jobs, b->d_hitems, b->d_hnitems, b->d_hctrl,
-                               b->d_err, ctas, b->st);
+    e = emd::launch_halo_batch(b->cur.tile, b->d_hjobs, b->max_jobs, b->d_hitems, b->d_hnitems,
+                               b->d_hctrl, b->d_err, ctas, b->st);
   }
   if (e == cudaSuccess && b->has_fft)
     e = emd::launch_fft_batch(b->d_fjobs, b->max_jobs, b->d_fitems, b->d_fnitems, b->d_fcounters,
@@ -1186,8 +1359,8 @@ emd_batch* emd_batch_create(int max_jobs) {
   }
   b->smem = emd::batch_smem_bytes();
   b->max_clusters = emd::batch_max_clusters(b->smem);
-  b->halo_ctas = emd::halo_batch_ctas();
-  if (b->max_clusters <= 0 || b->halo_ctas <= 0) {
+  for (int cfg = 0; cfg < emd::kHaloTileConfigs; ++cfg) b->halo_ctas[cfg] = emd::halo_batch_ctas(cfg);
+  if (b->max_clusters <= 0 || b->halo_ctas[0] <= 0) {
     set_err("emd_batch_create: the persistent kernels cannot be resident");
     cudaFree(b->arena);
     delete b;
@@ -1337,22 +1510,25 @@ int emd_batch_step(emd_batch* b, int* finished) {
     b->trial_ms.clear();
     auto it = b->tuned.find(sig);
     if (it != b->tuned.end()) {
-      if (it->second.order != b->cur.order || it->second.form != b->cur.form) b->dirty = true;
+      if (!it->second.same_table(b->cur)) b->dirty = true;
       b->cur = it->second;
     } else {
       // candidates: the FP32 jobs' form (halo-exchange: round-robin or most
-      // expensive job first; CTA pairs: all or 3/4 of the resident pairs)
+      // expensive job first, 64-row tiles; most expensive first on 48-row
+      // tiles (three CTAs per SM); CTA pairs: all or 3/4 of the resident
+      // pairs)
       const int full = b->max_clusters, part = b->max_clusters - b->max_clusters / 4;
-      b->trying.push_back({full, 0, 0});
-      b->trying.push_back({full, 1, 0});
-      b->trying.push_back({full, 1, 1});
-      b->trying.push_back({part, 1, 1});
+      b->trying.push_back({full, 0, 0, 0});
+      b->trying.push_back({full, 1, 0, 0});
+      if (b->halo_ctas[1] > 0) b->trying.push_back({full, 1, 0, 1});
+      b->trying.push_back({full, 1, 1, 0});
+      b->trying.push_back({part, 1, 1, 0});
       b->dirty = true;
     }
   }
   if (!b->trying.empty()) {
     const TuneChoice next = b->trying[b->trial_ms.size()];
-    if (next.order != b->cur.order || next.form != b->cur.form) b->dirty = true;
+    if (!next.same_table(b->cur)) b->dirty = true;
     b->cur = next;
     timing = true;
   }
@@ -1374,8 +1550,7 @@ int emd_batch_step(emd_batch* b, int* finished) {
       size_t best = 0;
       for (size_t k = 1; k < b->trial_ms.size(); ++k)
         if (b->trial_ms[k] < b->trial_ms[best]) best = k;
-      if (b->trying[best].order != b->cur.order || b->trying[best].form != b->cur.form)
-        b->dirty = true;
+      if (!b->trying[best].same_table(b->cur)) b->dirty = true;
       b->cur = b->trying[best];
       b->tuned[b->sig] = b->cur;
       b->trying.clear();
@@ -1410,12 +1585,14 @@ int emd_batch_sync(emd_batch* b) {
   return EMD_OK;
 }
 
-int emd_batch_config(emd_batch* b, int* clusters, int* order, int* max_clusters, int* form) {
+int emd_batch_config(emd_batch* b, int* clusters, int* order, int* max_clusters, int* form,
+                     int* tile_rows) {
   if (int rc = batch_check(b)) return rc;
   if (clusters) *clusters = b->cur.clusters;
   if (order) *order = b->cur.order;
   if (max_clusters) *max_clusters = b->max_clusters;
   if (form) *form = b->cur.form;
+  if (tile_rows) *tile_rows = emd::halo_tile_rows(b->cur.tile);
   return EMD_OK;
 }
 

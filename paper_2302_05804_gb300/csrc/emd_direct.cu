@@ -72,6 +72,9 @@ bool make_shape(int H, int W, int n, int K, int r, Shape* s, const char** why) {
   g.P = rup(P, 8);
   int PH = (s->gy - 1) * kTile + 2 * s->Rh + 4 * hc + 8;
   if (PH < g.B + H + 1) PH = g.B + H + 1;
+  // the halo-exchange kernel's last row of tiles (TH = 64, 48 or 32 rows)
+  // reaches row ceil(H / TH) TH + hc - 1 <= H + 63 + hc of the image
+  if (PH < H + 64 + 3 * hc) PH = H + 64 + 3 * hc;
   g.PH = PH;
   g.plane = (long long)g.PH * g.P;
   return true;

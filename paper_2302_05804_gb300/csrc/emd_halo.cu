@@ -15,9 +15,15 @@
 // 4096^2, 34 MB), written and read again within a few hundred items, so it
 // stays in L2; no per-exposure image is kept.
 //
-// Tiles are 64 rows x 128 columns, one per CTA of 128 threads (a 4 x 16
-// block of outputs per thread), two CTAs per SM: when one waits at a
-// barrier or on its staging loads, the other keeps the FMA pipes busy.
+// Tiles are TH rows x 128 columns, one per CTA of 128 threads (an RY x 16
+// block of outputs per thread, TH = 16 RY), several CTAs per SM: when one
+// waits at a barrier or on its staging loads, the others keep the FMA pipes
+// busy. Three tile shapes are built (TileCfg below) and the library's
+// autotuner picks one per problem shape: 64-row tiles (4 x 16 outputs per
+// thread, two CTAs per SM), 48-row tiles (3 x 16, at most 168 registers, three
+// CTAs per SM) and 32-row tiles (2 x 16, four CTAs per SM where the shared
+// memory allows). All give the same iterates bit for bit: every output's
+// taps are summed in the same order whatever block it falls in.
 //
 // Item order. One atomic counter hands out a fixed sequence: the first L
 // forward items, then adjoint and forward items alternately, then the last
@@ -43,26 +49,35 @@ namespace emd {
 
 namespace {
 
-constexpr int kHT = 128;   // threads per CTA (two CTAs per SM)
-constexpr int kTH = 64;    // tile rows (columns: kTile = 128)
-constexpr int kTileFloats = kTH * kTile;
-constexpr int kHaloCtasMax = 320;      // grid cap (>= 2 x SMs of one GB300); sizes the ring
+constexpr int kHT = 128;   // threads per CTA: 16 thread rows x 8 thread columns
 constexpr uint32_t kPollLimit = 1u << 23;  // x ~0.3 us per poll: seconds, not a hang
 constexpr int kGather = 8;             // 16-byte loads in flight per thread while staging
+
+// Tile shapes: TH rows (16 thread rows of RY outputs) x 128 columns (8 thread
+// columns of 16 outputs), MINB CTAs per SM requested from the compiler (which
+// caps registers at 65536 / (128 MINB)). CTAS caps the grid (>= MINB x the
+// SMs of one GB300) and, with it, the claim lag and the ring.
+template <int CFG> struct TileCfg;
+template <> struct TileCfg<0> { static constexpr int TH = 64, RY = 4, MINB = 2, CTAS = 320; };
+template <> struct TileCfg<1> { static constexpr int TH = 48, RY = 3, MINB = 3, CTAS = 480; };
+template <> struct TileCfg<2> { static constexpr int TH = 32, RY = 2, MINB = 4, CTAS = 640; };
+
+__host__ __device__ constexpr int cfg_rows(int cfg) { return cfg == 0 ? 64 : cfg == 1 ? 48 : 32; }
+constexpr int cfg_ctas(int cfg) { return cfg == 0 ? 320 : cfg == 1 ? 480 : 640; }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct HaloShape {
-  int rows;   // staged rows: kTH + 2 hc
+  int rows;   // staged rows: TH + 2 hc
   int cols;   // staged columns: kTile + KP
   int pitch;  // floats per staged row; rows also carry a skew of 4 floats every 4 rows
   int buf;    // floats of the staged window
   int ks;     // floats of one Kc x KP kernel
 };
 
-__host__ __device__ inline HaloShape halo_shape(const Shape& s) {
+__host__ __device__ inline HaloShape halo_shape(const Shape& s, int TH) {
   HaloShape h;
-  h.rows = kTH + 2 * s.hc;
+  h.rows = TH + 2 * s.hc;
   h.cols = kTile + s.KP;
   h.pitch = h.cols;  // a multiple of 4: rows start 16-byte aligned; even: the
                      // 8 lanes of a load phase (rows 4 apart) hit distinct bank groups
@@ -71,8 +86,8 @@ __host__ __device__ inline HaloShape halo_shape(const Shape& s) {
   return h;
 }
 
-size_t halo_smem_bytes(const Shape& s) {
-  const HaloShape h = halo_shape(s);
+size_t halo_smem_bytes(const Shape& s, int TH) {
+  const HaloShape h = halo_shape(s, TH);
   return (size_t)(h.buf + h.ks) * sizeof(float);
 }
 
@@ -122,7 +137,7 @@ __device__ __forceinline__ void put4(float* row, int C, int cols, const float4 v
   }
 }
 
-// Forward item: the x window of rows [i0 - hc, i0 + kTH + hc) and columns
+// Forward item: the x window of rows [i0 - hc, i0 + TH + hc) and columns
 // [j0 - hc, j0 - hc + cols) of one padded latent plane (read-only during
 // the launch), through 16-byte loads on the plane's 16-byte grid.
 __device__ void gather_plane(const Shape& s, const HaloShape& hs, const SPlane& sp,
@@ -153,19 +168,20 @@ __device__ void gather_plane(const Shape& s, const HaloShape& hs, const SPlane& 
   }
 }
 
-// Adjoint item: the w window of rows [i0 - hc, i0 + kTH + hc) and columns
+// Adjoint item: the w window of rows [i0 - hc, i0 + TH + hc) and columns
 // [j0 - hc, j0 - hc + cols) from the ring slots of the tile and its
 // neighbours (nb[3 * (dy + 1) + (dx + 1)], null outside the tile grid: w = 0
 // there), `off` floats into each slot. Tile column origins are multiples of
 // 128, so the 16-byte image-column grid is each slot's own. Loads bypass L1
 // (the slots are rewritten by other SMs during the launch).
+template <int TH>
 __device__ void gather_ring(const HaloShape& hs, const SPlane& sp, const float* const* nb,
                             int off, int hc, int i0, int j0) {
   const int c0 = j0 - hc;   // image column of window column 0
   const int q0 = c0 >> 2;   // floor
   const int nq = ((c0 + hs.cols - 1) >> 2) - q0 + 1;
   const int total = hs.rows * nq;
-  const int ti = i0 / kTH, tj = j0 >> 7;
+  const int ti = i0 / TH, tj = j0 >> 7;
   for (int e0 = threadIdx.x; e0 < total; e0 += kHT * kGather) {
     float4 v[kGather];
 #pragma unroll
@@ -175,10 +191,10 @@ __device__ void gather_ring(const HaloShape& hs, const SPlane& sp, const float* 
       if (e < total) {
         const int R = e / nq, m = e - R * nq;
         const int ii = i0 - hc + R, cc = (q0 + m) << 2;
-        const int tr = ii >= 0 ? ii / kTH : -1, tc = cc >> 7;  // floor: neighbour tile row / column
+        const int tr = ii >= 0 ? ii / TH : -1, tc = cc >> 7;  // floor: neighbour tile row / column
         const float* src = nb[3 * (tr - ti + 1) + (tc - tj + 1)];
         if (src)
-          v[q] = __ldcg(reinterpret_cast<const float4*>(src + off + (ii - tr * kTH) * kTile +
+          v[q] = __ldcg(reinterpret_cast<const float4*>(src + off + (ii - tr * TH) * kTile +
                                                          (cc - (tc << 7))));
       }
     }
@@ -227,30 +243,31 @@ __device__ void prefetch_rect(const float* plane, int P, int r0, int nrows, int 
 // reads from DRAM (u, x and Den are each touched once per exposure, so they
 // are not in L2 any more): a forward item's x window and u tile, an adjoint
 // item's Den tile (and x and N for the update of the last exposure).
+template <int TH>
 __device__ void prefetch_item(const Shape& s, const FusedArgs& a, const HaloShape& hs,
                               const HaloPlan& pl, long long sq, int lane) {
   long long id;
   const bool fwd = decode_item(sq, pl.NT, pl.L, &id);
   const int e = (int)(id / pl.T), k = (int)(id - (long long)e * pl.T);
-  const int i0 = (k / s.gx) * kTH, j0 = (k % s.gx) * kTile;
+  const int i0 = (k / s.gx) * TH, j0 = (k % s.gx) * kTile;
   const Geom& g = s.g;
   const int t = a.t0 + e, ne = a.t1 - a.t0;
   if (fwd) {
     for (int phi = 0; phi < s.R2; ++phi)
       prefetch_rect(a.x + (long long)phi * g.plane, g.P, i0 + s.hc, hs.rows, j0 + s.hc, hs.cols,
                     lane);
-    prefetch_rect(a.u + (long long)t * g.plane, g.P, g.B + i0, kTH, g.B + j0, kTile, lane);
+    prefetch_rect(a.u + (long long)t * g.plane, g.P, g.B + i0, TH, g.B + j0, kTile, lane);
     if (a.nu > 0.f)
-      prefetch_rect(a.y + (long long)t * g.plane, g.P, g.B + i0, kTH, g.B + j0, kTile, lane);
+      prefetch_rect(a.y + (long long)t * g.plane, g.P, g.B + i0, TH, g.B + j0, kTile, lane);
   } else {
     for (int phi = 0; phi < s.R2; ++phi) {
       const long long pb = (long long)phi * g.plane;
-      if (e > 0) prefetch_rect(a.Den + pb, g.P, g.B + i0, kTH, g.B + j0, kTile, lane);
+      if (e > 0) prefetch_rect(a.Den + pb, g.P, g.B + i0, TH, g.B + j0, kTile, lane);
       if (e > 0 && a.nu > 0.f)
-        prefetch_rect(a.Nw + pb, g.P, g.B + i0, kTH, g.B + j0, kTile, lane);
+        prefetch_rect(a.Nw + pb, g.P, g.B + i0, TH, g.B + j0, kTile, lane);
       if (e + 1 == ne) {
-        prefetch_rect(a.x + pb, g.P, g.B + i0, kTH, g.B + j0, kTile, lane);
-        prefetch_rect(a.N + pb, g.P, g.B + i0, kTH, g.B + j0, kTile, lane);
+        prefetch_rect(a.x + pb, g.P, g.B + i0, TH, g.B + j0, kTile, lane);
+        prefetch_rect(a.N + pb, g.P, g.B + i0, TH, g.B + j0, kTile, lane);
       }
     }
   }
@@ -265,17 +282,19 @@ __device__ void prefetch_item(const Shape& s, const FusedArgs& a, const HaloShap
 // CTA. claim_next() is called once, after the item's window is staged (the
 // caller takes its next claim there and prefetches for it). nb_s: 9 shared
 // pointers. A wait that gives up sets timed_out.
-template <bool STUDENT, class ClaimNext>
+template <int CFG, bool STUDENT, class ClaimNext>
 __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, const HaloPlan& pl,
                                           long long sq, float* smem, const float** nb_s,
                                           bool& timed_out, ClaimNext&& claim_next) {
+  constexpr int TH = TileCfg<CFG>::TH, RY = TileCfg<CFG>::RY;
+  constexpr int kTileFloats = TH * kTile;
   const FusedArgs& a = h.a;
   const Geom& g = s.g;
-  const HaloShape hs = halo_shape(s);
+  const HaloShape hs = halo_shape(s, TH);
   const SPlane sp{smem, hs.pitch, 2};
   float* ks = smem + hs.buf;
   const int tid = threadIdx.x;
-  const int my = tid & 15, mx = tid >> 4;  // this thread's 4 x 16 outputs: rows 4 my, cols 16 mx
+  const int my = tid & 15, mx = tid >> 4;  // this thread's RY x 16 outputs: rows RY my, cols 16 mx
   const int T = pl.T;
   const long long NT = pl.NT, L = pl.L, RS = pl.R;
   const int ne = a.t1 - a.t0;
@@ -285,12 +304,12 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
   const bool fwd = decode_item(sq, NT, L, &id);
   const int e = (int)(id / T), k = (int)(id - (long long)e * T);
   const int ti = k / s.gx, tj = k - ti * s.gx;
-  const int i0 = ti * kTH, j0 = tj * kTile;
+  const int i0 = ti * TH, j0 = tj * kTile;
   const int t = a.t0 + e;
   bool ok = true;
-  float acc[4][16];
+  float acc[RY][16];
 #pragma unroll
-  for (int p = 0; p < 4; ++p)
+  for (int p = 0; p < RY; ++p)
 #pragma unroll
     for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
 
@@ -342,10 +361,10 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
     if (fwd) {
       gather_plane(s, hs, sp, a.x + (long long)phi * g.plane, i0, j0);
     } else {
-      if (phi == 0) gather_ring(hs, sp, nb_s, pass * kTileFloats, s.hc, i0, j0);
+      if (phi == 0) gather_ring<TH>(hs, sp, nb_s, pass * kTileFloats, s.hc, i0, j0);
       if (step > 0) {
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
+        for (int p = 0; p < RY; ++p)
 #pragma unroll
           for (int c = 0; c < 16; ++c) acc[p][c] = 0.f;
       }
@@ -363,14 +382,14 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
       }
     }
     __syncthreads();  // also orders the slot check above before the stores below
-    corr_tile<4, 16>(acc, sp, 4 * my, 16 * mx, ks, s.KP, s.Kc);
+    corr_tile<RY, 16>(acc, sp, RY * my, 16 * mx, ks, s.KP, s.Kc);
     if (fwd) continue;
     // ---------------- adjoint epilogue: running sum, or the update ----------------
     float* run = pass == 0 ? a.Den : a.Nw;  // running sum over the exposures
     const long long pbase = (long long)phi * g.plane;
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const int i = i0 + 4 * my + p;
+    for (int p = 0; p < RY; ++p) {
+      const int i = i0 + RY * my + p;
       const long long grow = pbase + (long long)(g.B + i) * g.P + g.B + j0 + 16 * mx;
       float2* run2 = reinterpret_cast<float2*>(run + grow);
       if (e > 0) {
@@ -413,14 +432,14 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
     float* wt = h.ring + slot * kSlot;
     const float* up = a.u + (long long)t * g.plane;
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
+    for (int p = 0; p < RY; ++p) {
       // B and P are even: each row of the tile starts 8-byte aligned
-      const long long grow = (long long)(g.B + i0 + 4 * my + p) * g.P + g.B + j0 + 16 * mx;
+      const long long grow = (long long)(g.B + i0 + RY * my + p) * g.P + g.B + j0 + 16 * mx;
       const float2* u2 = reinterpret_cast<const float2*>(up + grow);
-      float4* dst = reinterpret_cast<float4*>(wt + (4 * my + p) * kTile + 16 * mx);
+      float4* dst = reinterpret_cast<float4*>(wt + (RY * my + p) * kTile + 16 * mx);
       if (STUDENT) {
         const float2* y2 = reinterpret_cast<const float2*>(a.y + (long long)t * g.plane + grow);
-        float4* dst2 = reinterpret_cast<float4*>(wt + kTileFloats + (4 * my + p) * kTile + 16 * mx);
+        float4* dst2 = reinterpret_cast<float4*>(wt + kTileFloats + (RY * my + p) * kTile + 16 * mx);
         const float nu1 = a.nu + 1.f;
 #pragma unroll
         for (int c4 = 0; c4 < 4; ++c4) {
@@ -467,14 +486,14 @@ __device__ __forceinline__ void halo_item(const Shape& s, const HaloLaunch& h, c
 }
 
 // One launch per EM iteration of one context (exposures [a.t0, a.t1)).
-template <bool STUDENT>
-__global__ void __launch_bounds__(kHT, 2)
+template <int CFG, bool STUDENT>
+__global__ void __launch_bounds__(kHT, TileCfg<CFG>::MINB)
     halo_kernel(const Shape s, const HaloLaunch h, const HaloPlan pl) {
   extern __shared__ __align__(128) float smem[];
   __shared__ long long item_s;
   __shared__ const float* nb_s[9];
   __shared__ int last_s;
-  const HaloShape hs = halo_shape(s);
+  const HaloShape hs = halo_shape(s, TileCfg<CFG>::TH);
   const int tid = threadIdx.x;
   const long long total = 2 * pl.NT;
   bool timed_out = false;
@@ -497,10 +516,10 @@ __global__ void __launch_bounds__(kHT, 2)
       if (tid < 32) {
         const long long nx = (long long)__shfl_sync(0xffffffffu, nx_raw, 0);
         if (tid == 0) item_s = nx;
-        if (nx < total) prefetch_item(s, h.a, hs, pl, nx, tid);
+        if (nx < total) prefetch_item<TileCfg<CFG>::TH>(s, h.a, hs, pl, nx, tid);
       }
     };
-    halo_item<STUDENT>(s, h, pl, sq, smem, nb_s, timed_out, claim_next);
+    halo_item<CFG, STUDENT>(s, h, pl, sq, smem, nb_s, timed_out, claim_next);
     __syncthreads();  // readers of this item's window and kernel are done; item_s is set
     sq = item_s;
   }
@@ -532,7 +551,8 @@ __global__ void __launch_bounds__(kHT, 2)
 // job has its own ring, flags and abort flag; the list's claim counter and
 // the finished-CTA count are the batch's. The last CTA resets the flags of
 // every job that ran.
-__global__ void __launch_bounds__(kHT, 2)
+template <int CFG>
+__global__ void __launch_bounds__(kHT, TileCfg<CFG>::MINB)
     halo_batch_kernel(const HaloBatchJob* __restrict__ jobs, int njobs,
                       const int2* __restrict__ items, const int* __restrict__ n_items,
                       unsigned long long* ctrl, int* err) {
@@ -562,11 +582,12 @@ __global__ void __launch_bounds__(kHT, 2)
         if (nx < total) {
           const int2 nit = items[nx];
           const HaloBatchJob& NJ = jobs[nit.x];
-          prefetch_item(NJ.s, NJ.h[NJ.cur].a, halo_shape(NJ.s), NJ.pl, nit.y, tid);
+          prefetch_item<TileCfg<CFG>::TH>(NJ.s, NJ.h[NJ.cur].a, halo_shape(NJ.s, TileCfg<CFG>::TH),
+                                          NJ.pl, nit.y, tid);
         }
       }
     };
-    if (J.remaining > 0) halo_item<false>(s, h, pl, it.y, smem, nb_s, timed_out, claim_next);
+    if (J.remaining > 0) halo_item<CFG, false>(s, h, pl, it.y, smem, nb_s, timed_out, claim_next);
     else claim_next();
     __syncthreads();
     q = item_s;
@@ -605,10 +626,11 @@ template <bool STUDENT>
 __global__ void __launch_bounds__(kHT, 2)
     halo_chi2_kernel(const Shape s, const FusedArgs a, const int groups,
                      double* __restrict__ part) {
+  constexpr int kTH = TileCfg<0>::TH;  // 64-row tiles, 4 x 16 outputs per thread
   extern __shared__ __align__(128) float smem[];
   __shared__ double red[kHT / 32];
   const Geom& g = s.g;
-  const HaloShape hs = halo_shape(s);
+  const HaloShape hs = halo_shape(s, kTH);
   const SPlane sp{smem, hs.pitch, 2};
   float* ks = smem + hs.buf;
   const int tid = threadIdx.x;
@@ -692,75 +714,113 @@ cudaError_t launch_flag_wait_selftest(uint32_t limit, void* scratch, int* err, c
   return cudaGetLastError();
 }
 
-HaloPlan halo_plan(const Shape& s, int ne) {
+int halo_tile_rows(int cfg) { return cfg >= 0 && cfg < kHaloTileConfigs ? cfg_rows(cfg) : 0; }
+
+HaloPlan halo_plan(const Shape& s, int ne, int cfg) {
   HaloPlan p;
-  const int gyh = (s.H + kTH - 1) / kTH;
+  p.cfg = cfg;
+  p.TH = cfg_rows(cfg);
+  const int gyh = (s.H + p.TH - 1) / p.TH;
   p.T = s.gx * gyh;
   p.dmax = (gyh > 1 ? s.gx : 0) + (s.gx > 1 ? 1 : 0);
   p.NT = (long long)ne * p.T;
-  p.L = p.dmax + 2LL * kHaloCtasMax;
+  const int cap = cfg_ctas(cfg);
+  p.L = p.dmax + 2LL * cap;
   if (p.L > p.NT) p.L = p.NT;
-  p.R = p.L + p.dmax + 1 + kHaloCtasMax;
+  p.R = p.L + p.dmax + 1 + cap;
   if (p.R > p.NT) p.R = p.NT;
   return p;
 }
 
+namespace {
+// The buffer of one context, shared by every tile shape: the control words,
+// the slot flags and tile counters (each shape uses a prefix of them; all are
+// zero between launches, so the shape may change from one launch to the
+// next), then the ring.
+struct HaloBufLayout {
+  size_t flags, adone, ring, total;
+  long long Rmax;
+  int Tmax;
+};
+
+HaloBufLayout halo_layout(const Shape& s, bool student) {
+  HaloBufLayout b{};
+  size_t ring = 0;
+  for (int cfg = 0; cfg < kHaloTileConfigs; ++cfg) {
+    const HaloPlan p = halo_plan(s, s.n, cfg);
+    if (p.R > b.Rmax) b.Rmax = p.R;
+    if (p.T > b.Tmax) b.Tmax = p.T;
+    const size_t slot = (student ? 2 : 1) * (size_t)p.TH * kTile * sizeof(float);
+    if ((size_t)p.R * slot > ring) ring = (size_t)p.R * slot;
+  }
+  b.flags = 256;
+  b.adone = b.flags + align256((size_t)b.Rmax * sizeof(int));
+  b.ring = b.adone + align256((size_t)b.Tmax * sizeof(int));
+  b.total = b.ring + align256(ring);
+  return b;
+}
+}  // namespace
+
 size_t halo_buffer_bytes(const Shape& s, bool student) {
-  const HaloPlan p = halo_plan(s, s.n);
-  if (2 * p.NT + 2LL * kHaloCtasMax >= (1LL << 31)) return 0;  // 32-bit item ids
-  const size_t slot = (student ? 2 : 1) * (size_t)kTileFloats * sizeof(float);
-  return align256((size_t)p.R * slot) + align256((size_t)p.R * sizeof(int)) +
-         align256((size_t)p.T * sizeof(int)) + 256;
+  // 32-bit item ids: the shape with the most items decides
+  const HaloPlan p = halo_plan(s, s.n, kHaloTileConfigs - 1);
+  if (2 * p.NT + 2LL * cfg_ctas(kHaloTileConfigs - 1) >= (1LL << 31)) return 0;
+  return halo_layout(s, student).total;
 }
 
 void halo_bind(const Shape& s, bool student, void* buf, HaloLaunch* h) {
-  const HaloPlan p = halo_plan(s, s.n);
-  const size_t slot = (student ? 2 : 1) * (size_t)kTileFloats * sizeof(float);
-  char* b = static_cast<char*>(buf);
-  h->ring = reinterpret_cast<float*>(b);
-  b += align256((size_t)p.R * slot);
-  h->fflag = reinterpret_cast<int*>(b);
-  b += align256((size_t)p.R * sizeof(int));
-  h->adone = reinterpret_cast<int*>(b);
-  b += align256((size_t)p.T * sizeof(int));
-  h->ctrl = reinterpret_cast<unsigned long long*>(b);
+  const HaloBufLayout b = halo_layout(s, student);
+  char* base = static_cast<char*>(buf);
+  h->ctrl = reinterpret_cast<unsigned long long*>(base);
+  h->fflag = reinterpret_cast<int*>(base + b.flags);
+  h->adone = reinterpret_cast<int*>(base + b.adone);
+  h->ring = reinterpret_cast<float*>(base + b.ring);
 }
 
-template <bool STUDENT>
-cudaError_t launch_halo_t(const Shape& s, const HaloLaunch& h, const HaloPlan& pl,
-                          cudaStream_t st) {
-  const size_t smem = halo_smem_bytes(s);
-  cudaError_t e = cudaFuncSetAttribute(halo_kernel<STUDENT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+namespace {
+
+template <class Kern>
+cudaError_t resident_ctas(Kern kern, size_t smem, int cap, int* out) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, occ = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_kernel<STUDENT>, kHT,
-                                                         smem)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kHT, smem)) != cudaSuccess)
     return e;
   long long grid = (long long)sms * (occ > 0 ? occ : 1);
-  if (grid > kHaloCtasMax) grid = kHaloCtasMax;
-  if (grid > 2 * pl.NT) grid = 2 * pl.NT;
-  halo_kernel<STUDENT><<<(int)grid, kHT, smem, st>>>(s, h, pl);
+  if (grid > cap) grid = cap;
+  *out = (int)grid;
+  return cudaSuccess;
+}
+
+template <int CFG, bool STUDENT>
+cudaError_t launch_halo_t(const Shape& s, const HaloLaunch& h, const HaloPlan& pl,
+                          cudaStream_t st) {
+  const size_t smem = halo_smem_bytes(s, TileCfg<CFG>::TH);
+  int grid = 0;
+  cudaError_t e = resident_ctas(halo_kernel<CFG, STUDENT>, smem, TileCfg<CFG>::CTAS, &grid);
+  if (e != cudaSuccess) return e;
+  if (grid > 2 * pl.NT) grid = (int)(2 * pl.NT);
+  halo_kernel<CFG, STUDENT><<<grid, kHT, smem, st>>>(s, h, pl);
   return cudaGetLastError();
 }
 
-size_t halo_batch_smem_bytes() {
+// dynamic shared memory of the batch kernels: the largest accepted footprint
+size_t halo_batch_smem_bytes(int TH) {
   size_t m = 0;
   for (int hc = 0; hc <= EMD_MAX_HC; ++hc) {
     Shape s{};
     s.hc = hc;
     s.Kc = 2 * hc + 1;
     s.KP = (s.Kc + 3) / 4 * 4;
-    const size_t b = halo_smem_bytes(s);
+    const size_t b = halo_smem_bytes(s, TH);
     if (b > m) m = b;
   }
   return m;
 }
 
-namespace {
 __global__ void halo_batch_advance_kernel(HaloBatchJob* __restrict__ jobs, int njobs) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < njobs && jobs[j].remaining > 0) {
@@ -768,40 +828,90 @@ __global__ void halo_batch_advance_kernel(HaloBatchJob* __restrict__ jobs, int n
     jobs[j].cur ^= 1;
   }
 }
-}  // namespace
 
-int halo_batch_ctas() {
-  const size_t smem = halo_batch_smem_bytes();
-  if (cudaFuncSetAttribute(halo_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return 0;
-  int dev = 0, sms = 0, occ = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_batch_kernel, kHT, smem) !=
-          cudaSuccess) {
+template <int CFG>
+int halo_batch_ctas_t() {
+  int grid = 0;
+  if (resident_ctas(halo_batch_kernel<CFG>, halo_batch_smem_bytes(TileCfg<CFG>::TH),
+                    TileCfg<CFG>::CTAS, &grid) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  return sms * (occ > 0 ? occ : 1);
+  return grid;
 }
 
-cudaError_t launch_halo_batch(const HaloBatchJob* jobs, int njobs, const int2* items,
-                              const int* n_items, unsigned long long* ctrl, int* err, int ctas,
-                              cudaStream_t st) {
-  const size_t smem = halo_batch_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(halo_batch_kernel,
+template <int CFG>
+cudaError_t launch_halo_batch_t(const HaloBatchJob* jobs, int njobs, const int2* items,
+                                const int* n_items, unsigned long long* ctrl, int* err, int ctas,
+                                cudaStream_t st) {
+  const size_t smem = halo_batch_smem_bytes(TileCfg<CFG>::TH);
+  cudaError_t e = cudaFuncSetAttribute(halo_batch_kernel<CFG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  halo_batch_kernel<<<ctas, kHT, smem, st>>>(jobs, njobs, items, n_items, ctrl, err);
+  if (ctas > TileCfg<CFG>::CTAS) ctas = TileCfg<CFG>::CTAS;
+  halo_batch_kernel<CFG><<<ctas, kHT, smem, st>>>(jobs, njobs, items, n_items, ctrl, err);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   halo_batch_advance_kernel<<<(njobs + 127) / 128, 128, 0, st>>>(const_cast<HaloBatchJob*>(jobs),
                                                                  njobs);
   return cudaGetLastError();
 }
 
+}  // namespace
+
+int halo_batch_ctas(int cfg) {
+  switch (cfg) {
+    case 0: return halo_batch_ctas_t<0>();
+    case 1: return halo_batch_ctas_t<1>();
+    case 2: return halo_batch_ctas_t<2>();
+  }
+  return 0;
+}
+
+cudaError_t launch_halo_batch(int cfg, const HaloBatchJob* jobs, int njobs, const int2* items,
+                              const int* n_items, unsigned long long* ctrl, int* err, int ctas,
+                              cudaStream_t st) {
+  switch (cfg) {
+    case 0: return launch_halo_batch_t<0>(jobs, njobs, items, n_items, ctrl, err, ctas, st);
+    case 1: return launch_halo_batch_t<1>(jobs, njobs, items, n_items, ctrl, err, ctas, st);
+    case 2: return launch_halo_batch_t<2>(jobs, njobs, items, n_items, ctrl, err, ctas, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int halo_tile_ctas_per_sm(const Shape& s, int cfg) {
+  int occ = 0;
+  const size_t smem = halo_smem_bytes(s, cfg_rows(cfg));
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (cfg) {
+    case 0:
+      e = cudaFuncSetAttribute(halo_kernel<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_kernel<0, false>, kHT, smem);
+      break;
+    case 1:
+      e = cudaFuncSetAttribute(halo_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_kernel<1, false>, kHT, smem);
+      break;
+    case 2:
+      e = cudaFuncSetAttribute(halo_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_kernel<2, false>, kHT, smem);
+      break;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return occ;
+}
+
 int launch_halo_chi2(const Shape& s, const FusedArgs& a, double* part, int max_parts,
                      cudaStream_t st, cudaError_t* err) {
+  constexpr int kTH = TileCfg<0>::TH;
   const int T = s.gx * ((s.H + kTH - 1) / kTH);
   int groups = max_parts / T;
   if (groups > s.n) groups = s.n;
@@ -809,29 +919,30 @@ int launch_halo_chi2(const Shape& s, const FusedArgs& a, double* part, int max_p
     *err = cudaErrorInvalidValue;
     return 0;
   }
-  const size_t smem = halo_smem_bytes(s);
+  const size_t smem = halo_smem_bytes(s, kTH);
   auto kern = a.nu > 0.f ? halo_chi2_kernel<true> : halo_chi2_kernel<false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int dev = 0, sms = 0, occ = 0;
-  if (e == cudaSuccess) e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kHT, smem);
+  int grid = 0;
+  cudaError_t e = resident_ctas(kern, smem, 1 << 30, &grid);
   if (e != cudaSuccess) {
     *err = e;
     return 0;
   }
-  long long grid = (long long)sms * (occ > 0 ? occ : 1);
-  if (grid > (long long)T * groups) grid = (long long)T * groups;
-  kern<<<(int)grid, kHT, smem, st>>>(s, a, groups, part);
+  if (grid > T * groups) grid = T * groups;
+  kern<<<grid, kHT, smem, st>>>(s, a, groups, part);
   *err = cudaGetLastError();
   return T * groups;
 }
 
-cudaError_t launch_halo_iter(const Shape& s, const HaloLaunch& h, cudaStream_t st) {
+cudaError_t launch_halo_iter(const Shape& s, const HaloLaunch& h, int cfg, cudaStream_t st) {
   const int ne = h.a.t1 - h.a.t0;
-  if (ne <= 0 || ne > s.n) return cudaErrorInvalidValue;
-  const HaloPlan pl = halo_plan(s, ne);
-  return h.a.nu > 0.f ? launch_halo_t<true>(s, h, pl, st) : launch_halo_t<false>(s, h, pl, st);
+  if (ne <= 0 || ne > s.n || cfg < 0 || cfg >= kHaloTileConfigs) return cudaErrorInvalidValue;
+  const HaloPlan pl = halo_plan(s, ne, cfg);
+  const bool st_ = h.a.nu > 0.f;
+  switch (cfg) {
+    case 0: return st_ ? launch_halo_t<0, true>(s, h, pl, st) : launch_halo_t<0, false>(s, h, pl, st);
+    case 1: return st_ ? launch_halo_t<1, true>(s, h, pl, st) : launch_halo_t<1, false>(s, h, pl, st);
+    default: return st_ ? launch_halo_t<2, true>(s, h, pl, st) : launch_halo_t<2, false>(s, h, pl, st);
+  }
 }
 
 }  // namespace emd

@@ -42,7 +42,7 @@ EXPORTS = [
     "emd_batch_create", "emd_batch_destroy", "emd_batch_add", "emd_batch_remove",
     "emd_batch_step", "emd_batch_remaining", "emd_batch_sync", "emd_batch_config",
     "emd_selftest_wait_timeout", "emd_iterate_streaming", "emd_fit_psf", "emd_set_noise",
-    "emd_measure_fma_rate", "emd_ctx_bytes_precision",
+    "emd_measure_fma_rate", "emd_ctx_bytes_precision", "emd_set_tile_rows", "emd_get_tile_rows",
 ]
 
 
@@ -111,7 +111,11 @@ def load(build_if_missing: bool = False):
         lib.emd_batch_step.argtypes = [vp, ip]
         lib.emd_batch_remaining.argtypes = [vp, i]
         lib.emd_batch_sync.argtypes = [vp]
-        lib.emd_batch_config.argtypes = [vp, ip, ip, ip, ip]
+        lib.emd_batch_config.argtypes = [vp, ip, ip, ip, ip, ip]
+        lib.emd_set_tile_rows.argtypes = [vp, i]
+        lib.emd_set_tile_rows.restype = i
+        lib.emd_get_tile_rows.argtypes = [vp, ip, ip]
+        lib.emd_get_tile_rows.restype = i
         lib.emd_fit_psf.argtypes = [vp, i, i, i, vp, i, vp, C.c_float, C.c_float, i, vp, vp]
         lib.emd_fit_psf.restype = i
         lib.emd_set_noise.argtypes = [vp, i, C.c_double]
@@ -354,9 +358,24 @@ def emd_batch_sync(b) -> None:
 
 
 def emd_batch_config(b):
-    c, o, m, f = C.c_int(), C.c_int(), C.c_int(), C.c_int()
-    _check(load().emd_batch_config(b, C.byref(c), C.byref(o), C.byref(m), C.byref(f)))
-    return {"clusters": c.value, "order": o.value, "max_clusters": m.value, "form": f.value}
+    c, o, m, f, t = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(load().emd_batch_config(b, C.byref(c), C.byref(o), C.byref(m), C.byref(f),
+                                   C.byref(t)))
+    return {"clusters": c.value, "order": o.value, "max_clusters": m.value, "form": f.value,
+            "tile_rows": t.value}
+
+
+def emd_set_tile_rows(ctx, rows: int) -> None:
+    """Tile rows of the FP32 halo-exchange iteration: 64, 48, 32, or 0 for
+    the autotuner's choice."""
+    _check(load().emd_set_tile_rows(ctx, int(rows)))
+
+
+def emd_get_tile_rows(ctx):
+    """(rows, decided): the tile rows the next FP32 iteration uses."""
+    r, d = C.c_int(), C.c_int()
+    _check(load().emd_get_tile_rows(ctx, C.byref(r), C.byref(d)))
+    return r.value, bool(d.value)
 
 
 # -- convenience wrapper --------------------------------------------------------
@@ -399,6 +418,12 @@ class Deconvolver:
 
     def set_noise(self, model, nu=0.0):
         emd_set_noise(self.ctx, model, nu)
+
+    def set_tile_rows(self, rows):
+        emd_set_tile_rows(self.ctx, rows)
+
+    def tile_rows(self):
+        return emd_get_tile_rows(self.ctx)
 
     def x(self, out=None):
         if out is None:

@@ -88,16 +88,20 @@ def test_fit_psf_rejects_bad_arguments_before_touching_the_gpu(lib):
 def test_ctx_bytes_precision_host_only(lib):
     from paper_2302_05804_gb300 import emd
     base = emd.emd_ctx_bytes(4096, 4096, 33, 43, 1)
-    # FP32: the halo-exchange kernel's ring of 64 x 128 tiles: R = L + dmax + 1 + 320
-    # slots, L = dmax + 640 (adjoint lag), dmax = 32 + 1 tile ids, plus the flags
-    # (1027 slots, 2048 tile counters)
-    ring = 1027 * 64 * 128 * 4 + 4352 + 8192 + 256
+    # FP32: the halo-exchange kernel's buffer serves its three tile shapes
+    # (TH = 64, 48, 32 rows of 128 columns; grid caps 320, 480, 640 CTAs):
+    # R = L + dmax + 1 + cap slots, L = dmax + 2 cap (adjoint lag), dmax = 32 + 1
+    # tile ids. Control words (256 B), slot flags for the most slots (TH = 32:
+    # 1987), tile counters for the most tiles (32 x 128 = 4096), then the
+    # largest ring (TH = 48: 1507 slots of 48 x 128 floats).
+    ring = 256 + 8192 + 16384 + 1507 * 48 * 128 * 4
     assert emd.emd_ctx_bytes_precision(4096, 4096, 33, 43, 1, emd.EMD_PREC_FP32) == base + ring
     assert emd.emd_ctx_bytes_precision(4096, 4096, 33, 43, 1, emd.EMD_PREC_FP32_PAIR) == base
-    # small problems: the ring holds all n * T tiles (4 exposures x 8 tiles)
+    # small problems: the ring holds all n * T tiles (4 exposures x 12 tiles
+    # of 48 rows is the largest)
     small = emd.emd_ctx_bytes(256, 256, 4, 15, 1)
     assert (emd.emd_ctx_bytes_precision(256, 256, 4, 15, 1, emd.EMD_PREC_FP32)
-            == small + 32 * 64 * 128 * 4 + 256 + 256 + 256)
+            == small + 256 + 256 + 256 + 48 * 48 * 128 * 4)
     fft = emd.emd_ctx_bytes_precision(4096, 4096, 33, 43, 1, emd.EMD_PREC_FFT_FP32)
     assert base + 33 * 4096 * 4096 * 4 < fft < base + 33 * 4300 * 4300 * 4 + 10e6
     assert emd.emd_ctx_bytes_precision(4096, 4096, 33, 43, 1, emd.EMD_PREC_SPLIT_BF16) > base

@@ -63,7 +63,7 @@ SHAPES = [(1, 1), (1, 3), (3, 1), (2, 2), (5, 4), (8, 8), (4, 9)]
 
 @pytest.mark.parametrize("gx,gy", SHAPES)
 @pytest.mark.parametrize("ne", [1, 2, 5])
-@pytest.mark.parametrize("cap", [1, 3, 160])
+@pytest.mark.parametrize("cap", [1, 3, 160, 320, 480, 640])
 def test_dependencies_are_claimed_earlier(gx, gy, ne, cap):
     T, dmax, NT, L, R = plan(gx, gy, ne, cap)
     pos = {}
