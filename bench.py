@@ -271,11 +271,15 @@ def run_serving(p, args, precision=0, jobs=2000):
               iters=50)
     sat_trace = serve.poisson_trace(jobs, rate=1e9, seed=4004, **kw)
     srv = serve.Server(hbm_budget=80e9, max_slots=64, precision=precision)
+    t0 = time.perf_counter()
     try:
         res = srv.run(sat_trace, pool.make, realtime=False)
     finally:
         srv.close()
     sat = serve.Server.summary(res)
+    print(f"serving ({'fft' if precision == 5 else 'direct'}): {len(res)} jobs saturated, "
+          f"{sat['jobs_per_s']:.1f} jobs/s, {time.perf_counter() - t0:.0f} s", file=sys.stderr,
+          flush=True)
     per_rate = {}
     for frac in (0.5, 0.7, 0.9):
         rate_f = frac * sat["jobs_per_s"]
@@ -286,6 +290,9 @@ def run_serving(p, args, precision=0, jobs=2000):
         finally:
             srv.close()
         per_rate[frac] = (rate_f, trace_f, res_f, serve.Server.summary(res_f))
+        print(f"serving at {frac}x: p50 {per_rate[frac][3]['p50_s']:.3f} s, "
+              f"p99 {per_rate[frac][3]['p99_s']:.3f} s over {len(res_f)} jobs", file=sys.stderr,
+              flush=True)
     rate, trace, res, live = per_rate[0.7]
     fma = sum(2.0 * s.n * s.H * s.W * s.K ** 2 * s.iters for s in trace)
     return {"form": "fft" if precision == 5 else "direct fp32",

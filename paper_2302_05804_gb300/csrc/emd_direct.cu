@@ -25,6 +25,10 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "emd_corr.cuh"
 #include "emd_internal.cuh"
 
@@ -33,6 +37,27 @@ namespace cg = cooperative_groups;
 namespace emd {
 
 static inline int rup(int a, int b) { return (a + b - 1) / b * b; }
+
+cudaError_t allow_max_dynamic_smem(const void* func) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({func, dev})) return cudaSuccess;
+  int optin = 0;
+  cudaFuncAttributes fa;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncGetAttributes(&fa, func)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes)) != cudaSuccess)
+    return e;
+  done.insert({func, dev});
+  return cudaSuccess;
+}
 
 bool make_shape(int H, int W, int n, int K, int r, Shape* s, const char** why) {
   if (H < 1 || W < 1 || n < 1) { *why = "H, W and n must be >= 1"; return false; }
@@ -393,9 +418,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 template <bool STUDENT>
 cudaError_t launch_fused_t(const Shape& s, const FusedArgs& a, int mode, double* part,
                            cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(fused_kernel<STUDENT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)s.smem_fused);
+  cudaError_t e = allow_max_dynamic_smem((const void*)fused_kernel<STUDENT>);
   if (e != cudaSuccess) return e;
   dim3 grid(2 * s.gx, s.gy), block(kThreads);
   fused_kernel<STUDENT><<<grid, block, s.smem_fused, st>>>(s, a, mode, part);
@@ -479,9 +502,7 @@ size_t batch_smem_bytes() {
 int batch_max_clusters(size_t smem) {
   static int cached = -1;
   if (cached >= 0) return cached;
-  if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return -1;
+  if (allow_max_dynamic_smem((const void*)batch_kernel) != cudaSuccess) return -1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2, 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
@@ -497,8 +518,7 @@ int batch_max_clusters(size_t smem) {
 
 cudaError_t launch_batch(const BatchJob* jobs, int njobs, const int2* items, const int* n_items,
                          int* counter, int* err, int clusters, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_max_dynamic_smem((const void*)batch_kernel);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;

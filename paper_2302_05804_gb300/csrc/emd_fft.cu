@@ -732,8 +732,7 @@ int fft_tile_side(const Shape& s) { return kFT - 2 * s.hc; }
 
 cudaError_t launch_fft_spectra(const Shape& s, const float* ka, float2* spec, cudaStream_t st) {
   const size_t smem = (size_t)kFBuf * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(fft_spectra_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_dynamic_smem((const void*)fft_spectra_kernel);
   if (e != cudaSuccess) return e;
   fft_spectra_kernel<<<s.n * s.R2, kFThreads, smem, st>>>(ka, s.Kc, s.KP, spec);
   return cudaGetLastError();
@@ -749,11 +748,8 @@ int fft_tiles_total(const Shape& s) { return (int)fft_tiles(s); }
 cudaError_t launch_fft_batch(const FftBatchJob* jobs, int njobs, const int2* items,
                              const int* n_items, int* counters, int ctas, cudaStream_t st) {
   const size_t smem = fft_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(fft_batch_forward_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fft_batch_adjoint_kernel,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_dynamic_smem((const void*)fft_batch_forward_kernel);
+  if (e == cudaSuccess) e = allow_max_dynamic_smem((const void*)fft_batch_adjoint_kernel);
   if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 2 * sizeof(int), st);
   if (e != cudaSuccess) return e;
   fft_batch_forward_kernel<<<ctas, kFThreads, smem, st>>>(jobs, items, n_items, counters);
@@ -769,11 +765,8 @@ cudaError_t launch_fft_batch(const FftBatchJob* jobs, int njobs, const int2* ite
 
 cudaError_t launch_fft_iter(const Shape& s, const FftLaunch& a, cudaStream_t st) {
   const size_t smem = fft_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(fft_forward_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fft_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+  cudaError_t e = allow_max_dynamic_smem((const void*)fft_forward_kernel);
+  if (e == cudaSuccess) e = allow_max_dynamic_smem((const void*)fft_adjoint_kernel);
   if (e != cudaSuccess) return e;
   const int B = fft_tile_side(s);
   const dim3 grid((s.g.W + B - 1) / B, (s.g.H + B - 1) / B);

@@ -781,7 +781,7 @@ namespace {
 
 template <class Kern>
 cudaError_t resident_ctas(Kern kern, size_t smem, int cap, int* out) {
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_dynamic_smem((const void*)kern);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, occ = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -845,8 +845,7 @@ cudaError_t launch_halo_batch_t(const HaloBatchJob* jobs, int njobs, const int2*
                                 const int* n_items, unsigned long long* ctrl, int* err, int ctas,
                                 cudaStream_t st) {
   const size_t smem = halo_batch_smem_bytes(TileCfg<CFG>::TH);
-  cudaError_t e = cudaFuncSetAttribute(halo_batch_kernel<CFG>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_dynamic_smem((const void*)halo_batch_kernel<CFG>);
   if (e != cudaSuccess) return e;
   if (ctas > TileCfg<CFG>::CTAS) ctas = TileCfg<CFG>::CTAS;
   halo_batch_kernel<CFG><<<ctas, kHT, smem, st>>>(jobs, njobs, items, n_items, ctrl, err);
@@ -884,20 +883,17 @@ int halo_tile_ctas_per_sm(const Shape& s, int cfg) {
   cudaError_t e = cudaErrorInvalidValue;
   switch (cfg) {
     case 0:
-      e = cudaFuncSetAttribute(halo_kernel<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
+      e = allow_max_dynamic_smem((const void*)halo_kernel<0, false>);
       if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_kernel<0, false>, kHT, smem);
       break;
     case 1:
-      e = cudaFuncSetAttribute(halo_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
+      e = allow_max_dynamic_smem((const void*)halo_kernel<1, false>);
       if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_kernel<1, false>, kHT, smem);
       break;
     case 2:
-      e = cudaFuncSetAttribute(halo_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
+      e = allow_max_dynamic_smem((const void*)halo_kernel<2, false>);
       if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, halo_kernel<2, false>, kHT, smem);
       break;

@@ -99,6 +99,13 @@ cudaError_t launch_batch(const BatchJob* jobs, int njobs, const int2* items, con
 // sets the thread-local message returned by emd_last_error (emd_api.cu)
 void set_error_message(const char* msg);
 
+// Raises a kernel's dynamic shared-memory limit to the most the current
+// device allows it (the opt-in maximum per block less the kernel's static
+// shared memory), once per kernel and device. The limit is never set to one
+// launch's size: host threads launching one kernel for problems of different
+// shapes would race, one thread's smaller setting failing another's launch.
+cudaError_t allow_max_dynamic_smem(const void* func);
+
 // kernels (emd_direct.cu)
 cudaError_t launch_setup(const Shape& s, const SetupArgs& a, cudaStream_t st);
 cudaError_t launch_reduce_final(const double* part, int nblocks, int ncols,

@@ -349,8 +349,7 @@ template <int KG>
 cudaError_t launch_fit(int n, int creq, int K, int r, size_t smem, const float* f,
                        const float* g, const float* h0, float lambda, float lr, int iters,
                        float* mom, float* hn, float* hout, float* loss) {
-  cudaError_t e = cudaFuncSetAttribute(psf_fit_kernel<KG>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_dynamic_smem((const void*)psf_fit_kernel<KG>);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(kPsfThreads, 1, 1);

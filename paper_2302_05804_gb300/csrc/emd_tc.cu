@@ -715,16 +715,10 @@ cudaError_t launch_fp16_scales(const unsigned int* xmax_bits, float gscale, floa
 
 cudaError_t launch_tc_iter(const Shape& s, const TcShape& t, const TcLaunch& L,
                            const CUtensorMap& map, cudaStream_t st) {
-  static size_t attr1 = 0, attr3 = 0;
-  size_t& attr = (t.nprod == 3) ? attr3 : attr1;
-  if (t.smem > attr) {
-    cudaError_t e = (t.nprod == 3)
-                        ? cudaFuncSetAttribute(tc_iter_kernel<3>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem)
-                        : cudaFuncSetAttribute(tc_iter_kernel<1>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
+  {
+    cudaError_t e = allow_max_dynamic_smem(t.nprod == 3 ? (const void*)tc_iter_kernel<3>
+                                                       : (const void*)tc_iter_kernel<1>);
     if (e != cudaSuccess) return e;
-    attr = t.smem;
   }
   TcArgs a;
   a.x = L.x;
