@@ -428,6 +428,8 @@ def run_ours(args):
         d.set_precision(prec)
     if args.nu > 0:
         d.set_noise(emd.EMD_NOISE_STUDENT_T, args.nu)
+    if args.tile_rows:
+        d.set_tile_rows(args.tile_rows)
 
     def barrier():
         if world > 1:
@@ -541,18 +543,31 @@ def run_ours(args):
         h2d = sum(a.numel() * a.element_size() for a in (hy, hv, hf, hm))
         d2h = hx.numel() * 4 + 8
 
-        def job():
+        parts = {"set_frames_s": 0.0, "iterations_and_loglik_s": 0.0, "get_x_s": 0.0}
+
+        def job(record):
+            # host timestamps between the calls; every call that returns to
+            # the host already synchronises the stream (set_frames from host
+            # buffers, loglik, get_x), so none is added here
+            ta = time.perf_counter()
             d.set_frames(hy, hv, hf, hm)
+            tb = time.perf_counter()
             d.iterate(args.e2e_iters)
             d.loglik()
+            tc = time.perf_counter()
             emd.emd_get_x(d.ctx, hx)
+            td = time.perf_counter()
+            if record:
+                parts["set_frames_s"] += tb - ta
+                parts["iterations_and_loglik_s"] += tc - tb
+                parts["get_x_s"] += td - tc
 
-        job()  # warm
+        job(False)  # warm
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_jobs):
-            job()
+            job(True)
         torch.cuda.synchronize()
         el = torch.tensor([time.perf_counter() - t0], device="cuda")
         if world > 1:
@@ -560,7 +575,8 @@ def run_ours(args):
         e2e = {"value": Hf * Wf * p.n * args.e2e_iters * args.e2e_jobs * world / el.item() / 1e9,
                "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "iters_per_step": args.e2e_iters,
-               "step": "set_frames + iterations + loglik + get_x, host pinned buffers"}
+               "step": "set_frames + iterations + loglik + get_x, host pinned buffers",
+               "components_s_per_step": {k: v / args.e2e_jobs for k, v in parts.items()}}
     d.close()
 
     serving = serving_direct = None
@@ -630,6 +646,8 @@ def main():
                          "(0: Gaussian, Eq. (1))")
     ap.add_argument("--psf-iters", type=int, default=20000,
                     help="Adam iterations of the Eq. (4) PSF fit sample (0 disables it)")
+    ap.add_argument("--tile-rows", type=int, default=0, choices=[0, 64, 48, 32],
+                    help="tile rows of the FP32 halo-exchange kernel (0: autotuned)")
     ap.add_argument("--cpu-crop", type=int, default=512)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-crop", type=int, default=256)

@@ -102,24 +102,33 @@ __device__ __forceinline__ void init_twiddles(TwTab& T) {
   __syncthreads();
 }
 
-// One 128-point FFT per warp, in registers: lane l holds v[q] = x[32 q + l].
-// Decimation in frequency (natural in, bit-reversed out): the spans 64 and
-// 32 pair the four values a lane holds; spans 16 .. 1 pair lanes l and
-// l ^ s through shuffles.
-__device__ __forceinline__ void warp_fft_dif(float2 (&v)[4], const TwTab& T, int lane) {
+// J independent 128-point FFTs per warp, in registers: lane l holds
+// v[j][q] = x_j[32 q + l]. Decimation in frequency (natural in, bit-reversed
+// out): the spans 64 and 32 pair the four values a lane holds; spans 16 .. 1
+// pair lanes l and l ^ s through shuffles. The J transforms share the
+// twiddle loads, and their independent shuffles and butterflies overlap the
+// latency of one another (J = 2 in the row and column passes).
+template <int J>
+__device__ __forceinline__ void warp_fft_dif(float2 (&v)[J][4], const TwTab& T, int lane) {
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    const float2 a = v[q], b = v[q + 2];
-    v[q] = cadd(a, b);
-    v[q + 2] = cmul(csub(a, b), T.w[32 * q + lane]);
+    const float2 t = T.w[32 * q + lane];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const float2 a = v[j][q], b = v[j][q + 2];
+      v[j][q] = cadd(a, b);
+      v[j][q + 2] = cmul(csub(a, b), t);
+    }
   }
   const float2 t1 = T.lane2[lane];
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    const float2 a = v[2 * p], b = v[2 * p + 1];
-    v[2 * p] = cadd(a, b);
-    v[2 * p + 1] = cmul(csub(a, b), t1);
-  }
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const float2 a = v[j][2 * p], b = v[j][2 * p + 1];
+      v[j][2 * p] = cadd(a, b);
+      v[j][2 * p + 1] = cmul(csub(a, b), t1);
+    }
   // lane pairs (l, l ^ s): the lower lane keeps v + o, the upper one
   // (o - v) t; both as (o + sgn v) t' with t' = 1 on the lower lane
 #pragma unroll
@@ -127,19 +136,27 @@ __device__ __forceinline__ void warp_fft_dif(float2 (&v)[4], const TwTab& T, int
     const int s = 64 >> st;
     const float sgn = (lane & s) ? -1.f : 1.f;
     const float2 t = T.sh[st - 2][lane];
+    float2 o[J][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float2 o;
-      o.x = __shfl_xor_sync(0xffffffffu, v[q].x, s);
-      o.y = __shfl_xor_sync(0xffffffffu, v[q].y, s);
-      v[q] = cmul(make_float2(fmaf(sgn, v[q].x, o.x), fmaf(sgn, v[q].y, o.y)), t);
-    }
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        o[j][q].x = __shfl_xor_sync(0xffffffffu, v[j][q].x, s);
+        o[j][q].y = __shfl_xor_sync(0xffffffffu, v[j][q].y, s);
+      }
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        v[j][q] = cmul(make_float2(fmaf(sgn, v[j][q].x, o[j][q].x), fmaf(sgn, v[j][q].y, o[j][q].y)),
+                       t);
   }
 }
 
 // Inverse (conjugate twiddles), decimation in time: bit-reversed in,
 // natural out, unscaled. Stage st (span 1 << st) uses sh[4 - st].
-__device__ __forceinline__ void warp_ifft_dit(float2 (&v)[4], const TwTab& T, int lane) {
+template <int J>
+__device__ __forceinline__ void warp_ifft_dit(float2 (&v)[J][4], const TwTab& T, int lane) {
   // lane pairs (l, l ^ s): the upper lane's value is first multiplied by
   // the twiddle (t' = 1 on the lower lane); then lower: w + o, upper: o - w
 #pragma unroll
@@ -147,27 +164,39 @@ __device__ __forceinline__ void warp_ifft_dit(float2 (&v)[4], const TwTab& T, in
     const int s = 1 << st;
     const float sgn = (lane & s) ? -1.f : 1.f;
     const float2 t = conjf2(T.sh[4 - st][lane]);
+    float2 w[J][4], o[J][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float2 w = cmul(v[q], t);
-      float2 o;
-      o.x = __shfl_xor_sync(0xffffffffu, w.x, s);
-      o.y = __shfl_xor_sync(0xffffffffu, w.y, s);
-      v[q] = make_float2(fmaf(sgn, w.x, o.x), fmaf(sgn, w.y, o.y));
-    }
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        w[j][q] = cmul(v[j][q], t);
+        o[j][q].x = __shfl_xor_sync(0xffffffffu, w[j][q].x, s);
+        o[j][q].y = __shfl_xor_sync(0xffffffffu, w[j][q].y, s);
+      }
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        v[j][q] = make_float2(fmaf(sgn, w[j][q].x, o[j][q].x), fmaf(sgn, w[j][q].y, o[j][q].y));
   }
   const float2 t1 = conjf2(T.lane2[lane]);
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    const float2 a = v[2 * p], b = cmul(v[2 * p + 1], t1);
-    v[2 * p] = cadd(a, b);
-    v[2 * p + 1] = csub(a, b);
-  }
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const float2 a = v[j][2 * p], b = cmul(v[j][2 * p + 1], t1);
+      v[j][2 * p] = cadd(a, b);
+      v[j][2 * p + 1] = csub(a, b);
+    }
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    const float2 a = v[q], b = cmul(v[q + 2], conjf2(T.w[32 * q + lane]));
-    v[q] = cadd(a, b);
-    v[q + 2] = csub(a, b);
+    const float2 t = conjf2(T.w[32 * q + lane]);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const float2 a = v[j][q], b = cmul(v[j][q + 2], t);
+      v[j][q] = cadd(a, b);
+      v[j][q + 2] = csub(a, b);
+    }
   }
 }
 
@@ -234,36 +263,89 @@ __device__ __forceinline__ void load_spec_cols(SpecRegs& kr, const float2* kt) {
   }
 }
 
-// forward 2D transform, rows: 64 packed row FFTs and the split
+// forward 2D transform, rows: 64 packed row FFTs and the split, two rows per
+// warp at a time (each warp owns row pairs warp + 16 i)
 __device__ void r2c_rows(float2* buf, const TwTab& T) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = warp; k < 64; k += kWarps) {
-    float2* r = buf + 2 * k * kFP;
-    float2 v[4];
+  for (int k = warp; k < 64; k += 2 * kWarps) {
+    float2* r[2] = {buf + 2 * k * kFP, buf + 2 * (k + kWarps) * kFP};
+    float2 v[2][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = r[32 * q + lane];
-    warp_fft_dif(v, T, lane);
+    for (int j = 0; j < 2; ++j)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) r[swz(32 * q + lane)] = v[q];
+      for (int q = 0; q < 4; ++q) v[j][q] = r[j][32 * q + lane];
+    warp_fft_dif<2>(v, T, lane);
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) r[j][swz(32 * q + lane)] = v[j][q];
     __syncwarp();
-    split_pair(r, lane);
+    split_pair(r[0], lane);
+    split_pair(r[1], lane);
   }
   __syncthreads();
 }
 
+// J column FFTs (columns m[0..J)) of buf in place
+template <int J, bool INVERSE>
+__device__ __forceinline__ void columns_inplace(float2* buf, const int (&m)[J], const TwTab& T,
+                                                int lane) {
+  float2 v[J][4];
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[j][q] = buf[(32 * q + lane) * kFP + m[j]];
+  if (INVERSE)
+    warp_ifft_dit<J>(v, T, lane);
+  else
+    warp_fft_dif<J>(v, T, lane);
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) buf[(32 * q + lane) * kFP + m[j]] = v[j][q];
+}
+
+// the 65 column FFTs: warp w owns columns w + 16 c (c < 4) two at a time,
+// and warp 0 also column 64
+template <bool INVERSE>
+__device__ __forceinline__ void all_columns(float2* buf, const TwTab& T) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll 1
+  for (int c = 0; c < 4; c += 2) {
+    const int m[2] = {warp + kWarps * c, warp + kWarps * (c + 1)};
+    columns_inplace<2, INVERSE>(buf, m, T, lane);
+  }
+  if (warp == 0) {
+    const int m[1] = {64};
+    columns_inplace<1, INVERSE>(buf, m, T, lane);
+  }
+}
+
 // forward real 2D transform in place (see the file comment)
 __device__ void r2c_2d(float2* buf, const TwTab& T) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   r2c_rows(buf, T);
-  for (int m = warp; m < kFBins; m += kWarps) {
-    float2 v[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = buf[(32 * q + lane) * kFP + m];
-    warp_fft_dif(v, T, lane);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) buf[(32 * q + lane) * kFP + m] = v[q];
-  }
+  all_columns<false>(buf, T);
   __syncthreads();
+}
+
+// columns c0 .. c0+J-1 of this warp (m = warp + 16 c): acc += FFT(buf) conj(k^)
+template <int J>
+__device__ __forceinline__ void columns_accumulate(const float2* buf, float2* acc,
+                                                   const SpecRegs& kr, int c0, const TwTab& T,
+                                                   int warp, int lane) {
+  float2 v[J][4];
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[j][q] = buf[(32 * q + lane) * kFP + warp + kWarps * (c0 + j)];
+  warp_fft_dif<J>(v, T, lane);
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float2* o = acc + (32 * q + lane) * kFP + warp + kWarps * (c0 + j);
+      *o = cadd(*o, cmulc(v[j][q], kr[c0 + j][q]));
+    }
 }
 
 // forward transform of buf (destroyed) added, times conj(spectrum), into acc:
@@ -271,72 +353,80 @@ __device__ void r2c_2d(float2* buf, const TwTab& T) {
 __device__ void r2c_2d_accumulate(float2* buf, float2* acc, const SpecRegs& kr, const TwTab& T) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   r2c_rows(buf, T);
-#pragma unroll
-  for (int c = 0; c < kColsPerWarp; ++c) {
-    const int m = warp + kWarps * c;
-    if (m < kFBins) {
-      float2 v[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = buf[(32 * q + lane) * kFP + m];
-      warp_fft_dif(v, T, lane);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float2* o = acc + (32 * q + lane) * kFP + m;
-        *o = cadd(*o, cmulc(v[q], kr[c][q]));
-      }
-    }
-  }
+  columns_accumulate<2>(buf, acc, kr, 0, T, warp, lane);
+  columns_accumulate<2>(buf, acc, kr, 2, T, warp, lane);
+  if (warp == 0) columns_accumulate<1>(buf, acc, kr, 4, T, warp, lane);
   __syncthreads();
 }
 
+// merge, inverse row FFTs of the J row pairs k[0..J)
+template <int J>
+__device__ __forceinline__ void rows_inverse(float2* buf, const int (&k)[J], const TwTab& T,
+                                             int lane) {
+  float2 v[J][4];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    float2* r = buf + 2 * k[j] * kFP;
+    merge_pair(r, lane);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[j][q] = r[swz(32 * q + lane)];
+  }
+  warp_ifft_dit<J>(v, T, lane);
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) buf[2 * k[j] * kFP + 32 * q + lane] = v[j][q];
+}
+
 // inverse transform, rows: merge and the packed row inverse FFTs of the row
-// pairs [k0, k1) (the rows a caller reads; the others are left undone)
+// pairs [k0, k1) (the rows a caller reads; the others are left undone), two
+// at a time per warp
 __device__ void c2r_rows(float2* buf, const TwTab& T, int k0 = 0, int k1 = 64) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = k0 + warp; k < k1; k += kWarps) {
-    float2* r = buf + 2 * k * kFP;
-    merge_pair(r, lane);
-    float2 v[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = r[swz(32 * q + lane)];
-    warp_ifft_dit(v, T, lane);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) r[32 * q + lane] = v[q];
+  for (int k = k0 + warp; k < k1; k += 2 * kWarps) {
+    if (k + kWarps < k1) {
+      const int kk[2] = {k, k + kWarps};
+      rows_inverse<2>(buf, kk, T, lane);
+    } else {
+      const int kk[1] = {k};
+      rows_inverse<1>(buf, kk, T, lane);
+    }
   }
   __syncthreads();
 }
 
 // inverse real 2D transform in place (unscaled); rows of the pairs [k0, k1)
 __device__ void c2r_2d(float2* buf, const TwTab& T, int k0 = 0, int k1 = 64) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int m = warp; m < kFBins; m += kWarps) {
-    float2 v[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = buf[(32 * q + lane) * kFP + m];
-    warp_ifft_dit(v, T, lane);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) buf[(32 * q + lane) * kFP + m] = v[q];
-  }
+  all_columns<true>(buf, T);
   __syncthreads();
   c2r_rows(buf, T, k0, k1);
+}
+
+// columns c0 .. c0+J-1 of this warp: dst = IFFT(src . k^) along the column
+template <int J>
+__device__ __forceinline__ void columns_product(const float2* src, float2* dst,
+                                                const SpecRegs& kr, int c0, const TwTab& T,
+                                                int warp, int lane) {
+  float2 v[J][4];
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      v[j][q] = cmul(src[(32 * q + lane) * kFP + warp + kWarps * (c0 + j)], kr[c0 + j][q]);
+  warp_ifft_dit<J>(v, T, lane);
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[(32 * q + lane) * kFP + warp + kWarps * (c0 + j)] = v[j][q];
 }
 
 // dst = C2R(src . k^) (unscaled), rows of the pairs [k0, 64); src is left intact
 __device__ void c2r_2d_product(const float2* src, float2* dst, const SpecRegs& kr,
                                const TwTab& T, int k0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int c = 0; c < kColsPerWarp; ++c) {
-    const int m = warp + kWarps * c;
-    if (m < kFBins) {
-      float2 v[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = cmul(src[(32 * q + lane) * kFP + m], kr[c][q]);
-      warp_ifft_dit(v, T, lane);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) dst[(32 * q + lane) * kFP + m] = v[q];
-    }
-  }
+  columns_product<2>(src, dst, kr, 0, T, warp, lane);
+  columns_product<2>(src, dst, kr, 2, T, warp, lane);
+  if (warp == 0) columns_product<1>(src, dst, kr, 4, T, warp, lane);
   __syncthreads();
   c2r_rows(dst, T, k0, 64);
 }
@@ -413,19 +503,19 @@ __device__ void c2r_2d_phase_sum(const float2* xs, const float2* kt, int R2, flo
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per = kFT * kFBins;
   for (int m = warp; m < kFBins; m += kWarps) {
-    float2 v[4];
+    float2 v[1][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = make_float2(0.f, 0.f);
+    for (int q = 0; q < 4; ++q) v[0][q] = make_float2(0.f, 0.f);
     for (int ph = 0; ph < R2; ++ph) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int o = ph * per + m * kFT + 32 * q + lane;
-        v[q] = cadd(v[q], cmul(xs[o], kt[o]));
+        v[0][q] = cadd(v[0][q], cmul(xs[o], kt[o]));
       }
     }
-    warp_ifft_dit(v, T, lane);
+    warp_ifft_dit<1>(v, T, lane);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) dst[(32 * q + lane) * kFP + m] = v[q];
+    for (int q = 0; q < 4; ++q) dst[(32 * q + lane) * kFP + m] = v[0][q];
   }
   __syncthreads();
   c2r_rows(dst, T, k0, 64);
@@ -527,15 +617,15 @@ __device__ void r2c_2d_accumulate_phases(float2* buf, float2* acc, const float2*
   const int per = kFT * kFBins;
   r2c_rows(buf, T);
   for (int m = warp; m < kFBins; m += kWarps) {
-    float2 v[4];
+    float2 v[1][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = buf[(32 * q + lane) * kFP + m];
-    warp_fft_dif(v, T, lane);
+    for (int q = 0; q < 4; ++q) v[0][q] = buf[(32 * q + lane) * kFP + m];
+    warp_fft_dif<1>(v, T, lane);
     for (int ph = 0; ph < R2; ++ph) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int o = ph * per + m * kFT + 32 * q + lane;
-        acc[o] = cadd(acc[o], cmulc(v[q], kt[o]));
+        acc[o] = cadd(acc[o], cmulc(v[0][q], kt[o]));
       }
     }
   }
