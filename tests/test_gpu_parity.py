@@ -320,20 +320,21 @@ def test_contexts_order_against_a_busy_legacy_stream(emd):
 
 def test_parity_fifty_iterations_k43_with_ring_reuse(emd):
     """50 iterations of the FP32 halo-exchange kernel with 43 x 43 PSFs on
-    512^2 x 33 exposures: 33 x 32 = 1056 forward items of 64 x 128 tiles
-    against a ring of 971 slots, so slots are reused within every launch
-    (the regime of the full-size workload). Spec bars: 1e-5 after one
-    iteration, 1e-4 after 50."""
+    512^2 x 33 exposures, on 64 x 128 tiles: 33 x 32 = 1056 forward items
+    against a ring of R = L + dmax + 1 + 320 = 971 slots (dmax = 4 + 1 tile
+    ids, L = dmax + 640), so slots are reused within every launch (the regime
+    of the full-size workload). Spec bars: 1e-5 after one iteration,
+    1e-4 after 50."""
     p = make("hsc", H=512, W=512, seed_offset=7)
     assert p.n == 33 and p.K == 43
-    ring = (emd.emd_ctx_bytes_precision(512, 512, 33, 43, 1, emd.EMD_PREC_FP32)
-            - emd.emd_ctx_bytes(512, 512, 33, 43, 1))
-    assert ring < 33 * 32 * 64 * 128 * 4                # fewer slots than forward items
+    dmax = 512 // 128 + 1
+    assert (dmax + 640) + dmax + 1 + 320 < 33 * (512 // 64) * (512 // 128)
     x0 = start(p, seed=3)
     u, y, N, _ = oracle.prepare(p)
     d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
     try:
         d.set_frames(p.y, p.v, p.f, p.mask)
+        d.set_tile_rows(64)
         d.set_x(x0)
         d.iterate(1)
         x1 = d.x()
