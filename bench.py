@@ -50,6 +50,9 @@ KERNEL_SOURCES = {
     "fused": ["paper_2302_05804_gb300/csrc/emd_direct.cu",
               "paper_2302_05804_gb300/csrc/emd_corr.cuh",
               "paper_2302_05804_gb300/csrc/emd_internal.cuh"],
+    "fft": ["paper_2302_05804_gb300/csrc/emd_fft.cu",
+            "paper_2302_05804_gb300/csrc/emd_fft.cuh",
+            "paper_2302_05804_gb300/csrc/emd_internal.cuh"],
 }
 
 
@@ -117,6 +120,62 @@ def tc_executed_flops(H, W, n, K, r, nprod):
     return tiles * n * r * r * per
 
 
+def fft_flops(H, W, n, K, r, nu):
+    """flops one FFT-form iteration runs: 128^2 real transforms (2.5 N log2 N
+    each, N = 128^2) on overlap-save tiles of 128 - 2 hc outputs, and the
+    spectrum products. Forward: R2 + n transforms per tile; adjoint: n + R2,
+    or 2 n + 2 R2 with the heavy-tailed numerator planes."""
+    hc = ((K - 1) // 2 + r - 1) // r
+    B = 128 - 2 * hc
+    tiles = -(-H // B) * -(-W // B)
+    m = 2 if nu > 0 else 1
+    ffts = tiles * ((1 + m) * (n + r * r))
+    return ffts * 2.5 * 16384 * 14 + tiles * (1 + m) * n * r * r * 6 * 128 * 65
+
+
+def bf16_peak():
+    """(TFLOP/s, description) of the measured dense BF16 peak (burst)."""
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(mp["bf16_tflops"]), "measured bf16_tflops (burst), of measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback 1.9 PFLOP/s bf16 burst"
+
+
+def variant_roofline(name, p, launch_s, peak32, peak32_src):
+    """Roofline record of one timed variant (same conventions as the
+    headline's): FMA pipe for the direct forms, FP32 issue for the FFT form,
+    the tensor pipe (executed flops) for the tensor-core forms."""
+    flops = algorithmic_flops(p.H, p.W, p.n, p.K, p.r)
+    nu = 3.0 if name.startswith("student") else 0.0
+    if name.startswith("student"):
+        flops *= 1.5
+    if "fft" in name:
+        fl = fft_flops(p.H, p.W, p.n, p.K, p.r, nu)
+        ex = fl / launch_s / 1e12
+        rec = {"bound": "alu", "achieved": ex, "peak": peak32, "unit": "TFLOP/s",
+               "frac": ex / peak32, "peak_source": peak32_src,
+               "kernel": "fft_forward_kernel + fft_adjoint_kernel",
+               "fft_tflop_per_iteration": fl / 1e12,
+               "direct_equivalent_tflops": flops / launch_s / 1e12}
+        tr = committed_traffic("fft", "hsc") if nu == 0 else None
+        if tr:
+            rec["traffic"] = tr
+            rec["hbm_gbs"] = tr / launch_s / 1e9
+        return rec
+    if name in ("split_bf16", "bf16"):
+        nprod = 3 if name.startswith("split") else 1
+        ex = tc_executed_flops(p.H, p.W, p.n, p.K, p.r, nprod) / launch_s / 1e12
+        pk, src = bf16_peak()
+        return {"bound": "tensor", "achieved": ex, "peak": pk, "unit": "TFLOP/s",
+                "frac": ex / pk, "peak_source": src, "kernel": "tc_iter_kernel",
+                "useful_tflops": flops / launch_s / 1e12}
+    ach = flops / launch_s / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
+            "frac": ach / peak32, "peak_source": peak32_src,
+            "kernel": "fused_kernel" if name == "fp32_pair" else "halo_kernel"}
+
+
 def kernel_source_hash(kernel):
     h = hashlib.sha256()
     for p in KERNEL_SOURCES[kernel]:
@@ -126,8 +185,10 @@ def kernel_source_hash(kernel):
 
 
 def committed_traffic(kernel, workload):
-    """DRAM bytes per launch of a direct-form kernel ("halo" or "fused") from
-    the committed ncu summary, or None when its source changed since."""
+    """DRAM bytes per iteration of a kernel ("halo", "fused"; "fft": its
+    forward and adjoint launches together) from the committed ncu summary
+    profiles/<kernel>_<workload>_traffic.json, or None when the kernel's
+    source changed since it was taken."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}_traffic.json")
     if not os.path.exists(path):
         return None
@@ -313,9 +374,10 @@ def run_serving(p, args, precision=0, jobs=2000):
                         "64 slots"}
 
 
-def run_variants(p, steps=5, warmup=2):
+def run_variants(p, peak32, peak32_src, steps=5, warmup=2):
     """The other built forms of the iteration on the same frame set, each in
-    its own context: CUDA events per iteration on the context's stream."""
+    its own context: CUDA events per iteration on the context's stream, and a
+    roofline record for each."""
     import torch
     from paper_2302_05804_gb300 import emd
     forms = [("fp32_pair", emd.EMD_PREC_FP32_PAIR, 0.0),
@@ -343,7 +405,8 @@ def run_variants(p, steps=5, warmup=2):
         finally:
             d.close()
         out[name] = {"ms_per_iteration": ms,
-                     "value": p.r * p.r * p.H * p.W * p.n / (ms / 1e3) / 1e9, "unit": UNIT}
+                     "value": p.r * p.r * p.H * p.W * p.n / (ms / 1e3) / 1e9, "unit": UNIT,
+                     "roofline": variant_roofline(name, p, ms / 1e3, peak32, peak32_src)}
     return out
 
 
@@ -477,17 +540,11 @@ def run_ours(args):
         # = 2.5 N log2 N, N = 128^2) and of the spectrum products, against
         # the FP32 peak; the direct-form flops it replaces are reported beside
         peak = peak32
-        hc = ((p.K - 1) // 2 + p.r - 1) // p.r
-        B = 128 - 2 * hc
-        tiles = -(-p.H // B) * -(-p.W // B)
-        # forward: R2 + n transforms; adjoint: n + R2, or 2n + 2 R2 with the
-        # heavy-tailed numerator planes
-        m = 2 if args.nu > 0 else 1
-        ffts = tiles * ((1 + m) * (p.n + p.r * p.r))
-        fl = ffts * 2.5 * 16384 * 14 + tiles * (1 + m) * p.n * p.r * p.r * 6 * 128 * 65
+        fl = fft_flops(p.H, p.W, p.n, p.K, p.r, args.nu)
         ex = fl / launch_s / 1e12
+        traffic = committed_traffic("fft", args.workload) if args.nu == 0 else None
         roofline = {"bound": "alu", "achieved": ex, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ex / peak, "traffic": None,
+                    "frac": ex / peak, "traffic": traffic,
                     "kernel": "fft_forward_kernel + fft_adjoint_kernel (FP32 FFT)",
                     "peak_source": peak32_src,
                     "direct_equivalent_tflops": achieved,
@@ -524,12 +581,7 @@ def run_ours(args):
     else:
         nprod = 3 if args.precision.startswith("split") else 1
         ex = tc_executed_flops(p.H, p.W, p.n, p.K, p.r, nprod) / launch_s / 1e12
-        peak, src = 1900.0, "fallback 1.9 PFLOP/s bf16 burst"
-        try:
-            mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-            peak, src = float(mp["bf16_tflops"]), "measured bf16_tflops (burst), of measured"
-        except (OSError, KeyError, ValueError):
-            pass
+        peak, src = bf16_peak()
         roofline = {"bound": "tensor", "achieved": ex, "peak": peak, "unit": "TFLOP/s",
                     "frac": ex / peak, "traffic": None, "kernel": "tc_iter_kernel (tcgen05)",
                     "useful_tflops": achieved, "peak_source": src}
@@ -589,7 +641,7 @@ def run_ours(args):
         psf_fit = run_psf_fit(p, args.psf_iters)
     variants = None
     if args.variants and prec == 0 and args.nu == 0:
-        variants = run_variants(p)
+        variants = run_variants(p, peak32, peak32_src)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
