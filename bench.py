@@ -561,8 +561,10 @@ def run_ours(args):
                               (" heavy-tailed instance" if args.nu > 0 else ""),
                     "peak_source": peak32_src}
         if prec == 0:
+            how = ("fixed by --tile-rows" if args.tile_rows else
+                   "autotuned" if tile_rows[1] else "autotuner undecided")
             roofline["tile"] = (f"{tile_rows[0]} x 128 tiles, {tile_rows[0] // 16} x 16 outputs "
-                                f"per thread ({'autotuned' if tile_rows[1] else 'undecided'})")
+                                f"per thread ({how})")
         if traffic:
             hbm_peak, hsrc = 6800.0, "fallback 6.8 TB/s"
             try:
