@@ -36,6 +36,11 @@ sys.path.insert(0, ROOT)
 METRIC = "EM Gpix·exposure-iters/s"
 UNIT = "Gpix·exposure-iters/s"
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (Blackwell)
+# tile shapes of the FP32 halo-exchange kernel (emd_tile_shape values)
+TILE_SHAPES = {"64": 1, "48": 2, "32": 3}
+TILE_NAMES = {1: "64 x 128 tiles, 4 x 16 outputs per thread",
+              2: "48 x 128 tiles, 3 x 16 outputs per thread",
+              3: "32 x 128 tiles, 2 x 16 outputs per thread"}
 # kernels one emd_iterate(ctx, 1) call launches: the fused kernel (FP32); the
 # x split + tensor-core kernel (BF16 modes); the x maximum, the power-of-two
 # scales, the split and the tensor-core kernel (FP16 modes)
@@ -491,8 +496,8 @@ def run_ours(args):
         d.set_precision(prec)
     if args.nu > 0:
         d.set_noise(emd.EMD_NOISE_STUDENT_T, args.nu)
-    if args.tile_rows:
-        d.set_tile_rows(args.tile_rows)
+    if args.tile_shape:
+        d.set_tile_shape(TILE_SHAPES[args.tile_shape])
 
     def barrier():
         if world > 1:
@@ -505,11 +510,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     if prec == 0:
         for _ in range(16):
-            if d.tile_rows()[1]:
+            if d.tile_shape()[1]:
                 break
             d.iterate(1)
             torch.cuda.synchronize()
-    tile_rows = d.tile_rows() if prec == 0 else None
+    tile = d.tile_shape() if prec == 0 else None
 
     # timed region: K steps, one fused-kernel launch each, events per step
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -561,10 +566,9 @@ def run_ours(args):
                               (" heavy-tailed instance" if args.nu > 0 else ""),
                     "peak_source": peak32_src}
         if prec == 0:
-            how = ("fixed by --tile-rows" if args.tile_rows else
-                   "autotuned" if tile_rows[1] else "autotuner undecided")
-            roofline["tile"] = (f"{tile_rows[0]} x 128 tiles, {tile_rows[0] // 16} x 16 outputs "
-                                f"per thread ({how})")
+            how = ("fixed by --tile-shape" if args.tile_shape else
+                   "autotuned" if tile[1] else "autotuner undecided")
+            roofline["tile"] = f"{TILE_NAMES[tile[0]]} ({how})"
         if traffic:
             hbm_peak, hsrc = 6800.0, "fallback 6.8 TB/s"
             try:
@@ -700,8 +704,8 @@ def main():
                          "(0: Gaussian, Eq. (1))")
     ap.add_argument("--psf-iters", type=int, default=20000,
                     help="Adam iterations of the Eq. (4) PSF fit sample (0 disables it)")
-    ap.add_argument("--tile-rows", type=int, default=0, choices=[0, 64, 48, 32],
-                    help="tile rows of the FP32 halo-exchange kernel (0: autotuned)")
+    ap.add_argument("--tile-shape", default="", choices=[""] + list(TILE_SHAPES),
+                    help="tile shape of the FP32 halo-exchange kernel (default: autotuned)")
     ap.add_argument("--cpu-crop", type=int, default=512)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-crop", type=int, default=256)

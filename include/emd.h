@@ -203,22 +203,30 @@ enum emd_noise {
 };
 int emd_set_noise(emd_ctx *ctx, int model, double nu);
 
-/* Tile shape of the FP32 halo-exchange iteration (EMD_PREC_FP32): the
- * kernel works on tiles of `rows` x 128 pixels, each of its 128 threads
- * computing a (rows/16) x 16 block of outputs. rows = 64 (two CTAs per SM),
- * 48 (three CTAs per SM, at most 168 registers a thread) or 32 (four CTAs
- * per SM where the shared memory allows); 0 (the default) lets the
- * autotuner choose: the first iterations of a problem shape (H, W, n, K, r,
- * noise model) not seen before in this process run each candidate shape
- * twice, timed with CUDA events on the context's stream and read without
- * blocking at later calls, and the fastest is kept for every context of
- * that shape. All shapes give the same iterates bit for bit. EMD_EINVAL for
- * another value. */
-int emd_set_tile_rows(emd_ctx *ctx, int rows);
-/* The tile rows the next FP32 iteration uses, and *decided = 1 once the
- * autotuner has decided (or the rows were fixed); either pointer may be
- * NULL. */
-int emd_get_tile_rows(emd_ctx *ctx, int *rows, int *decided);
+/* Tile shape of the FP32 halo-exchange iteration (EMD_PREC_FP32). Its 128
+ * threads compute a tile of rows x 128 pixels, each thread a (rows/16) x 16
+ * block of outputs:
+ *   EMD_TILE_64         64 rows, two CTAs per SM
+ *   EMD_TILE_48         48 rows, three CTAs per SM (at most 168 registers)
+ *   EMD_TILE_32         32 rows, four CTAs per SM where the shared memory allows
+ * EMD_TILE_AUTO (the default) lets the autotuner choose: the first
+ * iterations of a problem shape (H, W, n, K, r, noise model) not seen before
+ * in this process run each candidate twice, timed with CUDA events on the
+ * context's stream and read without blocking at later calls, and the
+ * fastest is kept for every context of that problem shape. All tile shapes
+ * give the same iterates bit for bit (every output sums its taps in the same
+ * order). EMD_EINVAL for another value. */
+enum emd_tile_shape {
+    EMD_TILE_AUTO = 0,
+    EMD_TILE_64 = 1,
+    EMD_TILE_48 = 2,
+    EMD_TILE_32 = 3
+};
+int emd_set_tile_shape(emd_ctx *ctx, int shape);
+/* The tile shape the next FP32 iteration uses (an emd_tile_shape other than
+ * EMD_TILE_AUTO), and *decided = 1 once the autotuner has decided (or the
+ * shape was fixed); either pointer may be NULL. */
+int emd_get_tile_shape(emd_ctx *ctx, int *shape, int *decided);
 
 /* Self-test of failure detection: launches, on ctx's stream, one CTA that
  * waits on an mbarrier nothing ever arrives on, with the same bounded-wait
@@ -290,9 +298,9 @@ int emd_batch_sync(emd_batch *b);
  * job-major, or round-robin over jobs in the halo-exchange form; 1 = most
  * expensive jobs first), the maximum pairs, the FP32 jobs' form (0 =
  * halo-exchange kernel, 1 = CTA-pair kernel) and the halo-exchange kernel's
- * tile rows (64 or 48; see emd_set_tile_rows). Any pointer may be NULL. */
+ * tile shape (an emd_tile_shape). Any pointer may be NULL. */
 int emd_batch_config(emd_batch *b, int *clusters, int *order, int *max_clusters, int *form,
-                     int *tile_rows);
+                     int *tile_shape);
 
 /*
  * emd_frame_stats_noalloc -- per-exposure FP64 frame statistics without any

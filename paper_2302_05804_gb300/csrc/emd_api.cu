@@ -127,7 +127,7 @@ struct emd_ctx {
   size_t halo_bytes = 0;
   bool halo_student = false;  // slots hold two tiles (heavy-tailed weights)
   emd::HaloLaunch halo{};
-  // its tile shape: fixed by emd_set_tile_rows (-1: autotuned), and the
+  // its tile shape: fixed by emd_set_tile_shape (-1: autotuned), and the
   // autotuner's trials on this context (candidates in launch order, events
   // around each launch)
   int tile_forced = -1;
@@ -939,22 +939,17 @@ int emd_iterate_streaming(emd_ctx* c, int k, const int* order) {
   return EMD_OK;
 }
 
-int emd_set_tile_rows(emd_ctx* c, int rows) {
+int emd_set_tile_shape(emd_ctx* c, int shape) {
   if (int rc = check_ctx(c, false)) return rc;
-  if (rows == 0) {
-    c->tile_forced = -1;
-    return EMD_OK;
+  if (shape < EMD_TILE_AUTO || shape > emd::kHaloTileConfigs) {
+    set_err("emd_set_tile_shape: unknown tile shape %d", shape);
+    return EMD_EINVAL;
   }
-  for (int cfg = 0; cfg < emd::kHaloTileConfigs; ++cfg)
-    if (emd::halo_tile_rows(cfg) == rows) {
-      c->tile_forced = cfg;
-      return EMD_OK;
-    }
-  set_err("emd_set_tile_rows: rows must be 0 (autotuned), 64, 48 or 32");
-  return EMD_EINVAL;
+  c->tile_forced = shape - 1;  // -1: autotuned
+  return EMD_OK;
 }
 
-int emd_get_tile_rows(emd_ctx* c, int* rows, int* decided) {
+int emd_get_tile_shape(emd_ctx* c, int* shape, int* decided) {
   if (int rc = check_ctx(c, false)) return rc;
   DeviceGuard dg(c->device);
   tile_trials_poll(c);
@@ -969,7 +964,7 @@ int emd_get_tile_rows(emd_ctx* c, int* rows, int* decided) {
       dec = 0;
     }
   }
-  if (rows) *rows = emd::halo_tile_rows(cfg);
+  if (shape) *shape = cfg + 1;
   if (decided) *decided = dec;
   return EMD_OK;
 }
@@ -1586,13 +1581,13 @@ int emd_batch_sync(emd_batch* b) {
 }
 
 int emd_batch_config(emd_batch* b, int* clusters, int* order, int* max_clusters, int* form,
-                     int* tile_rows) {
+                     int* tile_shape) {
   if (int rc = batch_check(b)) return rc;
   if (clusters) *clusters = b->cur.clusters;
   if (order) *order = b->cur.order;
   if (max_clusters) *max_clusters = b->max_clusters;
   if (form) *form = b->cur.form;
-  if (tile_rows) *tile_rows = emd::halo_tile_rows(b->cur.tile);
+  if (tile_shape) *tile_shape = b->cur.tile + 1;
   return EMD_OK;
 }
 

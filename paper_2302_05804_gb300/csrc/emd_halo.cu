@@ -714,8 +714,6 @@ cudaError_t launch_flag_wait_selftest(uint32_t limit, void* scratch, int* err, c
   return cudaGetLastError();
 }
 
-int halo_tile_rows(int cfg) { return cfg >= 0 && cfg < kHaloTileConfigs ? cfg_rows(cfg) : 0; }
-
 HaloPlan halo_plan(const Shape& s, int ne, int cfg) {
   HaloPlan p;
   p.cfg = cfg;
@@ -762,9 +760,11 @@ HaloBufLayout halo_layout(const Shape& s, bool student) {
 }  // namespace
 
 size_t halo_buffer_bytes(const Shape& s, bool student) {
-  // 32-bit item ids: the shape with the most items decides
-  const HaloPlan p = halo_plan(s, s.n, kHaloTileConfigs - 1);
-  if (2 * p.NT + 2LL * cfg_ctas(kHaloTileConfigs - 1) >= (1LL << 31)) return 0;
+  // 32-bit item ids for every tile shape
+  for (int cfg = 0; cfg < kHaloTileConfigs; ++cfg) {
+    const HaloPlan p = halo_plan(s, s.n, cfg);
+    if (2 * p.NT + 2LL * cfg_ctas(cfg) >= (1LL << 31)) return 0;
+  }
   return halo_layout(s, student).total;
 }
 

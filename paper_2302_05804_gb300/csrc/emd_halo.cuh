@@ -13,7 +13,6 @@ namespace emd {
 //      permitting)
 // Every shape gives the same iterates bit for bit.
 constexpr int kHaloTileConfigs = 3;
-int halo_tile_rows(int cfg);  // 0 for an unknown shape
 // CTAs of the shape's (Gaussian) kernel resident per SM for this problem (0 on error)
 int halo_tile_ctas_per_sm(const Shape& s, int cfg);
 

@@ -34,6 +34,10 @@ EMD_PREC_FFT_FP32 = 5
 EMD_PREC_FP32_PAIR = 6
 EMD_NOISE_GAUSSIAN = 0
 EMD_NOISE_STUDENT_T = 1
+EMD_TILE_AUTO = 0
+EMD_TILE_64 = 1
+EMD_TILE_48 = 2
+EMD_TILE_32 = 3
 
 EXPORTS = [
     "emd_create", "emd_ctx_bytes", "emd_destroy", "emd_last_error", "emd_set_stream",
@@ -42,7 +46,7 @@ EXPORTS = [
     "emd_batch_create", "emd_batch_destroy", "emd_batch_add", "emd_batch_remove",
     "emd_batch_step", "emd_batch_remaining", "emd_batch_sync", "emd_batch_config",
     "emd_selftest_wait_timeout", "emd_iterate_streaming", "emd_fit_psf", "emd_set_noise",
-    "emd_measure_fma_rate", "emd_ctx_bytes_precision", "emd_set_tile_rows", "emd_get_tile_rows",
+    "emd_measure_fma_rate", "emd_ctx_bytes_precision", "emd_set_tile_shape", "emd_get_tile_shape",
 ]
 
 
@@ -112,10 +116,10 @@ def load(build_if_missing: bool = False):
         lib.emd_batch_remaining.argtypes = [vp, i]
         lib.emd_batch_sync.argtypes = [vp]
         lib.emd_batch_config.argtypes = [vp, ip, ip, ip, ip, ip]
-        lib.emd_set_tile_rows.argtypes = [vp, i]
-        lib.emd_set_tile_rows.restype = i
-        lib.emd_get_tile_rows.argtypes = [vp, ip, ip]
-        lib.emd_get_tile_rows.restype = i
+        lib.emd_set_tile_shape.argtypes = [vp, i]
+        lib.emd_set_tile_shape.restype = i
+        lib.emd_get_tile_shape.argtypes = [vp, ip, ip]
+        lib.emd_get_tile_shape.restype = i
         lib.emd_fit_psf.argtypes = [vp, i, i, i, vp, i, vp, C.c_float, C.c_float, i, vp, vp]
         lib.emd_fit_psf.restype = i
         lib.emd_set_noise.argtypes = [vp, i, C.c_double]
@@ -362,20 +366,20 @@ def emd_batch_config(b):
     _check(load().emd_batch_config(b, C.byref(c), C.byref(o), C.byref(m), C.byref(f),
                                    C.byref(t)))
     return {"clusters": c.value, "order": o.value, "max_clusters": m.value, "form": f.value,
-            "tile_rows": t.value}
+            "tile_shape": t.value}
 
 
-def emd_set_tile_rows(ctx, rows: int) -> None:
-    """Tile rows of the FP32 halo-exchange iteration: 64, 48, 32, or 0 for
-    the autotuner's choice."""
-    _check(load().emd_set_tile_rows(ctx, int(rows)))
+def emd_set_tile_shape(ctx, shape: int) -> None:
+    """Tile shape of the FP32 halo-exchange iteration: an EMD_TILE_* value
+    (EMD_TILE_AUTO: the autotuner's choice)."""
+    _check(load().emd_set_tile_shape(ctx, int(shape)))
 
 
-def emd_get_tile_rows(ctx):
-    """(rows, decided): the tile rows the next FP32 iteration uses."""
-    r, d = C.c_int(), C.c_int()
-    _check(load().emd_get_tile_rows(ctx, C.byref(r), C.byref(d)))
-    return r.value, bool(d.value)
+def emd_get_tile_shape(ctx):
+    """(shape, decided): the tile shape the next FP32 iteration uses."""
+    sh, d = C.c_int(), C.c_int()
+    _check(load().emd_get_tile_shape(ctx, C.byref(sh), C.byref(d)))
+    return sh.value, bool(d.value)
 
 
 # -- convenience wrapper --------------------------------------------------------
@@ -419,11 +423,11 @@ class Deconvolver:
     def set_noise(self, model, nu=0.0):
         emd_set_noise(self.ctx, model, nu)
 
-    def set_tile_rows(self, rows):
-        emd_set_tile_rows(self.ctx, rows)
+    def set_tile_shape(self, shape):
+        emd_set_tile_shape(self.ctx, shape)
 
-    def tile_rows(self):
-        return emd_get_tile_rows(self.ctx)
+    def tile_shape(self):
+        return emd_get_tile_shape(self.ctx)
 
     def x(self, out=None):
         if out is None:

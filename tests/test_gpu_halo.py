@@ -200,38 +200,39 @@ TILE_CASES = [(300, 257, 5, 43, 1, 0.0), (1024, 1024, 12, 43, 1, 0.0), (200, 330
 @pytest.mark.parametrize("H,W,n,K,r,nu", TILE_CASES)
 def test_tile_shapes_give_bit_identical_iterates(emd, H, W, n, K, r, nu):
     """Every output's taps are summed in the same order whatever block of
-    the tile it falls in, so the three tile shapes give the same iterates bit
-    for bit (ragged last rows of tiles, ring reuse at 1024^2 x 12, r = 2,
-    heavy-tailed noise), and they match the oracle."""
+    the tile it falls in, so all tile shapes give the same iterates bit for bit (ragged
+    last rows of tiles, ring reuse at 1024^2 x 12, r = 2, heavy-tailed
+    noise), and they match the oracle."""
     p = synth.make_problem("hsc", H=H, W=W, n=n, K=K, r=r, mask_frac=0.05,
                            fwhm=(2.0 * r, 5.0 * r), n_points=60, n_gal=4, seed_offset=H + K)
     x0 = start(p, seed=n)
     out = {}
-    for rows in (64, 48, 32):
+    shapes = (emd.EMD_TILE_64, emd.EMD_TILE_48, emd.EMD_TILE_32)
+    for shape in shapes:
         d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
         try:
             d.set_frames(p.y, p.v, p.f, p.mask)
             if nu > 0:
                 d.set_noise(emd.EMD_NOISE_STUDENT_T, nu)
-            d.set_tile_rows(rows)
-            assert d.tile_rows() == (rows, True)
+            d.set_tile_shape(shape)
+            assert d.tile_shape() == (shape, True)
             d.set_x(x0)
             d.iterate(3)
-            out[rows] = d.x()
+            out[shape] = d.x()
         finally:
             d.close()
-    np.testing.assert_array_equal(out[48], out[64])
-    np.testing.assert_array_equal(out[32], out[64])
+    for shape in shapes[1:]:
+        np.testing.assert_array_equal(out[shape], out[emd.EMD_TILE_64])
     if nu == 0:
         u, y, N, _ = oracle.prepare(p)
         xo = oracle.em_run(x0, N, u, p.f, 3, p.r)
-        assert np.linalg.norm(out[64] - xo) / np.linalg.norm(xo) <= 2e-5
+        assert np.linalg.norm(out[emd.EMD_TILE_64] - xo) / np.linalg.norm(xo) <= 2e-5
 
 
 def test_autotuner_decides_a_tile_shape(emd):
-    """With rows 0 (the default) the first iterations of a new problem shape
-    time the candidate shapes; the decision is kept for the shape and the
-    iterates equal those of a fixed shape."""
+    """With EMD_TILE_AUTO (the default) the first iterations of a new problem
+    shape time the candidate tile shapes; the decision is kept for the
+    problem shape and the iterates equal those of a fixed shape."""
     p = synth.make_problem("hsc", H=640, W=512, n=6, K=43, mask_frac=0.05, n_points=80,
                            n_gal=4, seed_offset=5)
     x0 = start(p, seed=2)
@@ -239,14 +240,14 @@ def test_autotuner_decides_a_tile_shape(emd):
     d.set_frames(p.y, p.v, p.f, p.mask)
     d.set_x(x0)
     done = 0
-    while done < 12:
+    while done < 16:
         d.iterate(1)
         done += 1
         emd.emd_get_x(d.ctx, np.empty((p.H, p.W), np.float32))   # synchronises
-        if d.tile_rows()[1]:
+        if d.tile_shape()[1]:
             break
-    rows, decided = d.tile_rows()
-    assert decided and rows in (64, 48, 32)
+    shape, decided = d.tile_shape()
+    assert decided and shape in (1, 2, 3)
     d.iterate(1)   # one iteration on the decided shape
     done += 1
     xt = d.x()
@@ -254,7 +255,7 @@ def test_autotuner_decides_a_tile_shape(emd):
     # the same number of iterations on a fixed shape
     e = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
     e.set_frames(p.y, p.v, p.f, p.mask)
-    e.set_tile_rows(64)
+    e.set_tile_shape(emd.EMD_TILE_64)
     e.set_x(x0)
     e.iterate(done)
     np.testing.assert_array_equal(xt, e.x())
@@ -262,11 +263,11 @@ def test_autotuner_decides_a_tile_shape(emd):
     # a second context of the same shape starts with the decision
     f = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
     f.set_frames(p.y, p.v, p.f, p.mask)
-    assert f.tile_rows() == (rows, True)
+    assert f.tile_shape() == (shape, True)
     f.close()
-    with pytest.raises(emd.EMDError):
-        g = emd.Deconvolver(8, 8, 1, 3, 1)
-        try:
-            g.set_tile_rows(40)
-        finally:
-            g.close()
+    g = emd.Deconvolver(8, 8, 1, 3, 1)
+    try:
+        with pytest.raises(emd.EMDError):
+            g.set_tile_shape(9)
+    finally:
+        g.close()

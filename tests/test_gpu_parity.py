@@ -334,7 +334,7 @@ def test_parity_fifty_iterations_k43_with_ring_reuse(emd):
     d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
     try:
         d.set_frames(p.y, p.v, p.f, p.mask)
-        d.set_tile_rows(64)
+        d.set_tile_shape(emd.EMD_TILE_64)
         d.set_x(x0)
         d.iterate(1)
         x1 = d.x()
