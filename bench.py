@@ -111,18 +111,17 @@ def aggregate_over_ranks(local_ms, units_per_rank, world, device="cuda"):
 
 
 def tc_executed_flops(H, W, n, K, r, nprod):
-    """Tensor-core flops one iteration issues: per 128x64 Den tile, exposure
-    and phase, two forward M-tiles of N = Nf over Kf input columns and one
-    adjoint M-tile of N = 64 over Nf input columns, for each of the Kc filter
-    rows and each product of the split."""
+    """Tensor-core flops one iteration issues: per 128 x 128 tile, exposure,
+    phase and filter row (Kc of them), one forward and one adjoint GEMM of
+    M = N = 128 over a band of Kd = rup(128 + 2 hc + hc mod 8, 16) columns
+    (the banded Toeplitz operand, zeros included), for each product of the
+    split."""
     rup = lambda a, b: (a + b - 1) // b * b
     hc = ((K - 1) // 2 + r - 1) // r
     Kc = 2 * hc + 1
-    Nf = rup(64 + 2 * hc, 16)
-    Kf = rup(Nf + 2 * hc, 16)
-    tiles = ((W + 63) // 64) * ((H + 127) // 128)
-    per = Kc * nprod * (2 * 128 * Nf * Kf + 128 * 64 * Nf) * 2
-    return tiles * n * r * r * per
+    Kd = rup(128 + 2 * hc + (hc & 7), 16)
+    tiles = ((W + 127) // 128) * ((H + 127) // 128)
+    return tiles * n * r * r * Kc * nprod * 2 * (128 * 128 * Kd) * 2
 
 
 def fft_flops(H, W, n, K, r, nu):

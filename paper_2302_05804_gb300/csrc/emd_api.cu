@@ -114,6 +114,8 @@ struct emd_ctx {
   uint16_t* xb = nullptr;
   uint16_t* hank = nullptr;
   CUtensorMap xmap;
+  CUtensorMap wmap;
+  uint16_t* wb = nullptr;  // 16-bit w planes of the tensor-core form
   bool hank_ready = false;
   float* scales = nullptr;       // device {z, w, Den, x} operand scales
   unsigned int* xmax = nullptr;  // device max of x (FP16 modes)
@@ -590,9 +592,11 @@ int emd_set_precision(emd_ctx* c, int mode) {
   const size_t xb_bytes = (4ull * c->s.R2 * c->s.g.plane * sizeof(uint16_t) + 255) & ~(size_t)255;
   c->xb = reinterpret_cast<uint16_t*>(c->tc_arena);
   c->hank = reinterpret_cast<uint16_t*>(c->tc_arena + xb_bytes);
+  c->wb = reinterpret_cast<uint16_t*>(c->tc_arena + emd::tc_w_offset(c->s, t));
   c->scales = reinterpret_cast<float*>(c->tc_arena + need - 256);
   c->xmax = reinterpret_cast<unsigned int*>(c->tc_arena + need - 128);
-  if (emd::make_x_tensormap(c->s, t, c->xb, &c->xmap) != 0) {
+  if (emd::make_plane_tensormap(c->s, t, c->xb, 4 * c->s.R2, &c->xmap) != 0 ||
+      emd::make_plane_tensormap(c->s, t, c->wb, 2 * c->s.n, &c->wmap) != 0) {
     set_err("emd_set_precision: cuTensorMapEncodeTiled failed");
     return EMD_ECUDA;
   }
@@ -768,12 +772,13 @@ int emd_iterate(emd_ctx* c, int k) {
       L.Den = c->Den;
       L.u = c->u;
       L.xb = c->xb;
+      L.wb = c->wb;
       L.hank = c->hank;
       L.pp = c->cur;
       L.scales = c->scales;
       L.write_xb = fp16 ? 0 : 1;
       L.err = c->err;
-      CK(emd::launch_tc_iter(c->s, c->ts, L, c->xmap, c->st));
+      CK(emd::launch_tc_iter(c->s, c->ts, L, c->xmap, c->wmap, c->st));
       c->cur ^= 1;
     }
     return EMD_OK;

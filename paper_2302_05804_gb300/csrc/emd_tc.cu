@@ -18,13 +18,19 @@
 // as A and the unflipped kernel ka. Tensor-memory column n of the result
 // holds output column N-1-n.
 //
-// One CTA computes a 128 x 64 tile of Den for all exposures (Den stays in
-// tensor memory for the whole iteration), recomputing the forward model on
-// the tile plus a halo of hc (two 128-row M-tiles of up to 112 columns),
-// and applies the multiplicative update at the end. Warp roles: warp 0
-// issues TMA / bulk copies, warp 1 allocates tensor memory and issues MMAs,
-// warps 2-5 run the epilogues (weighting by u into shared memory, update).
-// Every mbarrier wait is bounded; a timeout raises the error word.
+// Two kernels per iteration, each on 128 x 128 tiles (M = N = 128):
+//   tc_fwd_kernel: one CTA per tile of the exposure grid, every exposure:
+//     z_t on exactly the tile (no halo is recomputed), w_t = u_t z_t encoded
+//     as 16-bit hi (and lo) planes in device memory (zero outside the image);
+//   tc_adj_kernel: one CTA per tile of the latent planes: for every exposure
+//     the w_t band around the tile (rows and columns -hc .. 128 + hc) by TMA,
+//     its adjoint GEMM into a tensor-memory partial, added in FP32 to the
+//     running Den in exposure order; the last exposure applies the update.
+// A band starts 16-byte aligned: dlt = hc mod 8 columns before the window
+// it needs, which the Hankel operands absorb (their index carries -dlt).
+// Warp roles in both: warp 0 issues TMA / bulk copies, warp 1 allocates
+// tensor memory and issues MMAs, warps 2-5 run the epilogue. Every mbarrier
+// wait is bounded; a timeout raises the error word.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -38,10 +44,10 @@ namespace emd {
 
 namespace {
 
-constexpr int kTcRows = 128;    // Den rows per CTA = MMA M
-constexpr int kTcCols = 64;     // Den columns per CTA = adjoint N
+constexpr int kTcRows = 128;    // tile rows = MMA M
+constexpr int kTcCols = 128;    // tile columns = MMA N
 constexpr int kTcThreads = 192; // 6 warps
-constexpr int kTcStages = 3;    // B (Hankel) ring depth
+constexpr int kTcStages = 4;    // B (Hankel) ring depth
 constexpr uint32_t kSpin = 1u << 22;
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -172,32 +178,25 @@ bool make_tc_shape(const Shape& s, int mode, TcShape* t, const char** why) {
   t->mode = mode;
   t->fp16 = (mode == EMD_PREC_FP16 || mode == EMD_PREC_SPLIT_FP16);
   t->nprod = (mode == EMD_PREC_SPLIT_BF16 || mode == EMD_PREC_SPLIT_FP16) ? 3 : 1;
-  t->TC = kTcCols;
-  t->Nf = rup(kTcCols + 2 * s.hc, 16);
-  t->Kf = rup(t->Nf + 2 * s.hc, 16);
-  t->Ka = t->Nf;
+  t->NW = kTcCols;
+  t->dlt = s.hc & 7;
+  t->Kd = rup(kTcCols + 2 * s.hc + t->dlt, 16);
   t->XRp = rup(kTcRows + 2 * s.hc, 8);
-  t->WRp = rup(kTcRows + 2 * s.hc, 8);
-  t->Sf = t->Kf / 8 + t->Nf / 8 - 1;
-  t->Sa = t->Ka / 8 + kTcCols / 8 - 1;
+  t->Sd = t->Kd / 8 + kTcCols / 8 - 1;
   t->gxt = (s.W + kTcCols - 1) / kTcCols;
   t->gyt = (s.H + kTcRows - 1) / kTcRows;
-  if (t->Nf > 128) { *why = "PSF footprint too large for the tensor-core tile"; return false; }
-  const size_t xs = 2ull * t->XRp * t->Kf * 2;
-  const size_t ws = 2ull * t->WRp * t->Ka * 2;
-  const size_t stage = 2ull * t->Sf * 128;
-  t->stage_bytes = (int)stage;
-  t->hank_block = 2 * (t->Sf + t->Sa) * 128;
-  t->smem = xs + ws + kTcStages * stage + 256;
+  t->stage_bytes = 2 * t->Sd * 128;
+  t->hank_block = 2 * t->stage_bytes;  // forward (hi, lo), adjoint (hi, lo)
+  const size_t band = 2ull * t->XRp * t->Kd * 2;
+  t->smem = band + kTcStages * (size_t)t->stage_bytes;
   if (t->smem > 227 * 1024 - 1024) { *why = "tensor-core tile exceeds shared memory"; return false; }
   // one CTA per SM: a second resident CTA would wait in tcgen05.alloc for
-  // the 512 tensor-memory columns of the first
+  // the tensor-memory columns of the first
   if (t->smem < 120 * 1024) t->smem = 120 * 1024;
-  // the epilogue's u reads (region rows < 128 + 2hc, columns < Nf) stay in
-  // the padded planes; TMA loads outside the planes read zeros
+  // the epilogues' plane accesses (rows < gyt 128, columns < gxt 128 of the
+  // image) stay in the padded planes; TMA loads outside them read zeros
   const Geom& g = s.g;
-  if ((t->gxt - 1) * kTcCols + s.hc + t->Nf > g.P ||
-      (t->gyt - 1) * kTcRows + 3 * s.hc + kTcRows > g.PH) {
+  if (g.B + t->gxt * kTcCols > g.P || g.B + t->gyt * kTcRows > g.PH) {
     *why = "padded geometry too small for the tensor-core tiles";
     return false;
   }
@@ -209,12 +208,13 @@ bool make_tc_shape(const Shape& s, int mode, TcShape* t, const char** why) {
 // ---------------------------------------------------------------------------
 
 // Hankel core matrices of every (t, phi, a): block = [F_hi | F_lo | A_hi | A_lo],
-// F: Sf x 8 x 8 entries g[8s + r + e - (Nf - 1)] of kf row a; A: the same with
-// ka and N = TC. lo = rounding residue of the scaled value.
+// each Sd x 8 x 8 entries g[8s + r + e - (NW - 1) - dlt] of row a of kf (F)
+// or ka (A); lo = rounding residue of the scaled value.
 __global__ void build_hankel_kernel(const Shape s, const TcShape t, const float* __restrict__ kf,
                                     const float* __restrict__ ka, uint16_t* __restrict__ hank,
                                     float gscale) {
-  const long long per = (long long)(t.Sf + t.Sa) * 64;
+  const int per_op = t.Sd * 64;
+  const long long per = 2LL * per_op;
   const long long total = (long long)s.n * s.R2 * s.Kc * per;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -222,20 +222,17 @@ __global__ void build_hankel_kernel(const Shape s, const TcShape t, const float*
     const int within = (int)(e - blk * per);
     const int a = (int)(blk % s.Kc);
     const long long tp = blk / s.Kc;  // t * R2 + phi
-    const bool fwd = within < t.Sf * 64;
-    const int w = fwd ? within : within - t.Sf * 64;
+    const bool fwd = within < per_op;
+    const int w = fwd ? within : within - per_op;
     const int sidx = w / 64, r = (w / 8) % 8, c = w % 8;
-    const int N = fwd ? t.Nf : t.TC;
-    const int idx = 8 * sidx + r + c - (N - 1);
+    const int idx = 8 * sidx + r + c - (t.NW - 1) - t.dlt;
     const float* krow = (fwd ? kf : ka) + (tp * s.Kc + a) * s.KP;
     const float g = (idx >= 0 && idx < s.Kc) ? krow[idx] * gscale : 0.f;
     const uint16_t hi = enc16(g, t.fp16);
     const uint16_t lo = enc16(g - dec16(hi, t.fp16), t.fp16);
-    uint16_t* base = hank + blk * (long long)(t.hank_block / 2);
-    const int S = fwd ? t.Sf : t.Sa;
-    uint16_t* part = base + (fwd ? 0 : 2 * t.Sf * 64);
+    uint16_t* part = hank + blk * (long long)(t.hank_block / 2) + (fwd ? 0 : 2 * per_op);
     part[w] = hi;
-    part[S * 64 + w] = lo;
+    part[per_op + w] = lo;
   }
 }
 
@@ -268,6 +265,7 @@ struct TcArgs {
   float* Den;            // R2 planes: running sum of the exposures' partials
   const float* u;        // n planes
   uint16_t* xb;          // [2][2][R2] 16-bit planes
+  uint16_t* wb;          // [2 hi/lo][n] 16-bit planes of w = u z
   const uint16_t* hank;  // Hankel blocks
   int pp;                // ping-pong slot of the current x in xb
   const float* scales;   // device: {forward acc -> z, w -> operand, adjoint acc -> Den, x -> operand}
@@ -275,362 +273,388 @@ struct TcArgs {
   int* err;
 };
 
-template <int NPROD>
-__global__ void __launch_bounds__(kTcThreads, 1)
-    tc_iter_kernel(const Shape s, const TcShape t, const TcArgs A,
-                   const __grid_constant__ CUtensorMap xmap) {
-  extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ uint64_t bars[9 + 2 * kTcStages];
-  __shared__ uint32_t tmem_base_s;
-  __shared__ int abort_s;
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = blockIdx.y * kTcRows, j0 = blockIdx.x * kTcCols;
-  const Geom& g = s.g;
-  const int hc = s.hc, Kc = s.Kc, R2 = s.R2;
-
-  const uint32_t xplane_b = (uint32_t)t.XRp * t.Kf * 2;  // bytes of one x band plane
-  const uint32_t wplane_b = (uint32_t)t.WRp * t.Ka * 2;
-  uint8_t* xs = sm;
-  uint8_t* ws = xs + 2 * xplane_b;
-  uint8_t* ring = ws + 2 * wplane_b;
-  uint64_t* x_full = &bars[0];
-  uint64_t* x_empty = &bars[1];
-  uint64_t* acc_full = &bars[2];   // [2]
-  uint64_t* acc_empty = &bars[4];  // [2]
-  uint64_t* w_full = &bars[6];
-  uint64_t* den_full = &bars[7];
-  uint64_t* den_empty = &bars[8];
-  uint64_t* b_full = &bars[9];
-  uint64_t* b_empty = &bars[9 + kTcStages];
-  volatile int* abort = &abort_s;
-
+// CTA set-up shared by both kernels: barriers (count per entry of `counts`),
+// tensor memory (`cols` columns, a power of two), abort flag.
+__device__ __forceinline__ uint32_t tc_setup(uint64_t* bars, const uint32_t* counts, int nbars,
+                                             uint32_t* tmem_base_s, int* abort_s, uint32_t cols) {
+  const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    abort_s = 0;
-    bar_init(x_full, 1);
-    bar_init(x_empty, 1);
-    for (int i = 0; i < 2; ++i) {
-      bar_init(&acc_full[i], 1);
-      bar_init(&acc_empty[i], 128);
-    }
-    bar_init(w_full, 128);
-    bar_init(den_full, 1);
-    bar_init(den_empty, 128);
-    for (int i = 0; i < kTcStages; ++i) {
-      bar_init(&b_full[i], 1);
-      bar_init(&b_empty[i], 1);
-    }
+    *abort_s = 0;
+    for (int i = 0; i < nbars; ++i) bar_init(&bars[i], counts[i]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-        su32(&tmem_base_s)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_base_s)),
+                 "r"(cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = tmem_base_s;
-  constexpr int nprod = NPROD;
-  const float zscale = A.scales[0], wscale = A.scales[1], dscale = A.scales[2],
-              xscale = A.scales[3];
-  const int KSf = t.Kf / 16, KSa = t.Ka / 16;
+  return *tmem_base_s;
+}
+
+__device__ __forceinline__ void tc_teardown(uint32_t tmem, uint32_t cols, int abort_s, int* err) {
+  tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+  }
+  if (threadIdx.x == 0 && abort_s) atomicOr(err, kErrTimeout);
+}
+
+// instruction descriptor: FP32 accumulate, BF16 or FP16 operands, M = 128, N = 128
+__device__ __forceinline__ uint32_t tc_idesc(int fp16) {
+  return (1u << 4) | ((fp16 ? 0u : 1u) << 7) | ((fp16 ? 0u : 1u) << 10) |
+         ((uint32_t)(kTcCols >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+// One filter row's GEMM of a band (rows shifted by a) with the Hankel operand
+// of a ring stage: Kd / 16 k-steps, 1 or 3 products (hi hi, hi lo, lo hi).
+template <int NPROD>
+__device__ __forceinline__ void tc_row_gemm(uint32_t dacc, uint32_t band_a, uint32_t bandplane,
+                                            uint32_t lbo, uint32_t bst, int Sd, int ksteps,
+                                            int a, uint32_t idesc, uint32_t& accum) {
+  uint64_t ah = sdesc(band_a + a * 16, lbo, 128);
+  uint64_t al = ah + (bandplane >> 4);
+  uint64_t bh = sdesc(bst, 128, 128);
+  uint64_t bl = bh + ((uint32_t)(Sd * 128) >> 4);
+  const uint64_t astep = (2u * lbo) >> 4, bstep = 256u >> 4;
+#pragma unroll 2
+  for (int kk = 0; kk < ksteps; ++kk) {
+    mma(dacc, ah, bh, idesc, accum);
+    if (NPROD == 3) {
+      mma(dacc, ah, bl, idesc, 1u);
+      mma(dacc, al, bh, idesc, 1u);
+    }
+    accum = 1;
+    ah += astep;
+    al += astep;
+    bh += bstep;
+    bl += bstep;
+  }
+}
+
+// Forward model of one 128 x 128 tile for every exposure: z_t = sum over the
+// phases and the Kc filter rows of (x band rows shifted by a) x Hankel(kf),
+// then w_t = u_t z_t into the 16-bit w planes (hi, and lo for the split).
+// Tensor memory: two accumulators of 128 columns (exposure t in t & 1).
+template <int NPROD>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_fwd_kernel(const Shape s, const TcShape t, const TcArgs A,
+                  const __grid_constant__ CUtensorMap xmap) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ uint64_t bars[6 + 2 * kTcStages];
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.y * kTcRows, j0 = blockIdx.x * kTcCols;
+  const Geom& g = s.g;
+  const int hc = s.hc, Kc = s.Kc, R2 = s.R2;
+  constexpr int nslots = NPROD == 3 ? 2 : 1;
+  const uint32_t bandplane = (uint32_t)t.XRp * t.Kd * 2;
+  uint8_t* band = sm;
+  uint8_t* ring = band + 2 * bandplane;
+  uint64_t* x_full = &bars[0];
+  uint64_t* x_empty = &bars[1];
+  uint64_t* acc_full = &bars[2];   // [2]
+  uint64_t* acc_empty = &bars[4];  // [2]
+  uint64_t* b_full = &bars[6];
+  uint64_t* b_empty = &bars[6 + kTcStages];
+  uint32_t counts[6 + 2 * kTcStages];
+  counts[0] = 1; counts[1] = 1; counts[2] = 1; counts[3] = 1; counts[4] = 128; counts[5] = 128;
+  for (int i = 0; i < 2 * kTcStages; ++i) counts[6 + i] = 1;
+  const uint32_t tmem = tc_setup(bars, counts, 6 + 2 * kTcStages, &tmem_base_s, &abort_s, 256);
+  volatile int* abort = &abort_s;
+  const float zscale = A.scales[0], wscale = A.scales[1];
+  const int ksteps = t.Kd / 16;
+  const int cs = j0 + hc - t.dlt;  // padded column of band column 0 (a multiple of 8)
 
   if (warp == 0) {
-    // ------------------------------ producer ------------------------------
-    if (lane == 0) {
-      uint32_t xe_phase = 1;  // x_empty: the first wait passes
+    if (lane == 0) {  // ------------------------------ producer
+      uint32_t xe_phase = 1, be_phase = 1;
       int stage = 0;
-      uint32_t be_phase = 1;
-      const long long hb = t.hank_block;
+      const uint32_t hbytes = (uint32_t)(nslots * t.Sd * 128);
       for (int tt = 0; tt < s.n && !*abort; ++tt) {
-        // split products: one pass per forward M-tile with its hi and lo x
-        // bands; one product: a single pass with both M-tiles' bands resident
-        // (the lo slot holds the second band), so consecutive MMAs share B
-        for (int pass = 0; pass < (nprod == 1 ? 1 : 2); ++pass) {
-          for (int phi = 0; phi < R2; ++phi) {
+        for (int phi = 0; phi < R2; ++phi) {
+          if (R2 > 1 || tt == 0) {  // r = 1: the band stays resident for all exposures
             bar_wait(x_empty, xe_phase, abort);
             xe_phase ^= 1u;
-            bar_expect_tx(x_full, 2 * xplane_b);
-            for (int slot = 0; slot < 2; ++slot) {
-              const int hl = (nprod == 1) ? 0 : slot;
-              const int mt = (nprod == 1) ? slot : pass;
+            bar_expect_tx(x_full, nslots * bandplane);
+            for (int hl = 0; hl < nslots; ++hl) {
               const int plane = (A.pp * 2 + hl) * R2 + phi;
-              for (int c = 0; c < t.Kf / 8; ++c)
-                tma_3d(xs + slot * xplane_b + c * t.XRp * 16, &xmap, j0 + 8 * c, i0 + kTcRows * mt,
-                       plane, x_full);
-            }
-            for (int a = 0; a < Kc; ++a) {
-              bar_wait(&b_empty[stage], be_phase, abort);
-              const uint8_t* src =
-                  reinterpret_cast<const uint8_t*>(A.hank) + (((long long)tt * R2 + phi) * Kc + a) * hb;
-              const uint32_t bytes = 2u * t.Sf * 128u;
-              bar_expect_tx(&b_full[stage], bytes);
-              bulk_copy(ring + stage * t.stage_bytes, src, bytes, &b_full[stage]);
-              if (++stage == kTcStages) { stage = 0; be_phase ^= 1u; }
+              for (int c = 0; c < t.Kd / 8; ++c)
+                tma_3d(band + hl * bandplane + c * t.XRp * 16, &xmap, cs + 8 * c, i0 + hc, plane,
+                       x_full);
             }
           }
-        }
-        for (int phi = 0; phi < R2; ++phi) {
           for (int a = 0; a < Kc; ++a) {
             bar_wait(&b_empty[stage], be_phase, abort);
             const uint8_t* src = reinterpret_cast<const uint8_t*>(A.hank) +
-                                 (((long long)tt * R2 + phi) * Kc + a) * hb + 2ll * t.Sf * 128;
-            const uint32_t bytes = 2u * t.Sa * 128u;
-            bar_expect_tx(&b_full[stage], bytes);
-            bulk_copy(ring + stage * t.stage_bytes, src, bytes, &b_full[stage]);
+                                 (((long long)tt * R2 + phi) * Kc + a) * t.hank_block;
+            bar_expect_tx(&b_full[stage], hbytes);
+            bulk_copy(ring + stage * t.stage_bytes, src, hbytes, &b_full[stage]);
             if (++stage == kTcStages) { stage = 0; be_phase ^= 1u; }
           }
         }
       }
     }
   } else if (warp == 1) {
-    // ------------------------------ MMA issuer -----------------------------
-    if (lane == 0) {
-      const uint32_t idesc_base = (1u << 4) | ((t.fp16 ? 0u : 1u) << 7) | ((t.fp16 ? 0u : 1u) << 10) |
-                                  ((uint32_t)(kTcRows >> 4) << 24);
-      const uint32_t idesc_f = idesc_base | ((uint32_t)(t.Nf >> 3) << 17);
-      const uint32_t idesc_a = idesc_base | ((uint32_t)(t.TC >> 3) << 17);
-      const uint32_t xs_a = su32(xs), ws_a = su32(ws), ring_a = su32(ring);
-      const uint32_t x_lbo = (uint32_t)t.XRp * 16, w_lbo = (uint32_t)t.WRp * 16;
-      uint32_t xf_phase = 0, wf_phase = 0, bf_phase = 0, de_phase = 1;
+    if (lane == 0) {  // ------------------------------ MMA issuer
+      const uint32_t idesc = tc_idesc(t.fp16);
+      const uint32_t band_a = su32(band), ring_a = su32(ring);
+      const uint32_t lbo = (uint32_t)t.XRp * 16;
+      uint32_t xf_phase = 0, bf_phase = 0;
       uint32_t ae_phase[2] = {1u, 1u};
       int stage = 0;
       for (int tt = 0; tt < s.n && !*abort; ++tt) {
-        for (int pass = 0; pass < (nprod == 1 ? 1 : 2); ++pass) {
-          const int mt0 = (nprod == 1) ? 0 : pass;
-          const int mt1 = (nprod == 1) ? 1 : pass;
-          for (int mt = mt0; mt <= mt1; ++mt) {
-            bar_wait(&acc_empty[mt], ae_phase[mt], abort);
-            ae_phase[mt] ^= 1u;
-          }
-          tc_fence_after();
-          const uint32_t dacc = tmem + (uint32_t)(128 * mt0);
-          uint32_t accum = 0;
-          for (int phi = 0; phi < R2; ++phi) {
+        const int buf = tt & 1;
+        bar_wait(&acc_empty[buf], ae_phase[buf], abort);
+        ae_phase[buf] ^= 1u;
+        tc_fence_after();
+        const uint32_t dacc = tmem + (uint32_t)(128 * buf);
+        uint32_t accum = 0;
+        for (int phi = 0; phi < R2; ++phi) {
+          if (R2 > 1 || tt == 0) {
             bar_wait(x_full, xf_phase, abort);
             xf_phase ^= 1u;
             tc_fence_after();
-            for (int a = 0; a < Kc; ++a) {
-              bar_wait(&b_full[stage], bf_phase, abort);
-              tc_fence_after();
-              const uint32_t bst = ring_a + stage * t.stage_bytes;
-              // descriptor bases; a k-step advances the start-address field.
-              // Split: ah/al = x_hi/x_lo of this M-tile. One product: ah/al =
-              // x of M-tile 0 / M-tile 1.
-              uint64_t ah = sdesc(xs_a + a * 16, x_lbo, 128);
-              uint64_t al = ah + (xplane_b >> 4);
-              uint64_t bh = sdesc(bst, 128, 128);
-              uint64_t bl = bh + ((uint32_t)(t.Sf * 128) >> 4);
-              const uint64_t astep = (2u * x_lbo) >> 4, bstep = 256u >> 4;
-#pragma unroll 2
-              for (int kk = 0; kk < KSf; ++kk) {
-                if (nprod == 3) {
-                  mma(dacc, ah, bh, idesc_f, accum);
-                  mma(dacc, ah, bl, idesc_f, 1u);
-                  mma(dacc, al, bh, idesc_f, 1u);
-                } else {
-                  mma(dacc, ah, bh, idesc_f, accum);
-                  mma(dacc + 128u, al, bh, idesc_f, accum);
-                }
-                accum = 1;
-                ah += astep;
-                al += astep;
-                bh += bstep;
-                bl += bstep;
-              }
-              mma_commit(&b_empty[stage]);
-              if (++stage == kTcStages) { stage = 0; bf_phase ^= 1u; }
-            }
-            mma_commit(x_empty);
           }
-          for (int mt = mt0; mt <= mt1; ++mt) mma_commit(&acc_full[mt]);
-        }
-        // adjoint of this exposure into the Den partial (tensor-memory
-        // columns 256 + 64 phi), once the epilogue has taken the last one
-        bar_wait(w_full, wf_phase, abort);
-        wf_phase ^= 1u;
-        bar_wait(den_empty, de_phase, abort);
-        de_phase ^= 1u;
-        tc_fence_after();
-        for (int phi = 0; phi < R2; ++phi) {
-          const uint32_t dden = tmem + 256u + (uint32_t)(t.TC * phi);
           for (int a = 0; a < Kc; ++a) {
             bar_wait(&b_full[stage], bf_phase, abort);
             tc_fence_after();
-            const uint32_t bst = ring_a + stage * t.stage_bytes;
-            uint64_t ah = sdesc(ws_a + a * 16, w_lbo, 128);
-            uint64_t al = ah + (wplane_b >> 4);
-            uint64_t bh = sdesc(bst, 128, 128);
-            uint64_t bl = bh + ((uint32_t)(t.Sa * 128) >> 4);
-            const uint64_t astep = (2u * w_lbo) >> 4, bstep = 256u >> 4;
-            uint32_t acc = (a > 0) ? 1u : 0u;
-#pragma unroll 2
-            for (int kk = 0; kk < KSa; ++kk) {
-              mma(dden, ah, bh, idesc_a, acc);
-              acc = 1u;
-              if (nprod == 3) {
-                mma(dden, ah, bl, idesc_a, 1u);
-                mma(dden, al, bh, idesc_a, 1u);
-              }
-              ah += astep;
-              al += astep;
-              bh += bstep;
-              bl += bstep;
-            }
+            tc_row_gemm<NPROD>(dacc, band_a, bandplane, lbo, ring_a + stage * t.stage_bytes,
+                               t.Sd, ksteps, a, idesc, accum);
             mma_commit(&b_empty[stage]);
             if (++stage == kTcStages) { stage = 0; bf_phase ^= 1u; }
           }
+          if (R2 > 1) mma_commit(x_empty);
         }
-        mma_commit(den_full);
+        mma_commit(&acc_full[buf]);
       }
     }
   } else {
-    // ------------------------------ epilogue (warps 2-5) -------------------
-    const int quad = warp & 3;           // tensor-memory lane quadrant of this warp
-    const int m = 32 * quad + lane;      // row within an M-tile
+    // ------------------------------ epilogue (warps 2-5): w = u z
+    const int quad = warp & 3;
+    const int m = 32 * quad + lane;  // tile row of this thread
     const uint32_t lane_off = (uint32_t)(32 * quad) << 16;
+    const int i = i0 + m;
+    const bool row_ok = i < g.H;
     uint32_t af_phase[2] = {0u, 0u};
-    uint32_t df_phase = 0;
     const int fp16 = t.fp16;
     for (int tt = 0; tt < s.n; ++tt) {
-      const float* ut = A.u + (long long)tt * g.plane;
-      for (int mt = 0; mt < 2; ++mt) {
-        const int rr = kTcRows * mt + m;  // region row (0 = coarse row i0 - hc)
-        const bool valid = rr < kTcRows + 2 * hc;
-        const bool warp_valid = kTcRows * mt + 32 * quad < kTcRows + 2 * hc;
-        const float* urow = ut + (long long)(i0 + hc + rr) * g.P + (j0 + hc);
-        const int nch = t.Nf / 16;
-        if (warp_valid) {
-          // tensor-memory columns 16cb..16cb+15 hold region columns
-          // Nf-1-16cb down to Nf-16-16cb; u of the next chunk is loaded while
-          // the current one is converted
-          float un[16];
-#pragma unroll
-          for (int e = 0; e < 16; ++e) un[e] = valid ? urow[t.Nf - 1 - e] : 0.f;
-          for (int cb = 0; cb < nch; ++cb) {
-            float uc[16];
-#pragma unroll
-            for (int e = 0; e < 16; ++e) uc[e] = un[e];
-            if (cb + 1 < nch) {
-#pragma unroll
-              for (int e = 0; e < 16; ++e) un[e] = valid ? urow[t.Nf - 17 - 16 * cb - e] : 0.f;
-            }
-            float z[16];
-            if (cb == 0) {
-              bar_wait(&acc_full[mt], af_phase[mt], abort);
-              tc_fence_after();
-            }
-            tmem_ld16(tmem + lane_off + (uint32_t)(128 * mt + 16 * cb), z);
-            if (valid) {
-              const int c_hi = t.Nf - 16 * cb - 1;  // region column of z[0]
-              uint16_t hv[16], lv[16];
-#pragma unroll
-              for (int e = 0; e < 16; ++e) {
-                const float w = uc[e] * z[e] * zscale * wscale;
-                const uint16_t h = enc16(w, fp16);
-                hv[15 - e] = h;
-                lv[15 - e] = enc16(w - dec16(h, fp16), fp16);
-              }
-              const int c0 = c_hi - 15;  // lowest region column of the chunk (multiple of 8)
-#pragma unroll
-              for (int half = 0; half < 2; ++half) {
-                const int grp = (c0 >> 3) + half;
-                uint4 ph, pl;
-                ph.x = hv[8 * half + 0] | ((uint32_t)hv[8 * half + 1] << 16);
-                ph.y = hv[8 * half + 2] | ((uint32_t)hv[8 * half + 3] << 16);
-                ph.z = hv[8 * half + 4] | ((uint32_t)hv[8 * half + 5] << 16);
-                ph.w = hv[8 * half + 6] | ((uint32_t)hv[8 * half + 7] << 16);
-                *reinterpret_cast<uint4*>(ws + (size_t)grp * t.WRp * 16 + rr * 16) = ph;
-                if (nprod == 3) {
-                  pl.x = lv[8 * half + 0] | ((uint32_t)lv[8 * half + 1] << 16);
-                  pl.y = lv[8 * half + 2] | ((uint32_t)lv[8 * half + 3] << 16);
-                  pl.z = lv[8 * half + 4] | ((uint32_t)lv[8 * half + 5] << 16);
-                  pl.w = lv[8 * half + 6] | ((uint32_t)lv[8 * half + 7] << 16);
-                  *reinterpret_cast<uint4*>(ws + wplane_b + (size_t)grp * t.WRp * 16 + rr * 16) = pl;
-                }
-              }
-            }
-          }
-        } else {
-          bar_wait(&acc_full[mt], af_phase[mt], abort);
-          tc_fence_after();
-        }
-        af_phase[mt] ^= 1u;
-        tc_fence_before();
-        bar_arrive(&acc_empty[mt]);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      bar_arrive(w_full);
-      // ---- this exposure's Den partial: summed into the running Den (FP32,
-      // exposures in ascending order); the last exposure applies
-      // x' = Den > 0 ? x max(N,0) / Den : x instead of storing
-      bar_wait(den_full, df_phase, abort);
-      df_phase ^= 1u;
+      const int buf = tt & 1;
+      bar_wait(&acc_full[buf], af_phase[buf], abort);
+      af_phase[buf] ^= 1u;
       tc_fence_after();
-      const int i = i0 + m;
-      const bool last = (tt + 1 == s.n);
-      for (int phi = 0; phi < R2; ++phi) {
-        const long long pb = (long long)phi * g.plane;
-        for (int cb = 0; cb < t.TC / 16; ++cb) {
-          float dv[16];
-          tmem_ld16(tmem + lane_off + 256u + (uint32_t)(t.TC * phi + 16 * cb), dv);
+      const long long roff = (long long)(g.B + i) * g.P + g.B + j0;  // tile column 0 of row i
+      const float* urow = A.u + (long long)tt * g.plane + roff;
+      uint16_t* wh = A.wb + (long long)tt * g.plane + roff;
+      uint16_t* wl = A.wb + (long long)(s.n + tt) * g.plane + roff;
+      // tensor-memory column q holds tile column 127 - q; chunk cb: columns
+      // c0 .. c0 + 15 with c0 = 112 - 16 cb (B is even: 8-byte aligned u pairs,
+      // 4-byte aligned w pairs)
+      for (int cb = 0; cb < kTcCols / 16; ++cb) {
+        float z[16];
+        tmem_ld16(tmem + lane_off + (uint32_t)(128 * buf + 16 * cb), z);
+        const int c0 = kTcCols - 16 - 16 * cb;
+        if (row_ok && !*abort) {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int jj = t.TC - 1 - (16 * cb + e);
-            const int j = j0 + jj;
-            if (i < g.H && j < g.W && !*abort) {
-              const long long off = pb + (long long)(g.B + i) * g.P + g.B + j;
-              float d = dv[e] * dscale;
-              if (tt > 0) d = A.Den[off] + d;
-              if (!last) {
-                A.Den[off] = d;
-                continue;
-              }
-              const float xo = A.x[off];
-              float xv = xo;
-              if (d > 0.f) {
-                const float nv = fmaxf(A.N[off], 0.f);
-                if (d < 1e-30f)
-                  xv = (float)((double)xo * (double)nv / (double)d);
-                else
-                  xv = xo * nv / d;
-              }
-              A.xn[off] = xv;
-              if (A.write_xb) {
-                const float sv = xv * xscale;
-                const uint16_t h = enc16(sv, fp16);
-                const long long plane_hi = ((long long)((A.pp ^ 1) * 2 + 0) * R2 + phi) * g.plane;
-                const long long plane_lo = ((long long)((A.pp ^ 1) * 2 + 1) * R2 + phi) * g.plane;
-                const long long o2 = (long long)(g.B + i) * g.P + g.B + j;
-                A.xb[plane_hi + o2] = h;
-                A.xb[plane_lo + o2] = enc16(sv - dec16(h, fp16), fp16);
-              }
+          for (int q = 0; q < 8; ++q) {
+            const int jc = c0 + 2 * q;  // tile columns jc, jc + 1
+            if (j0 + jc >= g.W) break;
+            const float2 uv = *reinterpret_cast<const float2*>(urow + jc);
+            const float w0 = uv.x * z[15 - 2 * q] * zscale * wscale;
+            const float w1 = (j0 + jc + 1 < g.W) ? uv.y * z[14 - 2 * q] * zscale * wscale : 0.f;
+            const uint16_t h0 = enc16(w0, fp16), h1 = enc16(w1, fp16);
+            *reinterpret_cast<uint32_t*>(wh + jc) = h0 | ((uint32_t)h1 << 16);
+            if (NPROD == 3) {
+              const uint16_t l0 = enc16(w0 - dec16(h0, fp16), fp16);
+              const uint16_t l1 = enc16(w1 - dec16(h1, fp16), fp16);
+              *reinterpret_cast<uint32_t*>(wl + jc) = l0 | ((uint32_t)l1 << 16);
             }
           }
         }
       }
       tc_fence_before();
-      bar_arrive(den_empty);
+      bar_arrive(&acc_empty[buf]);
     }
   }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  tc_teardown(tmem, 256, abort_s, A.err);
+}
+
+// Adjoint and update of one 128 x 128 tile of the latent planes: for every
+// exposure the w band (hi, lo) by TMA, per phase the Kc filter rows of
+// (band rows shifted by a) x Hankel(ka) into a tensor-memory partial, which
+// the epilogue adds in FP32 to the running Den (exposures in ascending
+// order); the last exposure applies x' = Den > 0 ? x max(N, 0) / Den : x.
+// Tensor memory: R2 partials of 128 columns, double-buffered when R2 = 1.
+template <int NPROD>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_adj_kernel(const Shape s, const TcShape t, const TcArgs A,
+                  const __grid_constant__ CUtensorMap wmap) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ uint64_t bars[6 + 2 * kTcStages];
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.y * kTcRows, j0 = blockIdx.x * kTcCols;
+  const Geom& g = s.g;
+  const int hc = s.hc, Kc = s.Kc, R2 = s.R2;
+  constexpr int nslots = NPROD == 3 ? 2 : 1;
+  const int nbuf = R2 == 1 ? 2 : 1;
+  const uint32_t bandplane = (uint32_t)t.XRp * t.Kd * 2;
+  uint8_t* band = sm;
+  uint8_t* ring = band + 2 * bandplane;
+  uint64_t* w_full = &bars[0];
+  uint64_t* w_empty = &bars[1];
+  uint64_t* den_full = &bars[2];   // [2]
+  uint64_t* den_empty = &bars[4];  // [2]
+  uint64_t* b_full = &bars[6];
+  uint64_t* b_empty = &bars[6 + kTcStages];
+  uint32_t counts[6 + 2 * kTcStages];
+  counts[0] = 1; counts[1] = 1; counts[2] = 1; counts[3] = 1; counts[4] = 128; counts[5] = 128;
+  for (int i = 0; i < 2 * kTcStages; ++i) counts[6 + i] = 1;
+  const uint32_t tmem = tc_setup(bars, counts, 6 + 2 * kTcStages, &tmem_base_s, &abort_s, 512);
+  volatile int* abort = &abort_s;
+  const float dscale = A.scales[2], xscale = A.scales[3];
+  const int ksteps = t.Kd / 16;
+  const int cs = j0 + hc - t.dlt;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ------------------------------ producer
+      uint32_t we_phase = 1, be_phase = 1;
+      int stage = 0;
+      const uint32_t hbytes = (uint32_t)(nslots * t.Sd * 128);
+      for (int tt = 0; tt < s.n && !*abort; ++tt) {
+        bar_wait(w_empty, we_phase, abort);
+        we_phase ^= 1u;
+        bar_expect_tx(w_full, nslots * bandplane);
+        for (int hl = 0; hl < nslots; ++hl)
+          for (int c = 0; c < t.Kd / 8; ++c)
+            tma_3d(band + hl * bandplane + c * t.XRp * 16, &wmap, cs + 8 * c, i0 + hc,
+                   hl * s.n + tt, w_full);
+        for (int phi = 0; phi < R2; ++phi) {
+          for (int a = 0; a < Kc; ++a) {
+            bar_wait(&b_empty[stage], be_phase, abort);
+            const uint8_t* src = reinterpret_cast<const uint8_t*>(A.hank) +
+                                 (((long long)tt * R2 + phi) * Kc + a) * t.hank_block +
+                                 t.stage_bytes;
+            bar_expect_tx(&b_full[stage], hbytes);
+            bulk_copy(ring + stage * t.stage_bytes, src, hbytes, &b_full[stage]);
+            if (++stage == kTcStages) { stage = 0; be_phase ^= 1u; }
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ------------------------------ MMA issuer
+      const uint32_t idesc = tc_idesc(t.fp16);
+      const uint32_t band_a = su32(band), ring_a = su32(ring);
+      const uint32_t lbo = (uint32_t)t.XRp * 16;
+      uint32_t wf_phase = 0, bf_phase = 0;
+      uint32_t de_phase[2] = {1u, 1u};
+      int stage = 0;
+      for (int tt = 0; tt < s.n && !*abort; ++tt) {
+        const int buf = nbuf == 2 ? (tt & 1) : 0;
+        bar_wait(&den_empty[buf], de_phase[buf], abort);
+        de_phase[buf] ^= 1u;
+        bar_wait(w_full, wf_phase, abort);
+        wf_phase ^= 1u;
+        tc_fence_after();
+        for (int phi = 0; phi < R2; ++phi) {
+          const uint32_t dden = tmem + (uint32_t)(128 * (R2 * buf + phi));
+          uint32_t accum = 0;
+          for (int a = 0; a < Kc; ++a) {
+            bar_wait(&b_full[stage], bf_phase, abort);
+            tc_fence_after();
+            tc_row_gemm<NPROD>(dden, band_a, bandplane, lbo, ring_a + stage * t.stage_bytes,
+                               t.Sd, ksteps, a, idesc, accum);
+            mma_commit(&b_empty[stage]);
+            if (++stage == kTcStages) { stage = 0; bf_phase ^= 1u; }
+          }
+        }
+        mma_commit(w_empty);
+        mma_commit(&den_full[buf]);
+      }
+    }
+  } else {
+    // ------------------------------ epilogue (warps 2-5): Den, update
+    const int quad = warp & 3;
+    const int m = 32 * quad + lane;
+    const uint32_t lane_off = (uint32_t)(32 * quad) << 16;
+    const int i = i0 + m;
+    const bool row_ok = i < g.H;
+    uint32_t df_phase[2] = {0u, 0u};
+    const int fp16 = t.fp16;
+    for (int tt = 0; tt < s.n; ++tt) {
+      const int buf = nbuf == 2 ? (tt & 1) : 0;
+      bar_wait(&den_full[buf], df_phase[buf], abort);
+      df_phase[buf] ^= 1u;
+      tc_fence_after();
+      const bool last = (tt + 1 == s.n);
+      for (int phi = 0; phi < R2; ++phi) {
+        const long long pb = (long long)phi * g.plane + (long long)(g.B + i) * g.P + g.B + j0;
+        for (int cb = 0; cb < kTcCols / 16; ++cb) {
+          float dv[16];
+          tmem_ld16(tmem + lane_off + (uint32_t)(128 * (R2 * buf + phi) + 16 * cb), dv);
+          if (!row_ok || *abort) continue;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int jc = kTcCols - 1 - (16 * cb + e);  // tile column of dv[e]
+            if (j0 + jc >= g.W) continue;
+            const long long off = pb + jc;
+            float d = dv[e] * dscale;
+            if (tt > 0) d = A.Den[off] + d;
+            if (!last) {
+              A.Den[off] = d;
+              continue;
+            }
+            const float xo = A.x[off];
+            float xv = xo;
+            if (d > 0.f) {
+              const float nv = fmaxf(A.N[off], 0.f);
+              if (d < 1e-30f)  // denominator near zero: guarded ratio in FP64
+                xv = (float)((double)xo * (double)nv / (double)d);
+              else
+                xv = xo * nv / d;
+            }
+            A.xn[off] = xv;
+            if (A.write_xb) {
+              const float sv = xv * xscale;
+              const uint16_t h = enc16(sv, fp16);
+              const long long o2 = off - (long long)phi * g.plane;
+              A.xb[((long long)((A.pp ^ 1) * 2 + 0) * R2 + phi) * g.plane + o2] = h;
+              A.xb[((long long)((A.pp ^ 1) * 2 + 1) * R2 + phi) * g.plane + o2] =
+                  enc16(sv - dec16(h, fp16), fp16);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      bar_arrive(&den_empty[buf]);
+    }
   }
-  if (threadIdx.x == 0 && abort_s) atomicOr(A.err, kErrTimeout);
+  tc_teardown(tmem, 512, abort_s, A.err);
 }
 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 
+// layout: 16-bit x planes [2][2][R2], Hankel blocks, 16-bit w planes [2][n],
+// then 512 bytes of scales and maxima
 size_t tc_buffer_bytes(const Shape& s, const TcShape& t) {
+  return tc_w_offset(s, t) + ((2ull * s.n * s.g.plane * sizeof(uint16_t) + 255) & ~(size_t)255) +
+         512;
+}
+
+size_t tc_w_offset(const Shape& s, const TcShape& t) {
   const size_t xb = 4ull * s.R2 * s.g.plane * sizeof(uint16_t);
   const size_t hk = (size_t)s.n * s.R2 * s.Kc * t.hank_block;
-  return ((xb + 255) & ~(size_t)255) + ((hk + 255) & ~(size_t)255) + 512;
+  return ((xb + 255) & ~(size_t)255) + ((hk + 255) & ~(size_t)255);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -638,7 +662,10 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-int make_x_tensormap(const Shape& s, const TcShape& t, void* xb, CUtensorMap* map) {
+// 3-D map over `planes` 16-bit padded planes (the x planes or the w planes):
+// boxes of 8 columns x XRp rows of one plane
+int make_plane_tensormap(const Shape& s, const TcShape& t, void* base, int planes,
+                         CUtensorMap* map) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -650,11 +677,11 @@ int make_x_tensormap(const Shape& s, const TcShape& t, void* xb, CUtensorMap* ma
     fn = reinterpret_cast<EncodeTiledFn>(p);
   }
   const Geom& g = s.g;
-  cuuint64_t dims[3] = {(cuuint64_t)g.P, (cuuint64_t)g.PH, (cuuint64_t)(4 * s.R2)};
+  cuuint64_t dims[3] = {(cuuint64_t)g.P, (cuuint64_t)g.PH, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)g.P * 2, (cuuint64_t)g.plane * 2};
   cuuint32_t box[3] = {8, (cuuint32_t)t.XRp, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, xb, dims, strides, box, estr,
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -2;
@@ -714,12 +741,14 @@ cudaError_t launch_fp16_scales(const unsigned int* xmax_bits, float gscale, floa
 }
 
 cudaError_t launch_tc_iter(const Shape& s, const TcShape& t, const TcLaunch& L,
-                           const CUtensorMap& map, cudaStream_t st) {
-  {
-    cudaError_t e = allow_max_dynamic_smem(t.nprod == 3 ? (const void*)tc_iter_kernel<3>
-                                                       : (const void*)tc_iter_kernel<1>);
-    if (e != cudaSuccess) return e;
-  }
+                           const CUtensorMap& xmap, const CUtensorMap& wmap, cudaStream_t st) {
+  const bool split = t.nprod == 3;
+  cudaError_t e = allow_max_dynamic_smem(split ? (const void*)tc_fwd_kernel<3>
+                                               : (const void*)tc_fwd_kernel<1>);
+  if (e == cudaSuccess)
+    e = allow_max_dynamic_smem(split ? (const void*)tc_adj_kernel<3>
+                                     : (const void*)tc_adj_kernel<1>);
+  if (e != cudaSuccess) return e;
   TcArgs a;
   a.x = L.x;
   a.xn = L.xn;
@@ -727,16 +756,22 @@ cudaError_t launch_tc_iter(const Shape& s, const TcShape& t, const TcLaunch& L,
   a.Den = L.Den;
   a.u = L.u;
   a.xb = L.xb;
+  a.wb = L.wb;
   a.hank = L.hank;
   a.pp = L.pp;
   a.scales = L.scales;
   a.write_xb = L.write_xb;
   a.err = L.err;
   dim3 grid(t.gxt, t.gyt);
-  if (t.nprod == 3)
-    tc_iter_kernel<3><<<grid, kTcThreads, t.smem, st>>>(s, t, a, map);
+  if (split)
+    tc_fwd_kernel<3><<<grid, kTcThreads, t.smem, st>>>(s, t, a, xmap);
   else
-    tc_iter_kernel<1><<<grid, kTcThreads, t.smem, st>>>(s, t, a, map);
+    tc_fwd_kernel<1><<<grid, kTcThreads, t.smem, st>>>(s, t, a, xmap);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (split)
+    tc_adj_kernel<3><<<grid, kTcThreads, t.smem, st>>>(s, t, a, wmap);
+  else
+    tc_adj_kernel<1><<<grid, kTcThreads, t.smem, st>>>(s, t, a, wmap);
   return cudaGetLastError();
 }
 
