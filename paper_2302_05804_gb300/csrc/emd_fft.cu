@@ -252,6 +252,16 @@ constexpr int kWarps = kFThreads / 32;
 constexpr int kColsPerWarp = (kFBins + kWarps - 1) / kWarps;  // 5
 using SpecRegs = float2[kColsPerWarp][4];
 
+// Visits (p, q) of a B x B output region, warp w taking the rows w, w + 16,
+// ... and its lanes the columns lane, lane + 32, ... (row addresses are
+// computed once per row; no division by B per element).
+template <class F>
+__device__ __forceinline__ void for_region(int B, F&& f) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int p = warp; p < B; p += kWarps)
+    for (int q = lane; q < B; q += 32) f(p, q);
+}
+
 __device__ __forceinline__ void load_spec_cols(SpecRegs& kr, const float2* kt) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -448,13 +458,21 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // start copying the 128 x 128 region with origin (r0, c0) of a padded plane
 // into stg (row-major, zero outside the H x W image)
 __device__ void region_async(float* stg, const float* plane, const Geom& g, int r0, int c0) {
-  for (int e = threadIdx.x; e < kFT * kFT; e += blockDim.x) {
-    const int P = e >> 7, Q = e & (kFT - 1);
-    const int i = r0 + P, j = c0 + Q;
-    if (i >= 0 && i < g.H && j >= 0 && j < g.W)
-      cp_async4(stg + e, plane + (long long)(g.B + i) * g.P + g.B + j);
-    else
-      stg[e] = 0.f;
+  // warp w copies the rows w, w + 16, ...; a row's address is formed once
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int P = warp; P < kFT; P += kFThreads / 32) {
+    const int i = r0 + P;
+    const bool row_in = i >= 0 && i < g.H;
+    const float* src = plane + (long long)(g.B + i) * g.P + g.B + c0;
+    float* dst = stg + P * kFT;
+#pragma unroll
+    for (int c = 0; c < kFT / 32; ++c) {
+      const int Q = lane + 32 * c, j = c0 + Q;
+      if (row_in && j >= 0 && j < g.W)
+        cp_async4(dst + Q, src + Q);
+      else
+        dst[Q] = 0.f;
+    }
   }
   cp_async_commit();
 }
@@ -557,10 +575,12 @@ __device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int
     // u of this exposure (B x B, row-major in stg) arrives during the
     // inverse transform
     const long long tplane = (long long)t * g.plane;
-    for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
-      const int p = e / B, q = e - p * B;
-      const int i = i0 + p, j = j0 + q;
-      if (i < g.H && j < g.W) cp_async4(stg + e, a.u + tplane + (long long)(g.B + i) * g.P + g.B + j);
+    {
+      const float* ut = a.u + tplane + (long long)(g.B + i0) * g.P + g.B + j0;
+      const int pmax = min(B, g.H - i0), qmax = min(B, g.W - j0);
+      for_region(B, [&](int p, int q) {
+        if (p < pmax && q < qmax) cp_async4(stg + p * B + q, ut + (long long)p * g.P + q);
+      });
     }
     cp_async_commit();
     if (R2 == 1) {
@@ -576,26 +596,25 @@ __device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int
       // heavy-tailed weights u' = u (nu+1) / (nu + u (y - z)^2): both u' z
       // (denominator) and u' y (numerator) go to planes
       const float nu1 = a.nu + 1.f;
-      for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
-        const int p = e / B, q = e - p * B;
-        const int i = i0 + p, j = j0 + q;
-        if (i < g.H && j < g.W) {
-          const long long gi = tplane + (long long)(g.B + i) * g.P + g.B + j;
+      const long long base = tplane + (long long)(g.B + i0) * g.P + g.B + j0;
+      const int pmax = min(B, g.H - i0), qmax = min(B, g.W - j0);
+      for_region(B, [&](int p, int q) {
+        if (p < pmax && q < qmax) {
+          const long long gi = base + (long long)p * g.P + q;
           const float z = tile_at(wk, p + 2 * hc, q + 2 * hc) * kFScale;
-          const float uv = stg[e], yv = a.y[gi], d = yv - z;
+          const float uv = stg[p * B + q], yv = a.y[gi], d = yv - z;
           const float us = uv > 0.f ? uv * nu1 / fmaf(uv * d, d, a.nu) : 0.f;
           a.w[gi] = us * z;
           a.w2[gi] = us * yv;
         }
-      }
+      });
     } else {
-      for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
-        const int p = e / B, q = e - p * B;
-        const int i = i0 + p, j = j0 + q;
-        if (i < g.H && j < g.W)
-          a.w[tplane + (long long)(g.B + i) * g.P + g.B + j] =
-              stg[e] * (tile_at(wk, p + 2 * hc, q + 2 * hc) * kFScale);
-      }
+      float* wt = a.w + tplane + (long long)(g.B + i0) * g.P + g.B + j0;
+      const int pmax = min(B, g.H - i0), qmax = min(B, g.W - j0);
+      for_region(B, [&](int p, int q) {
+        if (p < pmax && q < qmax)
+          wt[(long long)p * g.P + q] = stg[p * B + q] * (tile_at(wk, p + 2 * hc, q + 2 * hc) * kFScale);
+      });
     }
     __syncthreads();
   }
@@ -636,11 +655,11 @@ __device__ void r2c_2d_accumulate_phases(float2* buf, float2* acc, const float2*
 // numerator is a.N, or (Student-t) the transformed tile num
 __device__ void update_phase(const float2* sh, const float2* num, const FftLaunch& a,
                              const Geom& g, long long off, int i0, int j0, int B) {
-  for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
-    const int p = e / B, q = e - p * B;
-    const int i = i0 + p, j = j0 + q;
-    if (i < g.H && j < g.W) {
-      const long long gi = off + (long long)(g.B + i) * g.P + g.B + j;
+  const long long base = off + (long long)(g.B + i0) * g.P + g.B + j0;
+  const int pmax = min(B, g.H - i0), qmax = min(B, g.W - j0);
+  for_region(B, [&](int p, int q) {
+    if (p < pmax && q < qmax) {
+      const long long gi = base + (long long)p * g.P + q;
       const float d = tile_at(sh, p, q) * kFScale;
       const float xo = a.x[gi], nraw = a.N[gi];
       const float nt = num ? tile_at(num, p, q) * kFScale : nraw;
@@ -659,7 +678,7 @@ __device__ void update_phase(const float2* sh, const float2* num, const FftLaunc
       }
       a.xn[gi] = xv;
     }
-  }
+  });
 }
 
 // the adjoint pass and the update of one tile; starts and ends at a CTA
