@@ -168,7 +168,7 @@ def variant_roofline(name, p, launch_s, peak32, peak32_src):
             rec["traffic"] = tr
             rec["hbm_gbs"] = tr / launch_s / 1e9
         return rec
-    if name in ("split_bf16", "bf16"):
+    if name in ("split_bf16", "bf16", "split_fp16", "fp16"):
         nprod = 3 if name.startswith("split") else 1
         ex = tc_executed_flops(p.H, p.W, p.n, p.K, p.r, nprod) / launch_s / 1e12
         pk, src = bf16_peak()
@@ -387,7 +387,8 @@ def run_variants(p, peak32, peak32_src, steps=5, warmup=2):
     from paper_2302_05804_gb300 import emd
     forms = [("fp32_pair", emd.EMD_PREC_FP32_PAIR, 0.0),
              ("fft", emd.EMD_PREC_FFT_FP32, 0.0), ("split_bf16", emd.EMD_PREC_SPLIT_BF16, 0.0),
-             ("bf16", emd.EMD_PREC_BF16, 0.0), ("student_t_nu3", emd.EMD_PREC_FP32, 3.0),
+             ("bf16", emd.EMD_PREC_BF16, 0.0), ("split_fp16", emd.EMD_PREC_SPLIT_FP16, 0.0),
+             ("fp16", emd.EMD_PREC_FP16, 0.0), ("student_t_nu3", emd.EMD_PREC_FP32, 3.0),
              ("student_t_nu3_fft", emd.EMD_PREC_FFT_FP32, 3.0)]
     out = {}
     for name, prec, nu in forms:
