@@ -477,6 +477,31 @@ __device__ void region_async(float* stg, const float* plane, const Geom& g, int 
   cp_async_commit();
 }
 
+// start copying the 128 x 128 region with origin (r0, c0) of a padded plane
+// straight into the packed row-pair layout of buf (rows 2k and 2k + 1 as the
+// real and imaginary parts of buf[2k kFP + j]; zero outside the image);
+// complete after cp_async_wait_all and a CTA barrier
+__device__ void region_async_packed(float2* buf, const float* plane, const Geom& g, int r0,
+                                    int c0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* bf = reinterpret_cast<float*>(buf);
+  for (int P = warp; P < kFT; P += kFThreads / 32) {
+    const int i = r0 + P;
+    const bool row_in = i >= 0 && i < g.H;
+    const float* src = plane + (long long)(g.B + i) * g.P + g.B + c0;
+    float* dst = bf + 2 * ((P >> 1) * 2 * kFP) + (P & 1);
+#pragma unroll
+    for (int c = 0; c < kFT / 32; ++c) {
+      const int Q = lane + 32 * c, j = c0 + Q;
+      if (row_in && j >= 0 && j < g.W)
+        cp_async4(dst + 2 * Q, src + Q);
+      else
+        dst[2 * Q] = 0.f;
+    }
+  }
+  cp_async_commit();
+}
+
 // wait for the copies, then pack row pairs of stg into buf
 __device__ void pack_region(float2* buf, const float* stg) {
   cp_async_wait_all();
@@ -689,7 +714,9 @@ __device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int
                                  float2* fsm, const TwTab& T) {
   float2* sh = fsm;
   float2* wk = fsm + kFBuf;
-  float* stg = reinterpret_cast<float*>(fsm + 2 * kFBuf);  // 128 x 128 floats
+  // the w regions arrive straight in the packed layout, alternating between
+  // two work buffers: one is transformed while the next region lands in the other
+  float2* wbuf[2] = {fsm + kFBuf, fsm + 2 * kFBuf};
   const Geom& g = s.g;
   const int hc = s.hc, B = kFT - 2 * hc, R2 = s.R2;
   const int i0 = ty * B, j0 = tx * B;
@@ -711,17 +738,19 @@ __device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int
   } else {
     for (int e = threadIdx.x; e < nacc * per; e += blockDim.x) acc[e] = make_float2(0.f, 0.f);
   }
-  region_async(stg, src_plane(0), g, i0 - hc, j0 - hc);
+  region_async_packed(wbuf[0], src_plane(0), g, i0 - hc, j0 - hc);
   for (int k = 0; k < nsrc; ++k) {
-    pack_region(wk, stg);
+    float2* cur = wbuf[k & 1];
+    cp_async_wait_all();
+    __syncthreads();  // region k landed; every reader of the other buffer is done
     // the next source's region arrives during this transform
-    if (k + 1 < nsrc) region_async(stg, src_plane(k + 1), g, i0 - hc, j0 - hc);
+    if (k + 1 < nsrc) region_async_packed(wbuf[(k + 1) & 1], src_plane(k + 1), g, i0 - hc, j0 - hc);
     if (in_smem) {
-      r2c_2d_accumulate(wk, sh, kr, T);
+      r2c_2d_accumulate(cur, sh, kr, T);
       if (k + 1 < nsrc) load_spec_cols(kr, a.spec + (long long)(k + 1) * per);
     } else {
       const int t = student ? k >> 1 : k, base = student ? (k & 1) * R2 : 0;
-      r2c_2d_accumulate_phases(wk, acc + (long long)base * per, a.spec + (long long)t * R2 * per,
+      r2c_2d_accumulate_phases(cur, acc + (long long)base * per, a.spec + (long long)t * R2 * per,
                                R2, T);
     }
   }
@@ -835,7 +864,9 @@ size_t fft_buffer_bytes(const Shape& s, bool student) {
 }
 
 // two transform buffers and a 128 x 128 float staging area
-size_t fft_smem_bytes() { return 2 * (size_t)kFBuf * sizeof(float2) + (size_t)kFT * kFT * sizeof(float); }
+// three transform buffers (the adjoint: accumulator and two work buffers;
+// the forward: x^, work buffer and a 128 x 128 float staging area)
+size_t fft_smem_bytes() { return 3 * (size_t)kFBuf * sizeof(float2); }
 
 int fft_tile_side(const Shape& s) { return kFT - 2 * s.hc; }
 
