@@ -14,19 +14,20 @@
 // convolution multiplies by k^ and the correlation by conj(k^) (k is real).
 //
 // 2D real transforms in shared memory, in place, each 128-point FFT done by
-// one warp in registers (radix-2 butterflies; four values per lane, shuffles
-// across lanes):
+// one warp in registers (radix-2 butterflies; four values per lane; the
+// cross-lane stages exchange half of a lane's values with its partner lane):
 //   forward (R2C): two real rows packed as one complex row; 64 row FFTs by
-//     decimation in frequency (natural in, bit-reversed out); the packed
-//     spectra split into the half spectra (65 bins) of the two rows; 65
-//     column FFTs, again by decimation in frequency. Result: row frequency
-//     bit-reversed, column frequency 0..64 natural. The PSF spectra are made
-//     by the same code, so products never need a reordering.
+//     decimation in frequency (natural in; frequency 32 q + rev5(l) out in
+//     slot q of lane l, stored at 32 q + l); the packed spectra split into
+//     the half spectra (65 bins) of the two rows; 65 column FFTs, again by
+//     decimation in frequency, stored the same way. Result: row frequency
+//     permuted, column frequency 0..64 natural. The PSF spectra are made by
+//     the same code, so products never need a reordering.
 //   inverse (C2R): 65 column FFTs by decimation in time with conjugate
-//     twiddles (bit-reversed in, natural out); the half spectra of row pairs
-//     merged into one packed full spectrum (Hermitian symmetry), written in
-//     bit-reversed order; 64 row FFTs by decimation in time; real part = even
-//     row, imaginary part = odd row; scaled by 1/128^2 (exact).
+//     twiddles (the permuted order in, natural out); the half spectra of row
+//     pairs merged into one packed full spectrum (Hermitian symmetry),
+//     written in the permuted order; 64 row FFTs by decimation in time; real
+//     part = even row, imaginary part = odd row; scaled by 1/128^2 (exact).
 // A half-spectrum buffer is 128 rows x kFP complex; the packed row pair k
 // occupies the 2 kFP slots from 2k kFP, so splitting and merging stay in
 // place (each pair is one warp's, with a warp barrier between its reads and
@@ -61,25 +62,21 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a conj(b)
   return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ int rev7(int m) { return (int)(__brev((unsigned)m) >> 25); }
-// Position of element p of a packed row's spectrum between the row FFT and
-// the split (or between the merge and the inverse row FFT): bits 0-2 XORed
-// with bits 4-6, so that both the row FFT's natural accesses and the
-// bit-reversed accesses of the split and the merge (whose 16 lanes per
-// 64-bit phase differ only in bits 3-6) fall in distinct banks.
-__device__ __forceinline__ int swz(int p) { return p ^ ((p >> 4) & 7); }
+__device__ __forceinline__ int rev5(int m) { return (int)(__brev((unsigned)m) >> 27); }
 
 // Twiddles exp(-2 pi i k / 128), laid out so that the 32 lanes of a warp
 // read consecutive entries at every stage (no bank conflicts):
-//   w[k]          k < 64 (first stage: lane l, value q reads w[32 q + l])
-//   lane2[l]      w[2 l] (second stage)
-//   sh[st - 2][l] w[(l & (s - 1)) << st], s = 64 >> st, st = 2 .. 6, for the
-//                 lanes with bit s set, and 1 for the others (so that every
-//                 lane runs the same instructions; see warp_fft_dif)
+//   w[k]        k < 64 (first stage: lane l, value q reads w[32 q + l])
+//   lane2[l]    w[2 l] (second stage)
+//   xs[k][l]    the twiddle of the cross-lane stage on lane bit k (span
+//               2^k): w[(l mod 2^k) 64 / 2^k], negated on the lanes whose bit
+//               k is set (see warp_fft_dif)
+//   xu[k][l]    the same, not negated (warp_ifft_dit)
 struct TwTab {
   float2 w[64];
   float2 lane2[32];
-  float2 sh[5][32];
+  float2 xs[5][32];
+  float2 xu[5][32];
 };
 
 __device__ __forceinline__ float2 twiddle(int k) {
@@ -89,25 +86,63 @@ __device__ __forceinline__ float2 twiddle(int k) {
 }
 
 __device__ __forceinline__ void init_twiddles(TwTab& T) {
-  for (int e = threadIdx.x; e < 64 + 32 + 5 * 32; e += blockDim.x) {
+  for (int e = threadIdx.x; e < 64 + 32 + 10 * 32; e += blockDim.x) {
     if (e < 64) {
       T.w[e] = twiddle(e);
     } else if (e < 96) {
       T.lane2[e - 64] = twiddle(2 * (e - 64));
     } else {
-      const int st = 2 + (e - 96) / 32, l = (e - 96) & 31, s = 64 >> st;
-      T.sh[st - 2][l] = (l & s) ? twiddle((l & (s - 1)) << st) : make_float2(1.f, 0.f);
+      const int k = ((e - 96) >> 5) % 5, l = (e - 96) & 31, S = 1 << k;
+      const float2 w = twiddle((l & (S - 1)) * (64 >> k));
+      if (e < 96 + 5 * 32)
+        T.xs[k][l] = (l & S) ? make_float2(-w.x, -w.y) : w;
+      else
+        T.xu[k][l] = w;
     }
   }
   __syncthreads();
 }
 
-// J independent 128-point FFTs per warp, in registers: lane l holds
-// v[j][q] = x_j[32 q + l]. Decimation in frequency (natural in, bit-reversed
-// out): the spans 64 and 32 pair the four values a lane holds; spans 16 .. 1
-// pair lanes l and l ^ s through shuffles. The J transforms share the
-// twiddle loads, and their independent shuffles and butterflies overlap the
-// latency of one another (J = 2 in the row and column passes).
+// J independent 128-point FFTs per warp, in registers. A lane holds four
+// values per transform; slot q = 2 s1 + s0 and lane l address element
+// e = 32 q + l of the natural input. Decimation in frequency: the spans 64
+// and 32 pair a lane's own slots (s1, then s0). Each shorter span 2^k pairs
+// the lanes l and l ^ 2^k: the two exchange the halves of their slot pairs
+// that the other needs -- lane bit k trades places with a slot bit whose
+// element bit is already done (s1, s0, s1, s0, s1 for k = 4 .. 0) -- so
+// every lane holds whole butterflies: per stage it sends two values of the
+// four and runs two butterflies, (m + o, (m - o) t) with its own value m,
+// the received o and t negated on the upper lane (the lower lane's a - b is
+// the upper lane's b - a). Output: lane l, slot q holds the spectrum at
+// 32 q + rev5(l). The J transforms share the twiddle loads and overlap each
+// other's latency (J = 2 in the row and column passes).
+template <int J, int K, int SB>  // lane bit K, slot bit SB
+__device__ __forceinline__ void dif_exchange_stage(float2 (&v)[J][4], const TwTab& T, int lane) {
+  const bool lower = ((lane >> K) & 1) == 0;
+  const float2 t = T.xs[K][lane];
+#pragma unroll
+  for (int pr = 0; pr < 2; ++pr) {
+    const int q0 = SB == 1 ? pr : 2 * pr, q1 = q0 | (1 << SB);
+    float2 mine[J], snd[J], o[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      mine[j] = lower ? v[j][q0] : v[j][q1];
+      snd[j] = lower ? v[j][q1] : v[j][q0];
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      o[j].x = __shfl_xor_sync(0xffffffffu, snd[j].x, 1 << K);
+      o[j].y = __shfl_xor_sync(0xffffffffu, snd[j].y, 1 << K);
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      v[j][q0] = cadd(mine[j], o[j]);
+      v[j][q1] = K == 0 ? make_float2(t.x * (mine[j].x - o[j].x), t.x * (mine[j].y - o[j].y))
+                        : cmul(csub(mine[j], o[j]), t);
+    }
+  }
+}
+
 template <int J>
 __device__ __forceinline__ void warp_fft_dif(float2 (&v)[J][4], const TwTab& T, int lane) {
 #pragma unroll
@@ -129,56 +164,57 @@ __device__ __forceinline__ void warp_fft_dif(float2 (&v)[J][4], const TwTab& T, 
       v[j][2 * p] = cadd(a, b);
       v[j][2 * p + 1] = cmul(csub(a, b), t1);
     }
-  // lane pairs (l, l ^ s): the lower lane keeps v + o, the upper one
-  // (o - v) t; both as (o + sgn v) t' with t' = 1 on the lower lane
+  dif_exchange_stage<J, 4, 1>(v, T, lane);
+  dif_exchange_stage<J, 3, 0>(v, T, lane);
+  dif_exchange_stage<J, 2, 1>(v, T, lane);
+  dif_exchange_stage<J, 1, 0>(v, T, lane);
+  dif_exchange_stage<J, 0, 1>(v, T, lane);
+}
+
+// The inverse stage of dif_exchange_stage (conjugate twiddle, unscaled): the
+// butterfly on the lane's own slot pair, (a + b t*, a - b t*), then the same
+// exchange of lane bit K with slot bit SB, which undoes itself.
+template <int J, int K, int SB>
+__device__ __forceinline__ void dit_exchange_stage(float2 (&v)[J][4], const TwTab& T, int lane) {
+  const bool lower = ((lane >> K) & 1) == 0;
+  const float2 tc = conjf2(T.xu[K][lane]);
 #pragma unroll
-  for (int st = 2; st < 7; ++st) {
-    const int s = 64 >> st;
-    const float sgn = (lane & s) ? -1.f : 1.f;
-    const float2 t = T.sh[st - 2][lane];
-    float2 o[J][4];
+  for (int pr = 0; pr < 2; ++pr) {
+    const int q0 = SB == 1 ? pr : 2 * pr, q1 = q0 | (1 << SB);
+    float2 snd[J], o[J];
 #pragma unroll
-    for (int j = 0; j < J; ++j)
+    for (int j = 0; j < J; ++j) {
+      const float2 bt = K == 0 ? v[j][q1] : cmul(v[j][q1], tc);
+      const float2 a = v[j][q0];
+      v[j][q0] = cadd(a, bt);
+      v[j][q1] = csub(a, bt);
+      snd[j] = lower ? v[j][q1] : v[j][q0];
+    }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        o[j][q].x = __shfl_xor_sync(0xffffffffu, v[j][q].x, s);
-        o[j][q].y = __shfl_xor_sync(0xffffffffu, v[j][q].y, s);
-      }
+    for (int j = 0; j < J; ++j) {
+      o[j].x = __shfl_xor_sync(0xffffffffu, snd[j].x, 1 << K);
+      o[j].y = __shfl_xor_sync(0xffffffffu, snd[j].y, 1 << K);
+    }
 #pragma unroll
-    for (int j = 0; j < J; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        v[j][q] = cmul(make_float2(fmaf(sgn, v[j][q].x, o[j][q].x), fmaf(sgn, v[j][q].y, o[j][q].y)),
-                       t);
+    for (int j = 0; j < J; ++j) {
+      if (lower)
+        v[j][q1] = o[j];
+      else
+        v[j][q0] = o[j];
+    }
   }
 }
 
-// Inverse (conjugate twiddles), decimation in time: bit-reversed in,
-// natural out, unscaled. Stage st (span 1 << st) uses sh[4 - st].
+// Inverse (conjugate twiddles), unscaled: input in the layout warp_fft_dif
+// leaves (lane l, slot q: frequency 32 q + rev5(l)), output natural
+// (lane l, slot q: element 32 q + l).
 template <int J>
 __device__ __forceinline__ void warp_ifft_dit(float2 (&v)[J][4], const TwTab& T, int lane) {
-  // lane pairs (l, l ^ s): the upper lane's value is first multiplied by
-  // the twiddle (t' = 1 on the lower lane); then lower: w + o, upper: o - w
-#pragma unroll
-  for (int st = 0; st < 5; ++st) {
-    const int s = 1 << st;
-    const float sgn = (lane & s) ? -1.f : 1.f;
-    const float2 t = conjf2(T.sh[4 - st][lane]);
-    float2 w[J][4], o[J][4];
-#pragma unroll
-    for (int j = 0; j < J; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        w[j][q] = cmul(v[j][q], t);
-        o[j][q].x = __shfl_xor_sync(0xffffffffu, w[j][q].x, s);
-        o[j][q].y = __shfl_xor_sync(0xffffffffu, w[j][q].y, s);
-      }
-#pragma unroll
-    for (int j = 0; j < J; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        v[j][q] = make_float2(fmaf(sgn, w[j][q].x, o[j][q].x), fmaf(sgn, w[j][q].y, o[j][q].y));
-  }
+  dit_exchange_stage<J, 0, 1>(v, T, lane);
+  dit_exchange_stage<J, 1, 0>(v, T, lane);
+  dit_exchange_stage<J, 2, 1>(v, T, lane);
+  dit_exchange_stage<J, 3, 0>(v, T, lane);
+  dit_exchange_stage<J, 4, 1>(v, T, lane);
   const float2 t1 = conjf2(T.lane2[lane]);
 #pragma unroll
   for (int p = 0; p < 2; ++p)
@@ -200,7 +236,11 @@ __device__ __forceinline__ void warp_ifft_dit(float2 (&v)[J][4], const TwTab& T,
   }
 }
 
-// packed row spectrum of a pair (bit-reversed, at r) -> half spectra of the
+// Position, in a row stored from the registers of warp_fft_dif (slot q of
+// lane l at 32 q + l), of frequency m: 32 (m div 32) + rev5(m mod 32).
+__device__ __forceinline__ int fpos(int m) { return (m & 96) | rev5(m & 31); }
+
+// packed row spectrum of a pair (stored as warp_fft_dif leaves it, at r) -> half spectra of the
 // even row (r[0..64]) and the odd row (r[kFP .. kFP+64]); one warp
 __device__ __forceinline__ void split_pair(float2* r, int lane) {
   float2 e[3], o[3];
@@ -208,7 +248,7 @@ __device__ __forceinline__ void split_pair(float2* r, int lane) {
   const int cnt = lane == 0 ? 3 : 2;
   for (int q = 0; q < cnt; ++q) {
     const int m = ms[q];
-    const float2 cm = r[swz(rev7(m))], cn = conjf2(r[swz(rev7((128 - m) & 127))]);
+    const float2 cm = r[fpos(m)], cn = conjf2(r[fpos((128 - m) & 127)]);
     e[q] = make_float2(0.5f * (cm.x + cn.x), 0.5f * (cm.y + cn.y));
     const float2 d = csub(cm, cn);  // (cm - conj(c_-m)) / (2i) = -i d / 2
     o[q] = make_float2(0.5f * d.y, -0.5f * d.x);
@@ -221,7 +261,8 @@ __device__ __forceinline__ void split_pair(float2* r, int lane) {
   __syncwarp();
 }
 
-// half spectra of a row pair -> packed full spectrum, bit-reversed; one warp
+// half spectra of a row pair -> packed full spectrum in the input layout of
+// warp_ifft_dit (frequency m at fpos(m)); one warp
 __device__ __forceinline__ void merge_pair(float2* r, int lane) {
   float2 d[4];
 #pragma unroll
@@ -239,7 +280,7 @@ __device__ __forceinline__ void merge_pair(float2* r, int lane) {
   }
   __syncwarp();
 #pragma unroll
-  for (int q = 0; q < 4; ++q) r[swz(rev7(lane + 32 * q))] = d[q];
+  for (int q = 0; q < 4; ++q) r[32 * q + rev5(lane)] = d[q];  // frequency lane + 32 q
   __syncwarp();
 }
 
@@ -288,7 +329,7 @@ __device__ void r2c_rows(float2* buf, const TwTab& T) {
 #pragma unroll
     for (int j = 0; j < 2; ++j)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) r[j][swz(32 * q + lane)] = v[j][q];
+      for (int q = 0; q < 4; ++q) r[j][32 * q + lane] = v[j][q];
     __syncwarp();
     split_pair(r[0], lane);
     split_pair(r[1], lane);
@@ -379,7 +420,7 @@ __device__ __forceinline__ void rows_inverse(float2* buf, const int (&k)[J], con
     float2* r = buf + 2 * k[j] * kFP;
     merge_pair(r, lane);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[j][q] = r[swz(32 * q + lane)];
+    for (int q = 0; q < 4; ++q) v[j][q] = r[32 * q + lane];
   }
   warp_ifft_dit<J>(v, T, lane);
 #pragma unroll
