@@ -240,6 +240,11 @@ __device__ __forceinline__ void warp_ifft_dit(float2 (&v)[J][4], const TwTab& T,
 // lane l at 32 q + l), of frequency m: 32 (m div 32) + rev5(m mod 32).
 __device__ __forceinline__ int fpos(int m) { return (m & 96) | rev5(m & 31); }
 
+// Shared-memory slot of position i of such a row: bit 0 flipped by bits 4
+// and 5, so that a half-warp's 8-byte accesses in register order (32 q + l)
+// and in frequency order (fpos) both fall on 16 distinct bank pairs.
+__device__ __forceinline__ int rsw(int i) { return i ^ (((i >> 4) ^ (i >> 5)) & 1); }
+
 // packed row spectrum of a pair (stored as warp_fft_dif leaves it, at r) -> half spectra of the
 // even row (r[0..64]) and the odd row (r[kFP .. kFP+64]); one warp
 __device__ __forceinline__ void split_pair(float2* r, int lane) {
@@ -248,7 +253,7 @@ __device__ __forceinline__ void split_pair(float2* r, int lane) {
   const int cnt = lane == 0 ? 3 : 2;
   for (int q = 0; q < cnt; ++q) {
     const int m = ms[q];
-    const float2 cm = r[fpos(m)], cn = conjf2(r[fpos((128 - m) & 127)]);
+    const float2 cm = r[rsw(fpos(m))], cn = conjf2(r[rsw(fpos((128 - m) & 127))]);
     e[q] = make_float2(0.5f * (cm.x + cn.x), 0.5f * (cm.y + cn.y));
     const float2 d = csub(cm, cn);  // (cm - conj(c_-m)) / (2i) = -i d / 2
     o[q] = make_float2(0.5f * d.y, -0.5f * d.x);
@@ -262,7 +267,7 @@ __device__ __forceinline__ void split_pair(float2* r, int lane) {
 }
 
 // half spectra of a row pair -> packed full spectrum in the input layout of
-// warp_ifft_dit (frequency m at fpos(m)); one warp
+// warp_ifft_dit (frequency m at rsw(fpos(m))); one warp
 __device__ __forceinline__ void merge_pair(float2* r, int lane) {
   float2 d[4];
 #pragma unroll
@@ -280,18 +285,55 @@ __device__ __forceinline__ void merge_pair(float2* r, int lane) {
   }
   __syncwarp();
 #pragma unroll
-  for (int q = 0; q < 4; ++q) r[32 * q + rev5(lane)] = d[q];  // frequency lane + 32 q
+  for (int q = 0; q < 4; ++q) r[rsw(32 * q + rev5(lane))] = d[q];  // frequency lane + 32 q
   __syncwarp();
 }
 
-// The column passes are split between the warps: warp w owns columns
-// w, w + 16, ... (kColsPerWarp at most). A PSF spectrum is stored column by
-// column (column m: 128 rows, contiguous), so a warp loads the values of its
-// columns coalesced into registers: kr[c][q] = spectrum(row 32 q + lane,
-// column w + 16 c).
+// The column passes are split between the warps: warp w owns the column
+// slots w + 16 c (c < 4). Slot 0 carries two columns: the bins 0 and 64 of
+// a row's half spectrum are real (those of a real row), so columns 0 and 64
+// travel as one complex column, c0 + i c64, and one FFT serves both (the
+// two spectra are separated by Hermitian symmetry, C(k) = A(k) + i B(k)
+// with conj(C(-k)) = A(k) - i B(k)); every warp runs four column FFTs. A PSF
+// spectrum is stored column by column (column m: 128 rows, contiguous), so
+// a warp loads the values of its columns coalesced into registers:
+// kr[c][q] = spectrum(row 32 q + lane, column w + 16 c), c < 4, and on warp
+// 0 kr[4] = column 64.
 constexpr int kWarps = kFThreads / 32;
 constexpr int kColsPerWarp = (kFBins + kWarps - 1) / kWarps;  // 5
 using SpecRegs = float2[kColsPerWarp][4];
+
+// The spectra A (column 0) and B (column 64) from C = FFT(c0 + i c64) in
+// the layout of warp_fft_dif (lane l, slot q: frequency 32 q + rev5(l)).
+// The frequency -k of k = 32 q + s sits in slot 3 - q of the lane holding
+// 32 - s (s > 0), or in slot (4 - q) mod 4 of lane 0 (s = 0).
+__device__ __forceinline__ void split_dc_nyquist(const float2 (&v)[4], float2 (&a)[4],
+                                                 float2 (&b)[4], int lane) {
+  const int src = rev5((32 - rev5(lane)) & 31);
+  float2 p[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    p[q].x = __shfl_sync(0xffffffffu, v[3 - q].x, src);
+    p[q].y = __shfl_sync(0xffffffffu, v[3 - q].y, src);
+  }
+  if (lane == 0) {  // the shuffle brought v[3 - q]; the partner is v[(4 - q) mod 4]
+    p[0] = v[0];
+    p[1] = v[3];
+    p[2] = v[2];
+    p[3] = v[1];
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    a[q] = make_float2(0.5f * (v[q].x + p[q].x), 0.5f * (v[q].y - p[q].y));
+    const float2 d = make_float2(v[q].x - p[q].x, v[q].y + p[q].y);  // C(k) - conj(C(-k))
+    b[q] = make_float2(0.5f * d.y, -0.5f * d.x);
+  }
+}
+
+// c0 + i c64 for complex c0, c64
+__device__ __forceinline__ float2 pack_dc_nyquist(float2 c0, float2 c64) {
+  return make_float2(c0.x - c64.y, c0.y + c64.x);
+}
 
 // Visits (p, q) of a B x B output region, warp w taking the rows w, w + 16,
 // ... and its lanes the columns lane, lane + 32, ... (row addresses are
@@ -329,7 +371,7 @@ __device__ void r2c_rows(float2* buf, const TwTab& T) {
 #pragma unroll
     for (int j = 0; j < 2; ++j)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) r[j][32 * q + lane] = v[j][q];
+      for (int q = 0; q < 4; ++q) r[j][rsw(32 * q + lane)] = v[j][q];
     __syncwarp();
     split_pair(r[0], lane);
     split_pair(r[1], lane);
@@ -337,38 +379,62 @@ __device__ void r2c_rows(float2* buf, const TwTab& T) {
   __syncthreads();
 }
 
-// J column FFTs (columns m[0..J)) of buf in place
-template <int J, bool INVERSE>
+// J column FFTs (columns m[0..J)) of buf in place; with DN, m[0] = 0 is
+// the slot of columns 0 and 64 (forward: their real values in, their two
+// spectra out; inverse: their Hermitian spectra in, real values out)
+template <int J, bool INVERSE, bool DN>
 __device__ __forceinline__ void columns_inplace(float2* buf, const int (&m)[J], const TwTab& T,
                                                 int lane) {
   float2 v[J][4];
 #pragma unroll
   for (int j = 0; j < J; ++j)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[j][q] = buf[(32 * q + lane) * kFP + m[j]];
+    for (int q = 0; q < 4; ++q) {
+      const float2* row = buf + (32 * q + lane) * kFP;
+      if (DN && j == 0)
+        v[j][q] = INVERSE ? pack_dc_nyquist(row[0], row[64]) : make_float2(row[0].x, row[64].x);
+      else
+        v[j][q] = row[m[j]];
+    }
   if (INVERSE)
     warp_ifft_dit<J>(v, T, lane);
   else
     warp_fft_dif<J>(v, T, lane);
+  if (DN && !INVERSE) {
+    float2 a[4], b[4];
+    split_dc_nyquist(v[0], a, b, lane);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      v[0][q] = a[q];
+      buf[(32 * q + lane) * kFP + 64] = b[q];
+    }
+  }
 #pragma unroll
   for (int j = 0; j < J; ++j)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) buf[(32 * q + lane) * kFP + m[j]] = v[j][q];
+    for (int q = 0; q < 4; ++q) {
+      float2* row = buf + (32 * q + lane) * kFP;
+      if (DN && INVERSE && j == 0) {
+        row[0] = make_float2(v[0][q].x, 0.f);
+        row[64] = make_float2(v[0][q].y, 0.f);
+      } else {
+        row[m[j]] = v[j][q];
+      }
+    }
 }
 
-// the 65 column FFTs: warp w owns columns w + 16 c (c < 4) two at a time,
-// and warp 0 also column 64
+// the 65 column FFTs as 64 slots: warp w owns the slots w + 16 c (c < 4),
+// two at a time; slot 0 (warp 0) holds columns 0 and 64
 template <bool INVERSE>
 __device__ __forceinline__ void all_columns(float2* buf, const TwTab& T) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int c = 0; c < 4; c += 2) {
     const int m[2] = {warp + kWarps * c, warp + kWarps * (c + 1)};
-    columns_inplace<2, INVERSE>(buf, m, T, lane);
-  }
-  if (warp == 0) {
-    const int m[1] = {64};
-    columns_inplace<1, INVERSE>(buf, m, T, lane);
+    if (warp == 0 && c == 0)
+      columns_inplace<2, INVERSE, true>(buf, m, T, lane);
+    else
+      columns_inplace<2, INVERSE, false>(buf, m, T, lane);
   }
 }
 
@@ -379,19 +445,33 @@ __device__ void r2c_2d(float2* buf, const TwTab& T) {
   __syncthreads();
 }
 
-// columns c0 .. c0+J-1 of this warp (m = warp + 16 c): acc += FFT(buf) conj(k^)
-template <int J>
+// column slots c0, c0 + 1 of this warp (m = warp + 16 c): acc += FFT(buf)
+// conj(k^); with DN, slot 0 (columns 0 and 64)
+template <bool DN>
 __device__ __forceinline__ void columns_accumulate(const float2* buf, float2* acc,
                                                    const SpecRegs& kr, int c0, const TwTab& T,
                                                    int warp, int lane) {
-  float2 v[J][4];
+  float2 v[2][4];
 #pragma unroll
-  for (int j = 0; j < J; ++j)
+  for (int j = 0; j < 2; ++j)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[j][q] = buf[(32 * q + lane) * kFP + warp + kWarps * (c0 + j)];
-  warp_fft_dif<J>(v, T, lane);
+    for (int q = 0; q < 4; ++q) {
+      const float2* row = buf + (32 * q + lane) * kFP;
+      v[j][q] = DN && j == 0 ? make_float2(row[0].x, row[64].x) : row[warp + kWarps * (c0 + j)];
+    }
+  warp_fft_dif<2>(v, T, lane);
+  if (DN) {
+    float2 a[4], b[4];
+    split_dc_nyquist(v[0], a, b, lane);
 #pragma unroll
-  for (int j = 0; j < J; ++j)
+    for (int q = 0; q < 4; ++q) {
+      v[0][q] = a[q];
+      float2* o = acc + (32 * q + lane) * kFP + 64;
+      *o = cadd(*o, cmulc(b[q], kr[4][q]));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       float2* o = acc + (32 * q + lane) * kFP + warp + kWarps * (c0 + j);
@@ -404,9 +484,11 @@ __device__ __forceinline__ void columns_accumulate(const float2* buf, float2* ac
 __device__ void r2c_2d_accumulate(float2* buf, float2* acc, const SpecRegs& kr, const TwTab& T) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   r2c_rows(buf, T);
-  columns_accumulate<2>(buf, acc, kr, 0, T, warp, lane);
-  columns_accumulate<2>(buf, acc, kr, 2, T, warp, lane);
-  if (warp == 0) columns_accumulate<1>(buf, acc, kr, 4, T, warp, lane);
+  if (warp == 0)
+    columns_accumulate<true>(buf, acc, kr, 0, T, warp, lane);
+  else
+    columns_accumulate<false>(buf, acc, kr, 0, T, warp, lane);
+  columns_accumulate<false>(buf, acc, kr, 2, T, warp, lane);
   __syncthreads();
 }
 
@@ -420,7 +502,7 @@ __device__ __forceinline__ void rows_inverse(float2* buf, const int (&k)[J], con
     float2* r = buf + 2 * k[j] * kFP;
     merge_pair(r, lane);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[j][q] = r[32 * q + lane];
+    for (int q = 0; q < 4; ++q) v[j][q] = r[rsw(32 * q + lane)];
   }
   warp_ifft_dit<J>(v, T, lane);
 #pragma unroll
@@ -453,31 +535,46 @@ __device__ void c2r_2d(float2* buf, const TwTab& T, int k0 = 0, int k1 = 64) {
   c2r_rows(buf, T, k0, k1);
 }
 
-// columns c0 .. c0+J-1 of this warp: dst = IFFT(src . k^) along the column
-template <int J>
+// column slots c0, c0 + 1 of this warp: dst = IFFT(src . k^) along the
+// column; with DN, slot 0 (columns 0 and 64, real after the transform)
+template <bool DN>
 __device__ __forceinline__ void columns_product(const float2* src, float2* dst,
                                                 const SpecRegs& kr, int c0, const TwTab& T,
                                                 int warp, int lane) {
-  float2 v[J][4];
+  float2 v[2][4];
 #pragma unroll
-  for (int j = 0; j < J; ++j)
+  for (int j = 0; j < 2; ++j)
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      v[j][q] = cmul(src[(32 * q + lane) * kFP + warp + kWarps * (c0 + j)], kr[c0 + j][q]);
-  warp_ifft_dit<J>(v, T, lane);
+    for (int q = 0; q < 4; ++q) {
+      const float2* row = src + (32 * q + lane) * kFP;
+      v[j][q] = DN && j == 0
+                    ? pack_dc_nyquist(cmul(row[0], kr[0][q]), cmul(row[64], kr[4][q]))
+                    : cmul(row[warp + kWarps * (c0 + j)], kr[c0 + j][q]);
+    }
+  warp_ifft_dit<2>(v, T, lane);
 #pragma unroll
-  for (int j = 0; j < J; ++j)
+  for (int j = 0; j < 2; ++j)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) dst[(32 * q + lane) * kFP + warp + kWarps * (c0 + j)] = v[j][q];
+    for (int q = 0; q < 4; ++q) {
+      float2* row = dst + (32 * q + lane) * kFP;
+      if (DN && j == 0) {
+        row[0] = make_float2(v[0][q].x, 0.f);
+        row[64] = make_float2(v[0][q].y, 0.f);
+      } else {
+        row[warp + kWarps * (c0 + j)] = v[j][q];
+      }
+    }
 }
 
 // dst = C2R(src . k^) (unscaled), rows of the pairs [k0, 64); src is left intact
 __device__ void c2r_2d_product(const float2* src, float2* dst, const SpecRegs& kr,
                                const TwTab& T, int k0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  columns_product<2>(src, dst, kr, 0, T, warp, lane);
-  columns_product<2>(src, dst, kr, 2, T, warp, lane);
-  if (warp == 0) columns_product<1>(src, dst, kr, 4, T, warp, lane);
+  if (warp == 0)
+    columns_product<true>(src, dst, kr, 0, T, warp, lane);
+  else
+    columns_product<false>(src, dst, kr, 0, T, warp, lane);
+  columns_product<false>(src, dst, kr, 2, T, warp, lane);
   __syncthreads();
   c2r_rows(dst, T, k0, 64);
 }
@@ -524,16 +621,18 @@ __device__ void region_async(float* stg, const float* plane, const Geom& g, int 
 // complete after cp_async_wait_all and a CTA barrier
 __device__ void region_async_packed(float2* buf, const float* plane, const Geom& g, int r0,
                                     int c0) {
+  // warp w copies the row pairs w, w + 16, ...; lane 2 c + e takes row
+  // 2k + e, column c (+ 16 per step), so a warp writes 32 consecutive words
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* bf = reinterpret_cast<float*>(buf);
-  for (int P = warp; P < kFT; P += kFThreads / 32) {
-    const int i = r0 + P;
+  for (int k = warp; k < kFT / 2; k += kWarps) {
+    const int P = 2 * k + (lane & 1), i = r0 + P;
     const bool row_in = i >= 0 && i < g.H;
     const float* src = plane + (long long)(g.B + i) * g.P + g.B + c0;
-    float* dst = bf + 2 * ((P >> 1) * 2 * kFP) + (P & 1);
-#pragma unroll
-    for (int c = 0; c < kFT / 32; ++c) {
-      const int Q = lane + 32 * c, j = c0 + Q;
+    float* dst = bf + 2 * (2 * k * kFP) + (lane & 1);
+#pragma unroll 8
+    for (int c = 0; c < kFT / 16; ++c) {
+      const int Q = (lane >> 1) + 16 * c, j = c0 + Q;
       if (row_in && j >= 0 && j < g.W)
         cp_async4(dst + 2 * Q, src + Q);
       else
@@ -580,26 +679,49 @@ __global__ void __launch_bounds__(kFThreads, 1)
   }
 }
 
+// column slot m of c2r_2d_phase_sum (DN: slot 0, columns 0 and 64)
+template <bool DN>
+__device__ __forceinline__ void phase_sum_column(const float2* xs, const float2* kt, int R2,
+                                                 float2* dst, const TwTab& T, int m, int lane) {
+  const int per = kFT * kFBins;
+  float2 v[1][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[0][q] = make_float2(0.f, 0.f);
+  for (int ph = 0; ph < R2; ++ph) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int o = ph * per + m * kFT + 32 * q + lane;
+      if (DN) {
+        const int o64 = o + 64 * kFT;
+        v[0][q] = cadd(v[0][q], pack_dc_nyquist(cmul(xs[o], kt[o]), cmul(xs[o64], kt[o64])));
+      } else {
+        v[0][q] = cadd(v[0][q], cmul(xs[o], kt[o]));
+      }
+    }
+  }
+  warp_ifft_dit<1>(v, T, lane);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float2* row = dst + (32 * q + lane) * kFP;
+    if (DN) {
+      row[0] = make_float2(v[0][q].x, 0.f);
+      row[64] = make_float2(v[0][q].y, 0.f);
+    } else {
+      row[m] = v[0][q];
+    }
+  }
+}
+
 // r > 1: dst = C2R(sum_phi x^_phi . k^_phi) with both spectra read from
 // global memory (x^ from this tile's scratch, L2-resident), column by column
 __device__ void c2r_2d_phase_sum(const float2* xs, const float2* kt, int R2, float2* dst,
                                  const TwTab& T, int k0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int per = kFT * kFBins;
-  for (int m = warp; m < kFBins; m += kWarps) {
-    float2 v[1][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[0][q] = make_float2(0.f, 0.f);
-    for (int ph = 0; ph < R2; ++ph) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int o = ph * per + m * kFT + 32 * q + lane;
-        v[0][q] = cadd(v[0][q], cmul(xs[o], kt[o]));
-      }
-    }
-    warp_ifft_dit<1>(v, T, lane);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dst[(32 * q + lane) * kFP + m] = v[0][q];
+  for (int m = warp; m < 64; m += kWarps) {  // column slots; slot 0: columns 0 and 64
+    if (m == 0)
+      phase_sum_column<true>(xs, kt, R2, dst, T, m, lane);
+    else
+      phase_sum_column<false>(xs, kt, R2, dst, T, m, lane);
   }
   __syncthreads();
   c2r_rows(dst, T, k0, 64);
@@ -694,25 +816,52 @@ __global__ void __launch_bounds__(kFThreads, 1)
   fft_forward_tile(s, a, blockIdx.y, blockIdx.x, blockIdx.y * gridDim.x + blockIdx.x, fsm, T);
 }
 
+// column slot m of r2c_2d_accumulate_phases (DN: slot 0, columns 0 and 64)
+template <bool DN>
+__device__ __forceinline__ void accumulate_phases_column(const float2* buf, float2* acc,
+                                                         const float2* kt, int R2,
+                                                         const TwTab& T, int m, int lane) {
+  const int per = kFT * kFBins;
+  float2 v[1][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float2* row = buf + (32 * q + lane) * kFP;
+    v[0][q] = DN ? make_float2(row[0].x, row[64].x) : row[m];
+  }
+  warp_fft_dif<1>(v, T, lane);
+  if (DN) {
+    float2 a[4], b[4];
+    split_dc_nyquist(v[0], a, b, lane);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[0][q] = a[q];
+    for (int ph = 0; ph < R2; ++ph) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int o = ph * per + 64 * kFT + 32 * q + lane;
+        acc[o] = cadd(acc[o], cmulc(b[q], kt[o]));
+      }
+    }
+  }
+  for (int ph = 0; ph < R2; ++ph) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int o = ph * per + m * kFT + 32 * q + lane;
+      acc[o] = cadd(acc[o], cmulc(v[0][q], kt[o]));
+    }
+  }
+}
+
 // r > 1: acc_phi += FFT(buf) conj(k^_phi) for every phase, accumulators in
 // this tile's scratch (column by column, each element one lane's)
 __device__ void r2c_2d_accumulate_phases(float2* buf, float2* acc, const float2* kt, int R2,
                                          const TwTab& T) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int per = kFT * kFBins;
   r2c_rows(buf, T);
-  for (int m = warp; m < kFBins; m += kWarps) {
-    float2 v[1][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[0][q] = buf[(32 * q + lane) * kFP + m];
-    warp_fft_dif<1>(v, T, lane);
-    for (int ph = 0; ph < R2; ++ph) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int o = ph * per + m * kFT + 32 * q + lane;
-        acc[o] = cadd(acc[o], cmulc(v[0][q], kt[o]));
-      }
-    }
+  for (int m = warp; m < 64; m += kWarps) {  // column slots; slot 0: columns 0 and 64
+    if (m == 0)
+      accumulate_phases_column<true>(buf, acc, kt, R2, T, m, lane);
+    else
+      accumulate_phases_column<false>(buf, acc, kt, R2, T, m, lane);
   }
   __syncthreads();
 }
