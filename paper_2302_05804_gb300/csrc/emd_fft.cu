@@ -70,13 +70,11 @@ __device__ __forceinline__ int rev5(int m) { return (int)(__brev((unsigned)m) >>
 //   lane2[l]    w[2 l] (second stage)
 //   xs[k][l]    the twiddle of the cross-lane stage on lane bit k (span
 //               2^k): w[(l mod 2^k) 64 / 2^k], negated on the lanes whose bit
-//               k is set (see warp_fft_dif)
-//   xu[k][l]    the same, not negated (warp_ifft_dit)
+//               k is set (see warp_fft_dif and warp_ifft_dit)
 struct TwTab {
   float2 w[64];
   float2 lane2[32];
   float2 xs[5][32];
-  float2 xu[5][32];
 };
 
 __device__ __forceinline__ float2 twiddle(int k) {
@@ -86,18 +84,15 @@ __device__ __forceinline__ float2 twiddle(int k) {
 }
 
 __device__ __forceinline__ void init_twiddles(TwTab& T) {
-  for (int e = threadIdx.x; e < 64 + 32 + 10 * 32; e += blockDim.x) {
+  for (int e = threadIdx.x; e < 64 + 32 + 5 * 32; e += blockDim.x) {
     if (e < 64) {
       T.w[e] = twiddle(e);
     } else if (e < 96) {
       T.lane2[e - 64] = twiddle(2 * (e - 64));
     } else {
-      const int k = ((e - 96) >> 5) % 5, l = (e - 96) & 31, S = 1 << k;
+      const int k = (e - 96) >> 5, l = (e - 96) & 31, S = 1 << k;
       const float2 w = twiddle((l & (S - 1)) * (64 >> k));
-      if (e < 96 + 5 * 32)
-        T.xs[k][l] = (l & S) ? make_float2(-w.x, -w.y) : w;
-      else
-        T.xu[k][l] = w;
+      T.xs[k][l] = (l & S) ? make_float2(-w.x, -w.y) : w;
     }
   }
   __syncthreads();
@@ -171,36 +166,34 @@ __device__ __forceinline__ void warp_fft_dif(float2 (&v)[J][4], const TwTab& T, 
   dif_exchange_stage<J, 0, 1>(v, T, lane);
 }
 
-// The inverse stage of dif_exchange_stage (conjugate twiddle, unscaled): the
-// butterfly on the lane's own slot pair, (a + b t*, a - b t*), then the same
-// exchange of lane bit K with slot bit SB, which undoes itself.
+// The inverse stage of dif_exchange_stage (conjugate twiddle t*, unscaled):
+// the butterfly on the lane's own slot pair, (a + b t*, a - b t*), then the
+// same exchange of lane bit K with slot bit SB, which undoes itself. With
+// the signed twiddle s (= -t on the upper lane) and c = b s*, the lower lane
+// holds (a + c, a - c) and the upper (a - c, a + c): every lane keeps a + c,
+// sends a - c, and puts the received value in its other slot.
 template <int J, int K, int SB>
 __device__ __forceinline__ void dit_exchange_stage(float2 (&v)[J][4], const TwTab& T, int lane) {
   const bool lower = ((lane >> K) & 1) == 0;
-  const float2 tc = conjf2(T.xu[K][lane]);
+  const float2 sc = conjf2(T.xs[K][lane]);
 #pragma unroll
   for (int pr = 0; pr < 2; ++pr) {
     const int q0 = SB == 1 ? pr : 2 * pr, q1 = q0 | (1 << SB);
-    float2 snd[J], o[J];
+    float2 keep[J], o[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-      const float2 bt = K == 0 ? v[j][q1] : cmul(v[j][q1], tc);
+      const float2 b = v[j][q1];
+      const float2 c = K == 0 ? make_float2(sc.x * b.x, sc.x * b.y) : cmul(b, sc);
       const float2 a = v[j][q0];
-      v[j][q0] = cadd(a, bt);
-      v[j][q1] = csub(a, bt);
-      snd[j] = lower ? v[j][q1] : v[j][q0];
+      keep[j] = cadd(a, c);
+      const float2 snd = csub(a, c);
+      o[j].x = __shfl_xor_sync(0xffffffffu, snd.x, 1 << K);
+      o[j].y = __shfl_xor_sync(0xffffffffu, snd.y, 1 << K);
     }
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-      o[j].x = __shfl_xor_sync(0xffffffffu, snd[j].x, 1 << K);
-      o[j].y = __shfl_xor_sync(0xffffffffu, snd[j].y, 1 << K);
-    }
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-      if (lower)
-        v[j][q1] = o[j];
-      else
-        v[j][q0] = o[j];
+      v[j][q0] = lower ? keep[j] : o[j];
+      v[j][q1] = lower ? o[j] : keep[j];
     }
   }
 }
