@@ -104,6 +104,10 @@ struct emd_ctx {
   float* fft_w = nullptr;
   float* fft_w2 = nullptr;
   float2* fft_scratch = nullptr;
+  float2* fft_partials = nullptr;  // split launch (r = 1 Gaussian): partial accumulators
+  int* fft_counters = nullptr;     // and per-tile arrival counts
+  int fft_split_ctas = 0;          // persistent CTAs of the split launch (one per SM)
+  int fft_bound = -1;              // noise model the pointers are laid out for (-1: none)
   bool fft_ready = false;
   bool frames = false;
   int prec = EMD_PREC_FP32;
@@ -262,6 +266,21 @@ size_t emd_ctx_bytes(int H, int W, int n, int psf_k, int r) {
   return make_layout(s).total;
 }
 
+namespace {
+
+// SMs of the current device, 0 if there is none
+int current_device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms;
+}
+
+}  // namespace
+
 size_t emd_ctx_bytes_precision(int H, int W, int n, int psf_k, int r, int mode) {
   Shape s;
   const char* why = nullptr;
@@ -269,7 +288,8 @@ size_t emd_ctx_bytes_precision(int H, int W, int n, int psf_k, int r, int mode) 
   const size_t base = make_layout(s).total;
   if (mode == EMD_PREC_FP32) return base + emd::halo_buffer_bytes(s, false);
   if (mode == EMD_PREC_FP32_PAIR) return base;
-  if (mode == EMD_PREC_FFT_FP32) return base + emd::fft_buffer_bytes(s, false);
+  if (mode == EMD_PREC_FFT_FP32)
+    return base + emd::fft_buffer_bytes(s, false, current_device_sms());
   if (mode < EMD_PREC_FP32 || mode > EMD_PREC_FFT_FP32) return 0;
   emd::TcShape t;
   if (!emd::make_tc_shape(s, mode, &t, &why)) return 0;
@@ -354,28 +374,35 @@ int emd_set_stream(emd_ctx* c, void* stream) {
 
 namespace {
 
-// the FFT form's buffers, sized for the context's noise model (the
-// heavy-tailed form adds the w2 planes and a larger per-tile scratch);
-// a buffer that grows is re-made and its PSF spectra recomputed
+// the FFT form's buffers, sized and laid out for the context's noise model
+// (the heavy-tailed form adds the w2 planes and a larger per-tile scratch;
+// r = 1 Gaussian adds the split launch's partial accumulators, one per SM,
+// and per-tile flags); a buffer that grows is re-made, one whose layout
+// changes is re-bound (its flags cleared), and either way the PSF spectra
+// are recomputed
 int ensure_fft_arena(emd_ctx* c) {
   const bool student = c->noise == EMD_NOISE_STUDENT_T;
-  const size_t need = emd::fft_buffer_bytes(c->s, student);
-  if (c->fft_arena && c->fft_bytes >= need) return EMD_OK;
-  if (c->fft_arena) {
-    CK(cudaStreamSynchronize(c->st));
-    cudaFree(c->fft_arena);
-    c->fft_arena = nullptr;
-    c->fft_bytes = 0;
+  if (c->fft_split_ctas == 0) c->fft_split_ctas = current_device_sms();
+  const size_t need = emd::fft_buffer_bytes(c->s, student, c->fft_split_ctas);
+  if (!c->fft_arena || c->fft_bytes < need) {
+    if (c->fft_arena) {
+      CK(cudaStreamSynchronize(c->st));
+      cudaFree(c->fft_arena);
+      c->fft_arena = nullptr;
+      c->fft_bytes = 0;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, need) != cudaSuccess) {
+      cudaGetLastError();
+      set_err("cudaMalloc(%zu) for the FFT path failed", need);
+      return EMD_ENOMEM;
+    }
+    CK(cudaMemsetAsync(p, 0, need, c->st));
+    c->fft_arena = static_cast<char*>(p);
+    c->fft_bytes = need;
+    c->fft_bound = -1;
   }
-  void* p = nullptr;
-  if (cudaMalloc(&p, need) != cudaSuccess) {
-    cudaGetLastError();
-    set_err("cudaMalloc(%zu) for the FFT path failed", need);
-    return EMD_ENOMEM;
-  }
-  CK(cudaMemsetAsync(p, 0, need, c->st));
-  c->fft_arena = static_cast<char*>(p);
-  c->fft_bytes = need;
+  if (c->fft_bound == (int)student) return EMD_OK;
   const size_t spec =
       ((size_t)c->s.n * c->s.R2 * 128 * 65 * sizeof(float2) + 255) & ~(size_t)255;
   c->fft_spec = reinterpret_cast<float2*>(c->fft_arena);
@@ -383,6 +410,18 @@ int ensure_fft_arena(emd_ctx* c) {
   c->fft_w2 = student ? reinterpret_cast<float*>(c->fft_arena + emd::fft_w2_offset(c->s)) : nullptr;
   c->fft_scratch =
       reinterpret_cast<float2*>(c->fft_arena + emd::fft_scratch_offset(c->s, student));
+  const bool parts = emd::fft_buffer_bytes(c->s, student, c->fft_split_ctas) >
+                     emd::fft_buffer_bytes(c->s, student, 0);
+  c->fft_partials =
+      parts ? reinterpret_cast<float2*>(c->fft_arena + emd::fft_split_offset(c->s, student))
+            : nullptr;
+  c->fft_counters = parts ? reinterpret_cast<int*>(c->fft_arena + emd::fft_counters_offset(
+                                                                      c->s, student, c->fft_split_ctas))
+                          : nullptr;
+  if (c->fft_counters)
+    CK(cudaMemsetAsync(c->fft_counters, 0,
+                       need - emd::fft_counters_offset(c->s, student, c->fft_split_ctas), c->st));
+  c->fft_bound = (int)student;
   c->fft_ready = false;
   return EMD_OK;
 }
@@ -710,6 +749,10 @@ int emd_iterate(emd_ctx* c, int k) {
       L.w = c->fft_w;
       L.spec = c->fft_spec;
       L.scratch = c->fft_scratch;
+      L.partials = c->fft_partials;
+      L.counters = c->fft_counters;
+      L.split_ctas = c->fft_split_ctas;
+      L.err = c->err;
       if (c->noise == EMD_NOISE_STUDENT_T) {
         L.y = c->y;
         L.w2 = c->fft_w2;

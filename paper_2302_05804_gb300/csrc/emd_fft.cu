@@ -720,10 +720,11 @@ __device__ void c2r_2d_phase_sum(const float2* xs, const float2* kt, int R2, flo
   c2r_rows(dst, T, k0, 64);
 }
 
-// the forward pass of one tile (tile index `tile` = ty gx + tx of its job);
-// starts and ends at a CTA barrier, so a persistent CTA can run many
+// the forward pass of one tile (tile index `tile` = ty gx + tx of its job)
+// for the exposures [t_begin, t_end); starts and ends at a CTA barrier, so
+// a persistent CTA can run many
 __device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int tx, int tile,
-                                 float2* fsm, const TwTab& T) {
+                                 float2* fsm, const TwTab& T, int t_begin, int t_end) {
   float2* xh = fsm;
   float2* wk = fsm + kFBuf;
   float* stg = reinterpret_cast<float*>(fsm + 2 * kFBuf);  // 128 x 128 floats
@@ -735,7 +736,7 @@ __device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int
   float2* xs = a.scratch + (long long)tile * (a.nu > 0.f ? 2 * R2 : R2) * per;
   SpecRegs kr;
   if (R2 == 1) {
-    load_spec_cols(kr, a.spec);
+    load_spec_cols(kr, a.spec + (long long)t_begin * per);
     region_async(stg, a.x, g, i0 - hc, j0 - hc);
     pack_region(xh, stg);
     r2c_2d(xh, T);
@@ -752,7 +753,7 @@ __device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int
       __syncthreads();
     }
   }
-  for (int t = 0; t < s.n; ++t) {
+  for (int t = t_begin; t < t_end; ++t) {
     // u of this exposure (B x B, row-major in stg) arrives during the
     // inverse transform
     const long long tplane = (long long)t * g.plane;
@@ -767,7 +768,7 @@ __device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int
     if (R2 == 1) {
       c2r_2d_product(xh, wk, kr, T, hc);  // z is read at rows [2 hc, 128)
       // the next spectrum loads during the epilogue and the next column pass
-      if (t + 1 < s.n) load_spec_cols(kr, a.spec + (long long)(t + 1) * per);
+      if (t + 1 < t_end) load_spec_cols(kr, a.spec + (long long)(t + 1) * per);
     } else {
       c2r_2d_phase_sum(xs, a.spec + (long long)t * R2 * per, R2, wk, T, hc);
     }
@@ -806,7 +807,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
   extern __shared__ float2 fsm[];
   __shared__ TwTab T;
   init_twiddles(T);
-  fft_forward_tile(s, a, blockIdx.y, blockIdx.x, blockIdx.y * gridDim.x + blockIdx.x, fsm, T);
+  fft_forward_tile(s, a, blockIdx.y, blockIdx.x, blockIdx.y * gridDim.x + blockIdx.x, fsm, T, 0,
+                   s.n);
 }
 
 // column slot m of r2c_2d_accumulate_phases (DN: slot 0, columns 0 and 64)
@@ -889,12 +891,67 @@ __device__ void update_phase(const float2* sh, const float2* num, const FftLaunc
   });
 }
 
+// Equal ranges: CTA b of P takes the units [b U / P, (b+1) U / P) of U.
+__device__ __forceinline__ long long split_start(long long U, int P, int b) {
+  return (long long)b * U / P;
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+constexpr unsigned kPartPolls = 1u << 23;  // x ~0.3 us per poll: seconds, not a hang
+
+// A tile cut between two CTAs of a split launch: the head (exposures
+// [0, k)) is the first thing its CTA does; it stores the accumulator (sh)
+// in the CTA's slot and raises the tile's flag. The tail (exposures
+// [k, n)) is the last thing the other CTA does; it waits (bounded) for the
+// flag, starts from the stored accumulator and finishes the tile, so the
+// exposures are summed in the order a whole-tile CTA sums them (the same
+// bits). A wait that gives up sets the timeout bit of the error word.
+__device__ void adjoint_publish_head(const FftLaunch& a, int tile, const float2* sh) {
+  float2* slot = a.partials + (long long)blockIdx.x * kFBuf;
+  for (int e = threadIdx.x; e < kFBuf; e += blockDim.x) slot[e] = sh[e];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) st_release_gpu(a.counters + tile, 1);
+}
+
+__device__ void adjoint_resume_tail(const FftLaunch& a, int tile, float2* sh, int head_cta) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    unsigned i = 0;
+    while (i < kPartPolls && ld_acquire_gpu(a.counters + tile) == 0) {
+      __nanosleep(200);
+      ++i;
+    }
+    ok = i < kPartPolls;
+    if (ok)
+      a.counters[tile] = 0;  // ready for the next launch
+    else
+      atomicOr(a.err, kErrTimeout);
+  }
+  __syncthreads();
+  const float2* slot = a.partials + (long long)head_cta * kFBuf;
+  for (int e = threadIdx.x; e < kFBuf; e += blockDim.x)
+    sh[e] = ok ? __ldcg(slot + e) : make_float2(0.f, 0.f);
+}
+
 // the adjoint pass and the update of one tile; starts and ends at a CTA
 // barrier. r = 1 Gaussian: one accumulator in shared memory. Otherwise the
 // accumulators live in the tile's scratch: R2 for Den, and for Student-t R2
-// more for N' (the w2 planes, transformed the same way).
+// more for N' (the w2 planes, transformed the same way). A split launch
+// (r = 1 Gaussian) runs the sources [k_begin, k_end) of a cut tile: part 1
+// the head (published, no update), part 2 the tail (resumed, then the
+// update, its head computed by CTA head_cta); part 0 is the whole tile.
+enum { kWhole = 0, kHead = 1, kTail = 2 };
 __device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int tx, int tile,
-                                 float2* fsm, const TwTab& T) {
+                                 float2* fsm, const TwTab& T, int k_begin = 0, int k_end = -1,
+                                 int part = kWhole, int head_cta = 0) {
   float2* sh = fsm;
   float2* wk = fsm + kFBuf;
   // the w regions arrive straight in the packed layout, alternating between
@@ -910,27 +967,32 @@ __device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int
   float2* acc = a.scratch + (long long)tile * nacc * per;
   // sources in order: w_0 (, w2_0), w_1 (, w2_1), ...
   const int nsrc = student ? 2 * s.n : s.n;
+  if (k_end < 0) k_end = nsrc;
   auto src_plane = [&](int k) -> const float* {
     return student ? ((k & 1) ? a.w2 : a.w) + (long long)(k >> 1) * g.plane
                    : a.w + (long long)k * g.plane;
   };
   SpecRegs kr;
   if (in_smem) {
-    for (int e = threadIdx.x; e < kFBuf; e += blockDim.x) sh[e] = make_float2(0.f, 0.f);
-    load_spec_cols(kr, a.spec);
+    if (part == kTail)
+      adjoint_resume_tail(a, tile, sh, head_cta);
+    else
+      for (int e = threadIdx.x; e < kFBuf; e += blockDim.x) sh[e] = make_float2(0.f, 0.f);
+    load_spec_cols(kr, a.spec + (long long)k_begin * per);
   } else {
     for (int e = threadIdx.x; e < nacc * per; e += blockDim.x) acc[e] = make_float2(0.f, 0.f);
   }
-  region_async_packed(wbuf[0], src_plane(0), g, i0 - hc, j0 - hc);
-  for (int k = 0; k < nsrc; ++k) {
+  region_async_packed(wbuf[k_begin & 1], src_plane(k_begin), g, i0 - hc, j0 - hc);
+  for (int k = k_begin; k < k_end; ++k) {
     float2* cur = wbuf[k & 1];
     cp_async_wait_all();
     __syncthreads();  // region k landed; every reader of the other buffer is done
     // the next source's region arrives during this transform
-    if (k + 1 < nsrc) region_async_packed(wbuf[(k + 1) & 1], src_plane(k + 1), g, i0 - hc, j0 - hc);
+    if (k + 1 < k_end)
+      region_async_packed(wbuf[(k + 1) & 1], src_plane(k + 1), g, i0 - hc, j0 - hc);
     if (in_smem) {
       r2c_2d_accumulate(cur, sh, kr, T);
-      if (k + 1 < nsrc) load_spec_cols(kr, a.spec + (long long)(k + 1) * per);
+      if (k + 1 < k_end) load_spec_cols(kr, a.spec + (long long)(k + 1) * per);
     } else {
       const int t = student ? k >> 1 : k, base = student ? (k & 1) * R2 : 0;
       r2c_2d_accumulate_phases(cur, acc + (long long)base * per, a.spec + (long long)t * R2 * per,
@@ -938,8 +1000,12 @@ __device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int
     }
   }
   if (in_smem) {
-    c2r_2d(sh, T, 0, (B + 1) / 2);  // Den is read at rows [0, B)
-    update_phase(sh, nullptr, a, g, 0, i0, j0, B);
+    if (part == kHead) {
+      adjoint_publish_head(a, tile, sh);
+    } else {
+      c2r_2d(sh, T, 0, (B + 1) / 2);  // Den is read at rows [0, B)
+      update_phase(sh, nullptr, a, g, 0, i0, j0, B);
+    }
   } else {
     for (int ph = 0; ph < R2; ++ph) {
       for (int e = threadIdx.x; e < per; e += blockDim.x) {
@@ -963,6 +1029,54 @@ __global__ void __launch_bounds__(kFThreads, 1)
   __shared__ TwTab T;
   init_twiddles(T);
   fft_adjoint_tile(s, a, blockIdx.y, blockIdx.x, blockIdx.y * gridDim.x + blockIdx.x, fsm, T);
+}
+
+// Split forms (r = 1 Gaussian, at least as many tiles as CTAs): P =
+// a.split_ctas persistent CTAs, CTA b taking the (tile, exposure) units
+// [b U / P, (b+1) U / P) of the U = tiles x n, tile-major, so that every
+// CTA does the same work and the last wave of whole tiles leaves no SM
+// idle. A range holds at least n units, so it cuts at most its first and
+// its last tile. The forward pass recomputes x^ for a tile it shares.
+__global__ void __launch_bounds__(kFThreads, 1)
+    fft_forward_split_kernel(const Shape s, const FftLaunch a, int gxt, int tiles) {
+  extern __shared__ float2 fsm[];
+  __shared__ TwTab T;
+  init_twiddles(T);
+  const int P = a.split_ctas, n = s.n;
+  const long long U = (long long)tiles * n;
+  const long long u_end = split_start(U, P, blockIdx.x + 1);
+  for (long long u = split_start(U, P, blockIdx.x); u < u_end;) {
+    const int tile = (int)(u / n), t0 = (int)(u % n);
+    const int t1 = (int)min((long long)n, t0 + (u_end - u));
+    fft_forward_tile(s, a, tile / gxt, tile % gxt, tile, fsm, T, t0, t1);
+    u += t1 - t0;
+  }
+}
+
+// The adjoint: the head of the last tile first, then the whole tiles, then
+// the tail of the first tile, whose head the previous CTA ran first.
+__global__ void __launch_bounds__(kFThreads, 1)
+    fft_adjoint_split_kernel(const Shape s, const FftLaunch a, int gxt, int tiles) {
+  extern __shared__ float2 fsm[];
+  __shared__ TwTab T;
+  init_twiddles(T);
+  const int P = a.split_ctas, n = s.n;
+  const long long U = (long long)tiles * n;
+  const long long u0 = split_start(U, P, blockIdx.x), u1 = split_start(U, P, blockIdx.x + 1);
+  const int first = (int)(u0 / n), last = (int)((u1 - 1) / n);
+  const int head_k = (int)(u1 % n), tail_k = (int)(u0 % n);
+  const int w0 = tail_k != 0 ? first + 1 : first, w1 = head_k != 0 ? last : last + 1;
+  // items: [head of last], whole tiles w0 .. w1-1, [tail of first]
+  const int nh = head_k != 0, nw = w1 - w0, nt = tail_k != 0;
+  for (int i = 0; i < nh + nw + nt; ++i) {
+    int tile = first, k0 = tail_k, k1 = n, part = kTail;
+    if (i < nh) {
+      tile = last, k0 = 0, k1 = head_k, part = kHead;
+    } else if (i < nh + nw) {
+      tile = w0 + i - nh, k0 = 0, part = kWhole;
+    }
+    fft_adjoint_tile(s, a, tile / gxt, tile % gxt, tile, fsm, T, k0, k1, part, blockIdx.x - 1);
+  }
 }
 
 // Persistent forms for a batch of FFT jobs: every CTA claims (job, tile)
@@ -990,7 +1104,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
     const int2 w = items[item];
     const FftBatchJob& J = jobs[w.x];
     if (J.remaining <= 0) continue;
-    fft_forward_tile(J.s, J.a[J.cur], w.y / J.gxt, w.y % J.gxt, w.y, fsm, T);
+    fft_forward_tile(J.s, J.a[J.cur], w.y / J.gxt, w.y % J.gxt, w.y, fsm, T, 0, J.s.n);
   }
 }
 
@@ -1041,9 +1155,25 @@ size_t fft_scratch_offset(const Shape& s, bool student) {
   return fft_w2_offset(s) + (student ? wpl : 0);
 }
 
-size_t fft_buffer_bytes(const Shape& s, bool student) {
+size_t fft_split_offset(const Shape& s, bool student) {
   const int nacc = student ? 2 * s.R2 : (s.R2 > 1 ? s.R2 : 0);
-  return fft_scratch_offset(s, student) + fft_tiles(s) * nacc * kFT * kFBins * sizeof(float2);
+  const size_t scratch = fft_tiles(s) * nacc * kFT * kFBins * sizeof(float2);
+  return (fft_scratch_offset(s, student) + scratch + 255) & ~(size_t)255;
+}
+
+static bool fft_splits_adjoint(const Shape& s, bool student) { return s.R2 == 1 && !student; }
+
+size_t fft_counters_offset(const Shape& s, bool student, int split_ctas) {
+  const size_t parts = fft_splits_adjoint(s, student) && split_ctas > 0
+                           ? (size_t)split_ctas * kFBuf * sizeof(float2)
+                           : 0;
+  return fft_split_offset(s, student) + parts;
+}
+
+size_t fft_buffer_bytes(const Shape& s, bool student, int split_ctas) {
+  const size_t counters =
+      fft_splits_adjoint(s, student) && split_ctas > 0 ? fft_tiles(s) * sizeof(int) : 0;
+  return fft_counters_offset(s, student, split_ctas) + counters;
 }
 
 // two transform buffers and a 128 x 128 float staging area
@@ -1090,13 +1220,28 @@ cudaError_t launch_fft_iter(const Shape& s, const FftLaunch& a, cudaStream_t st)
   const size_t smem = fft_smem_bytes();
   cudaError_t e = allow_max_dynamic_smem((const void*)fft_forward_kernel);
   if (e == cudaSuccess) e = allow_max_dynamic_smem((const void*)fft_adjoint_kernel);
+  if (e == cudaSuccess) e = allow_max_dynamic_smem((const void*)fft_forward_split_kernel);
+  if (e == cudaSuccess) e = allow_max_dynamic_smem((const void*)fft_adjoint_split_kernel);
   if (e != cudaSuccess) return e;
   const int B = fft_tile_side(s);
   const dim3 grid((s.g.W + B - 1) / B, (s.g.H + B - 1) / B);
-  fft_forward_kernel<<<grid, kFThreads, smem, st>>>(s, a);
+  // the split forms: r = 1 (the forward pass of r > 1 keeps x^ in the
+  // tile's scratch), Gaussian (the partial slots), at least as many tiles
+  // as CTAs
+  const bool split = s.R2 == 1 && a.nu <= 0.f && a.split_ctas > 0 && a.partials &&
+                     a.counters && a.err && (long long)fft_tiles(s) >= a.split_ctas;
+  if (split)
+    fft_forward_split_kernel<<<a.split_ctas, kFThreads, smem, st>>>(s, a, (int)grid.x,
+                                                                     (int)fft_tiles(s));
+  else
+    fft_forward_kernel<<<grid, kFThreads, smem, st>>>(s, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  fft_adjoint_kernel<<<grid, kFThreads, smem, st>>>(s, a);
+  if (split)
+    fft_adjoint_split_kernel<<<a.split_ctas, kFThreads, smem, st>>>(s, a, (int)grid.x,
+                                                                     (int)fft_tiles(s));
+  else
+    fft_adjoint_kernel<<<grid, kFThreads, smem, st>>>(s, a);
   return cudaGetLastError();
 }
 

@@ -21,8 +21,21 @@ struct FftLaunch {
   const float* y;       // Student-t: n data planes (masked pixels 0)
   float* w2;            // Student-t: n planes of u'_t y_t
   float nu;             // Student-t degrees of freedom; 0 = Gaussian
+  // split launch (r = 1, at least split_ctas tiles): split_ctas persistent
+  // CTAs take equal ranges of the (tile, exposure) units; an adjoint tile
+  // cut between two CTAs passes its head's accumulator through the head
+  // CTA's slot (partials, one per CTA) and the tile's flag (counters).
+  // split_ctas = 0: one CTA per tile.
+  float2* partials;
+  int* counters;
+  int split_ctas;
+  int* err;  // device error word (a bounded wait that gives up sets kErrTimeout)
 };
-size_t fft_buffer_bytes(const Shape& s, bool student);
+// bytes of the FFT buffer; split_ctas > 0 adds the split launch's partial
+// accumulators and counters (r = 1 Gaussian)
+size_t fft_buffer_bytes(const Shape& s, bool student, int split_ctas = 0);
+size_t fft_split_offset(const Shape& s, bool student);     // bytes before the partials
+size_t fft_counters_offset(const Shape& s, bool student, int split_ctas);
 size_t fft_smem_bytes();
 int fft_tile_side(const Shape& s);
 size_t fft_w2_offset(const Shape& s);                      // bytes before the w2 planes

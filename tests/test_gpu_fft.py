@@ -119,3 +119,43 @@ def test_fft_full_size_sampled(emd, recipe):
     xo, _, _ = oracle.em_step_at(x0, p.y, u, p.f, idx, p.r)
     got = x1.ravel()[idx].astype(np.float64)
     assert np.linalg.norm(got - xo) / np.linalg.norm(xo) <= 1e-5
+
+
+def test_fft_split_launch_matches_whole_tile_kernels_bitwise(emd):
+    """With at least as many tiles as SMs (here 18 x 18 tiles of 114 pixels,
+    K = 15) a solo FFT iteration runs the split launch: persistent CTAs take
+    equal ranges of (tile, exposure) units, and a tile cut between two CTAs
+    passes the head's accumulator to the tail, which continues the sum in
+    exposure order. The batch path runs whole tiles (one CTA per tile), and
+    its iterates match the oracle (test_gpu_batch); the two must give the
+    same bits."""
+    p = synth.make_problem("hsc", H=2048, W=2048, n=3, K=15, r=1, mask_frac=0.05,
+                           n_points=400, n_gal=8)
+    x0 = np.full((p.H, p.W), 5.0, np.float32)
+
+    def ctx():
+        d = emd.Deconvolver(p.H, p.W, p.n, p.K, p.r)
+        d.set_frames(p.y, p.v, p.f, p.mask)
+        d.set_precision(emd.EMD_PREC_FFT_FP32)
+        d.set_x(x0)
+        return d
+
+    d = ctx()
+    d.iterate(3)
+    solo = d.x()
+    d.close()
+    b = emd.emd_batch_create(2)
+    d = ctx()
+    slot = emd.emd_batch_add(b, d.ctx, 3)
+    steps = 0
+    while emd.emd_batch_step(b) == 0:
+        steps += 1
+        assert steps < 10
+    emd.emd_batch_sync(b)
+    assert emd.emd_batch_remaining(b, slot) == 0
+    batched = d.x()
+    emd.emd_batch_remove(b, slot)
+    emd.emd_batch_destroy(b)
+    d.close()
+    np.testing.assert_array_equal(solo, batched)
+    assert np.isfinite(solo).all() and (solo >= 0).all()
