@@ -138,6 +138,18 @@ def fft_flops(H, W, n, K, r, nu):
     return ffts * 2.5 * 16384 * 14 + tiles * (1 + m) * n * r * r * 6 * 128 * 65
 
 
+def fft_kernels(H, W, n, K, r, nu, sms):
+    """Names of the two kernels an FFT-form iteration launches: the split
+    forms (persistent, one CTA per SM) for r = 1 Gaussian with at least as
+    many tiles as SMs, else one CTA per tile."""
+    hc = ((K - 1) // 2 + r - 1) // r
+    B = 128 - 2 * hc
+    tiles = -(-H // B) * -(-W // B)
+    if r == 1 and nu == 0 and tiles >= sms:
+        return "fft_forward_split_kernel + fft_adjoint_split_kernel"
+    return "fft_forward_kernel + fft_adjoint_kernel"
+
+
 def bf16_peak():
     """(TFLOP/s, description) of the measured dense BF16 peak (burst)."""
     try:
@@ -147,7 +159,7 @@ def bf16_peak():
         return 1900.0, "fallback 1.9 PFLOP/s bf16 burst"
 
 
-def variant_roofline(name, p, launch_s, peak32, peak32_src):
+def variant_roofline(name, p, launch_s, peak32, peak32_src, sms):
     """Roofline record of one timed variant (same conventions as the
     headline's): FMA pipe for the direct forms, FP32 issue for the FFT form,
     the tensor pipe (executed flops) for the tensor-core forms."""
@@ -160,7 +172,7 @@ def variant_roofline(name, p, launch_s, peak32, peak32_src):
         ex = fl / launch_s / 1e12
         rec = {"bound": "alu", "achieved": ex, "peak": peak32, "unit": "TFLOP/s",
                "frac": ex / peak32, "peak_source": peak32_src,
-               "kernel": "fft_forward_kernel + fft_adjoint_kernel",
+               "kernel": fft_kernels(p.H, p.W, p.n, p.K, p.r, nu, sms),
                "fft_tflop_per_iteration": fl / 1e12,
                "direct_equivalent_tflops": flops / launch_s / 1e12}
         tr = committed_traffic("fft", "hsc") if nu == 0 else None
@@ -412,7 +424,9 @@ def run_variants(p, peak32, peak32_src, steps=5, warmup=2):
             d.close()
         out[name] = {"ms_per_iteration": ms,
                      "value": p.r * p.r * p.H * p.W * p.n / (ms / 1e3) / 1e9, "unit": UNIT,
-                     "roofline": variant_roofline(name, p, ms / 1e3, peak32, peak32_src)}
+                     "roofline": variant_roofline(name, p, ms / 1e3, peak32, peak32_src,
+                                                  torch.cuda.get_device_properties(
+                                                      torch.cuda.current_device()).multi_processor_count)}
     return out
 
 
@@ -551,7 +565,8 @@ def run_ours(args):
         traffic = committed_traffic("fft", args.workload) if args.nu == 0 else None
         roofline = {"bound": "alu", "achieved": ex, "peak": peak, "unit": "TFLOP/s",
                     "frac": ex / peak, "traffic": traffic,
-                    "kernel": "fft_forward_kernel + fft_adjoint_kernel (FP32 FFT)",
+                    "kernel": fft_kernels(p.H, p.W, p.n, p.K, p.r, args.nu,
+                                          fp32_peak(local)[2]) + " (FP32 FFT)",
                     "peak_source": peak32_src,
                     "direct_equivalent_tflops": achieved,
                     "fft_tflop_per_iteration": fl / 1e12}

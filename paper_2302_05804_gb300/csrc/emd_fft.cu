@@ -114,7 +114,7 @@ __device__ __forceinline__ void init_twiddles(TwTab& T) {
 template <int J, int K, int SB>  // lane bit K, slot bit SB
 __device__ __forceinline__ void dif_exchange_stage(float2 (&v)[J][4], const TwTab& T, int lane) {
   const bool lower = ((lane >> K) & 1) == 0;
-  const float2 t = T.xs[K][lane];
+  const float2 t = K == 0 ? make_float2(lower ? 1.f : -1.f, 0.f) : T.xs[K][lane];
 #pragma unroll
   for (int pr = 0; pr < 2; ++pr) {
     const int q0 = SB == 1 ? pr : 2 * pr, q1 = q0 | (1 << SB);
@@ -175,7 +175,7 @@ __device__ __forceinline__ void warp_fft_dif(float2 (&v)[J][4], const TwTab& T, 
 template <int J, int K, int SB>
 __device__ __forceinline__ void dit_exchange_stage(float2 (&v)[J][4], const TwTab& T, int lane) {
   const bool lower = ((lane >> K) & 1) == 0;
-  const float2 sc = conjf2(T.xs[K][lane]);
+  const float2 sc = K == 0 ? make_float2(lower ? 1.f : -1.f, 0.f) : conjf2(T.xs[K][lane]);
 #pragma unroll
   for (int pr = 0; pr < 2; ++pr) {
     const int q0 = SB == 1 ? pr : 2 * pr, q1 = q0 | (1 << SB);
@@ -474,6 +474,7 @@ __device__ __forceinline__ void columns_accumulate(const float2* buf, float2* ac
 
 // forward transform of buf (destroyed) added, times conj(spectrum), into acc:
 // acc += FFT(buf) conj(k^), the column FFTs never written back
+// (no closing barrier: the caller's next barrier orders it)
 __device__ void r2c_2d_accumulate(float2* buf, float2* acc, const SpecRegs& kr, const TwTab& T) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   r2c_rows(buf, T);
@@ -482,7 +483,6 @@ __device__ void r2c_2d_accumulate(float2* buf, float2* acc, const SpecRegs& kr, 
   else
     columns_accumulate<false>(buf, acc, kr, 0, T, warp, lane);
   columns_accumulate<false>(buf, acc, kr, 2, T, warp, lane);
-  __syncthreads();
 }
 
 // merge, inverse row FFTs of the J row pairs k[0..J)
@@ -505,12 +505,16 @@ __device__ __forceinline__ void rows_inverse(float2* buf, const int (&k)[J], con
 }
 
 // inverse transform, rows: merge and the packed row inverse FFTs of the row
-// pairs [k0, k1) (the rows a caller reads; the others are left undone), two
-// at a time per warp
-__device__ void c2r_rows(float2* buf, const TwTab& T, int k0 = 0, int k1 = 64) {
+// pairs [k0, k1) (the rows a caller reads; the others are left undone), up
+// to three at a time per warp (43 pairs: one pass); sync = false leaves the
+// closing barrier to the caller
+__device__ void c2r_rows(float2* buf, const TwTab& T, int k0 = 0, int k1 = 64, bool sync = true) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = k0 + warp; k < k1; k += 2 * kWarps) {
-    if (k + kWarps < k1) {
+  for (int k = k0 + warp; k < k1; k += 3 * kWarps) {
+    if (k + 2 * kWarps < k1) {
+      const int kk[3] = {k, k + kWarps, k + 2 * kWarps};
+      rows_inverse<3>(buf, kk, T, lane);
+    } else if (k + kWarps < k1) {
       const int kk[2] = {k, k + kWarps};
       rows_inverse<2>(buf, kk, T, lane);
     } else {
@@ -518,7 +522,7 @@ __device__ void c2r_rows(float2* buf, const TwTab& T, int k0 = 0, int k1 = 64) {
       rows_inverse<1>(buf, kk, T, lane);
     }
   }
-  __syncthreads();
+  if (sync) __syncthreads();
 }
 
 // inverse real 2D transform in place (unscaled); rows of the pairs [k0, k1)
@@ -559,7 +563,8 @@ __device__ __forceinline__ void columns_product(const float2* src, float2* dst,
     }
 }
 
-// dst = C2R(src . k^) (unscaled), rows of the pairs [k0, 64); src is left intact
+// dst = C2R(src . k^) (unscaled), rows of the pairs [k0, 64); src is left
+// intact; no closing barrier (the caller's next barrier orders it)
 __device__ void c2r_2d_product(const float2* src, float2* dst, const SpecRegs& kr,
                                const TwTab& T, int k0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -569,7 +574,7 @@ __device__ void c2r_2d_product(const float2* src, float2* dst, const SpecRegs& k
     columns_product<false>(src, dst, kr, 0, T, warp, lane);
   columns_product<false>(src, dst, kr, 2, T, warp, lane);
   __syncthreads();
-  c2r_rows(dst, T, k0, 64);
+  c2r_rows(dst, T, k0, 64, false);
 }
 
 // value of tile pixel (P, Q) after c2r_2d (unscaled)
@@ -706,7 +711,8 @@ __device__ __forceinline__ void phase_sum_column(const float2* xs, const float2*
 }
 
 // r > 1: dst = C2R(sum_phi x^_phi . k^_phi) with both spectra read from
-// global memory (x^ from this tile's scratch, L2-resident), column by column
+// global memory (x^ from this tile's scratch, L2-resident), column by
+// column; no closing barrier (the caller's next barrier orders it)
 __device__ void c2r_2d_phase_sum(const float2* xs, const float2* kt, int R2, float2* dst,
                                  const TwTab& T, int k0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -717,7 +723,7 @@ __device__ void c2r_2d_phase_sum(const float2* xs, const float2* kt, int R2, flo
       phase_sum_column<false>(xs, kt, R2, dst, T, m, lane);
   }
   __syncthreads();
-  c2r_rows(dst, T, k0, 64);
+  c2r_rows(dst, T, k0, 64, false);
 }
 
 // the forward pass of one tile (tile index `tile` = ty gx + tx of its job)
@@ -991,7 +997,7 @@ __device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int
     if (k + 1 < k_end)
       region_async_packed(wbuf[(k + 1) & 1], src_plane(k + 1), g, i0 - hc, j0 - hc);
     if (in_smem) {
-      r2c_2d_accumulate(cur, sh, kr, T);
+      r2c_2d_accumulate(cur, sh, kr, T);  // the next loop-top barrier orders it
       if (k + 1 < k_end) load_spec_cols(kr, a.spec + (long long)(k + 1) * per);
     } else {
       const int t = student ? k >> 1 : k, base = student ? (k & 1) * R2 : 0;
@@ -1000,6 +1006,7 @@ __device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int
     }
   }
   if (in_smem) {
+    __syncthreads();  // the last accumulation is complete
     if (part == kHead) {
       adjoint_publish_head(a, tile, sh);
     } else {
