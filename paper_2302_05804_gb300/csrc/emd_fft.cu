@@ -912,37 +912,39 @@ __device__ __forceinline__ void st_release_gpu(int* p, int v) {
 }
 constexpr unsigned kPartPolls = 1u << 23;  // x ~0.3 us per poll: seconds, not a hang
 
-// A tile cut between two CTAs of a split launch: the head (exposures
-// [0, k)) is the first thing its CTA does; it stores the accumulator (sh)
-// in the CTA's slot and raises the tile's flag. The tail (exposures
-// [k, n)) is the last thing the other CTA does; it waits (bounded) for the
-// flag, starts from the stored accumulator and finishes the tile, so the
-// exposures are summed in the order a whole-tile CTA sums them (the same
-// bits). A wait that gives up sets the timeout bit of the error word.
-__device__ void adjoint_publish_head(const FftLaunch& a, int tile, const float2* sh) {
+// A tile cut into parts (consecutive exposure ranges) on different CTAs
+// of a split launch: part q > 0 waits (bounded) for the tile's flag to
+// reach q, starts from the accumulator part q - 1 left in its CTA's slot,
+// and, unless it is the last part, leaves its own in this CTA's slot and
+// raises the flag to q + 1; the last part finishes the tile and resets the
+// flag. The exposures are summed in the order a whole-tile CTA sums them
+// (the same bits). A wait that gives up sets the timeout bit of the error
+// word and starts from zero.
+__device__ void adjoint_publish_part(const FftLaunch& a, int tile, const float2* sh, int q) {
   float2* slot = a.partials + (long long)blockIdx.x * kFBuf;
   for (int e = threadIdx.x; e < kFBuf; e += blockDim.x) slot[e] = sh[e];
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) st_release_gpu(a.counters + tile, 1);
+  if (threadIdx.x == 0) st_release_gpu(a.counters + tile, q + 1);
 }
 
-__device__ void adjoint_resume_tail(const FftLaunch& a, int tile, float2* sh, int head_cta) {
+__device__ void adjoint_resume_part(const FftLaunch& a, int tile, float2* sh, int q, int prev_cta,
+                                    bool last) {
   __shared__ int ok;
   if (threadIdx.x == 0) {
     unsigned i = 0;
-    while (i < kPartPolls && ld_acquire_gpu(a.counters + tile) == 0) {
+    while (i < kPartPolls && ld_acquire_gpu(a.counters + tile) < q) {
       __nanosleep(200);
       ++i;
     }
     ok = i < kPartPolls;
-    if (ok)
-      a.counters[tile] = 0;  // ready for the next launch
-    else
+    if (!ok)
       atomicOr(a.err, kErrTimeout);
+    else if (last)
+      a.counters[tile] = 0;  // ready for the next launch
   }
   __syncthreads();
-  const float2* slot = a.partials + (long long)head_cta * kFBuf;
+  const float2* slot = a.partials + (long long)prev_cta * kFBuf;
   for (int e = threadIdx.x; e < kFBuf; e += blockDim.x)
     sh[e] = ok ? __ldcg(slot + e) : make_float2(0.f, 0.f);
 }
@@ -951,13 +953,12 @@ __device__ void adjoint_resume_tail(const FftLaunch& a, int tile, float2* sh, in
 // barrier. r = 1 Gaussian: one accumulator in shared memory. Otherwise the
 // accumulators live in the tile's scratch: R2 for Den, and for Student-t R2
 // more for N' (the w2 planes, transformed the same way). A split launch
-// (r = 1 Gaussian) runs the sources [k_begin, k_end) of a cut tile: part 1
-// the head (published, no update), part 2 the tail (resumed, then the
-// update, its head computed by CTA head_cta); part 0 is the whole tile.
-enum { kWhole = 0, kHead = 1, kTail = 2 };
+// (r = 1 Gaussian) runs part q of a cut tile: the sources [k_begin, k_end),
+// resumed from CTA prev_cta's part q - 1 (prev_cta < 0: from zero), then
+// the update if it is the last part, else published for part q + 1.
 __device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int tx, int tile,
                                  float2* fsm, const TwTab& T, int k_begin = 0, int k_end = -1,
-                                 int part = kWhole, int head_cta = 0) {
+                                 int q = 0, int prev_cta = -1, bool last = true) {
   float2* sh = fsm;
   float2* wk = fsm + kFBuf;
   // the w regions arrive straight in the packed layout, alternating between
@@ -980,8 +981,8 @@ __device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int
   };
   SpecRegs kr;
   if (in_smem) {
-    if (part == kTail)
-      adjoint_resume_tail(a, tile, sh, head_cta);
+    if (prev_cta >= 0)
+      adjoint_resume_part(a, tile, sh, q, prev_cta, last);
     else
       for (int e = threadIdx.x; e < kFBuf; e += blockDim.x) sh[e] = make_float2(0.f, 0.f);
     load_spec_cols(kr, a.spec + (long long)k_begin * per);
@@ -1007,8 +1008,8 @@ __device__ void fft_adjoint_tile(const Shape& s, const FftLaunch& a, int ty, int
   }
   if (in_smem) {
     __syncthreads();  // the last accumulation is complete
-    if (part == kHead) {
-      adjoint_publish_head(a, tile, sh);
+    if (!last) {
+      adjoint_publish_part(a, tile, sh, q);
     } else {
       c2r_2d(sh, T, 0, (B + 1) / 2);  // Den is read at rows [0, B)
       update_phase(sh, nullptr, a, g, 0, i0, j0, B);
@@ -1039,50 +1040,58 @@ __global__ void __launch_bounds__(kFThreads, 1)
 }
 
 // Split forms (r = 1 Gaussian, at least as many tiles as CTAs): P =
-// a.split_ctas persistent CTAs, CTA b taking the (tile, exposure) units
-// [b U / P, (b+1) U / P) of the U = tiles x n, tile-major, so that every
-// CTA does the same work and the last wave of whole tiles leaves no SM
-// idle. A range holds at least n units, so it cuts at most its first and
-// its last tile. The forward pass recomputes x^ for a tile it shares.
+// a.split_ctas persistent CTAs. The Wf = tiles / P whole waves run as one
+// CTA per tile would (CTA b takes the tiles b + P i, neighbours side by
+// side, so their overlapping regions share the L2); the R = tiles - Wf P
+// tiles of the last, partial wave are spread so that no SM idles through it.
+// Forward: the R n (tile, exposure) units of the last wave in equal ranges
+// over all CTAs (tile-major; a CTA recomputes x^ for each tile it touches).
 __global__ void __launch_bounds__(kFThreads, 1)
     fft_forward_split_kernel(const Shape s, const FftLaunch a, int gxt, int tiles) {
   extern __shared__ float2 fsm[];
   __shared__ TwTab T;
   init_twiddles(T);
-  const int P = a.split_ctas, n = s.n;
-  const long long U = (long long)tiles * n;
-  const long long u_end = split_start(U, P, blockIdx.x + 1);
-  for (long long u = split_start(U, P, blockIdx.x); u < u_end;) {
-    const int tile = (int)(u / n), t0 = (int)(u % n);
+  const int P = a.split_ctas, n = s.n, b = blockIdx.x;
+  const int Wf = tiles / P, R = tiles - Wf * P;
+  for (int i = 0; i < Wf; ++i) {
+    const int tile = b + P * i;
+    fft_forward_tile(s, a, tile / gxt, tile % gxt, tile, fsm, T, 0, n);
+  }
+  const long long U = (long long)R * n, base = (long long)Wf * P * n;
+  const long long u_end = split_start(U, P, b + 1);
+  for (long long u = split_start(U, P, b); u < u_end;) {
+    const int tile = (int)((base + u) / n), t0 = (int)((base + u) % n);
     const int t1 = (int)min((long long)n, t0 + (u_end - u));
     fft_forward_tile(s, a, tile / gxt, tile % gxt, tile, fsm, T, t0, t1);
     u += t1 - t0;
   }
 }
 
-// The adjoint: the head of the last tile first, then the whole tiles, then
-// the tail of the first tile, whose head the previous CTA ran first.
+// Adjoint: last-wave tile j is cut into k = min(n, P / R) parts of
+// consecutive exposures, part q on CTA q R + j, which runs it after
+// q Wf / (k - 1) of its whole tiles (part 0 first, part k - 1 last), so
+// each part finds its predecessor done waves earlier and the last wave
+// costs 1 / k of a tile.
 __global__ void __launch_bounds__(kFThreads, 1)
     fft_adjoint_split_kernel(const Shape s, const FftLaunch a, int gxt, int tiles) {
   extern __shared__ float2 fsm[];
   __shared__ TwTab T;
   init_twiddles(T);
-  const int P = a.split_ctas, n = s.n;
-  const long long U = (long long)tiles * n;
-  const long long u0 = split_start(U, P, blockIdx.x), u1 = split_start(U, P, blockIdx.x + 1);
-  const int first = (int)(u0 / n), last = (int)((u1 - 1) / n);
-  const int head_k = (int)(u1 % n), tail_k = (int)(u0 % n);
-  const int w0 = tail_k != 0 ? first + 1 : first, w1 = head_k != 0 ? last : last + 1;
-  // items: [head of last], whole tiles w0 .. w1-1, [tail of first]
-  const int nh = head_k != 0, nw = w1 - w0, nt = tail_k != 0;
-  for (int i = 0; i < nh + nw + nt; ++i) {
-    int tile = first, k0 = tail_k, k1 = n, part = kTail;
-    if (i < nh) {
-      tile = last, k0 = 0, k1 = head_k, part = kHead;
-    } else if (i < nh + nw) {
-      tile = w0 + i - nh, k0 = 0, part = kWhole;
+  const int P = a.split_ctas, n = s.n, b = blockIdx.x;
+  const int Wf = tiles / P, R = tiles - Wf * P;
+  const int k = R > 0 ? max(1, min(n, P / R)) : 0;
+  const int has = b < k * R, q = has ? b / R : 0, j = has ? b % R : 0;
+  const int pos = !has ? -1 : (k == 1 ? Wf : q * Wf / (k - 1));  // whole tiles before the part
+  for (int it = 0; it < Wf + has; ++it) {
+    int tile, k0 = 0, k1 = n, qq = 0, prev = -1;
+    bool last = true;
+    if (has && it == pos) {
+      tile = Wf * P + j, k0 = q * n / k, k1 = (q + 1) * n / k, qq = q;
+      prev = q > 0 ? (q - 1) * R + j : -1, last = q == k - 1;
+    } else {
+      tile = b + P * (it - (has && it > pos));
     }
-    fft_adjoint_tile(s, a, tile / gxt, tile % gxt, tile, fsm, T, k0, k1, part, blockIdx.x - 1);
+    fft_adjoint_tile(s, a, tile / gxt, tile % gxt, tile, fsm, T, k0, k1, qq, prev, last);
   }
 }
 
