@@ -577,6 +577,23 @@ __device__ void c2r_2d_product(const float2* src, float2* dst, const SpecRegs& k
   c2r_rows(dst, T, k0, 64, false);
 }
 
+// values of the tile pixels (P, Q) and (P, Q + 1) after c2r_2d (unscaled),
+// Q even: one 16-byte load of the two packed row pairs' entries
+__device__ __forceinline__ float2 tile_pair_at(const float2* buf, int P, int Q) {
+  const float4 v = *reinterpret_cast<const float4*>(buf + (P >> 1) * 2 * kFP + Q);
+  return (P & 1) ? make_float2(v.y, v.w) : make_float2(v.x, v.z);
+}
+
+// Visits (p, q) of a B x B output region by column pairs, q = 0, 2, ..., warp
+// w taking the rows w, w + 16, ... and its lanes the pairs lane, lane + 32,
+// ... (B is even)
+template <class F>
+__device__ __forceinline__ void for_region_pairs(int B, F&& f) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int p = warp; p < B; p += kWarps)
+    for (int c = lane; c < B / 2; c += 32) f(p, 2 * c);
+}
+
 // value of tile pixel (P, Q) after c2r_2d (unscaled)
 __device__ __forceinline__ float tile_at(const float2* buf, int P, int Q) {
   const float2 v = buf[(P >> 1) * 2 * kFP + Q];
@@ -587,6 +604,11 @@ __device__ __forceinline__ float tile_at(const float2* buf, int P, int Q) {
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(src) : "memory");
+}
+// asynchronous 8-byte global -> shared copy (both addresses 8-byte aligned)
+__device__ __forceinline__ void cp_async8(float* dst, const float* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -761,13 +783,16 @@ __device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int
   }
   for (int t = t_begin; t < t_end; ++t) {
     // u of this exposure (B x B, row-major in stg) arrives during the
-    // inverse transform
+    // inverse transform, by column pairs: the border (2 hc), the pitch (a
+    // multiple of 8) and the tile origins (multiples of B) are even, so a
+    // pair is 8-byte aligned; the last pair of an edge tile may read column
+    // W, inside the padded row (pitch > border + W) and never used
     const long long tplane = (long long)t * g.plane;
     {
       const float* ut = a.u + tplane + (long long)(g.B + i0) * g.P + g.B + j0;
       const int pmax = min(B, g.H - i0), qmax = min(B, g.W - j0);
-      for_region(B, [&](int p, int q) {
-        if (p < pmax && q < qmax) cp_async4(stg + p * B + q, ut + (long long)p * g.P + q);
+      for_region_pairs(B, [&](int p, int q) {
+        if (p < pmax && q < qmax) cp_async8(stg + p * B + q, ut + (long long)p * g.P + q);
       });
     }
     cp_async_commit();
@@ -786,22 +811,46 @@ __device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int
       const float nu1 = a.nu + 1.f;
       const long long base = tplane + (long long)(g.B + i0) * g.P + g.B + j0;
       const int pmax = min(B, g.H - i0), qmax = min(B, g.W - j0);
-      for_region(B, [&](int p, int q) {
+      for_region_pairs(B, [&](int p, int q) {
         if (p < pmax && q < qmax) {
           const long long gi = base + (long long)p * g.P + q;
-          const float z = tile_at(wk, p + 2 * hc, q + 2 * hc) * kFScale;
-          const float uv = stg[p * B + q], yv = a.y[gi], d = yv - z;
-          const float us = uv > 0.f ? uv * nu1 / fmaf(uv * d, d, a.nu) : 0.f;
-          a.w[gi] = us * z;
-          a.w2[gi] = us * yv;
+          const bool two = q + 1 < qmax;
+          const float2 zz = tile_pair_at(wk, p + 2 * hc, q + 2 * hc);
+          const float2 uu = *reinterpret_cast<const float2*>(stg + p * B + q);
+          const float2 yy = two ? *reinterpret_cast<const float2*>(a.y + gi)
+                                : make_float2(a.y[gi], 0.f);
+          float wv[2], w2v[2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float z = (e ? zz.y : zz.x) * kFScale, uv = e ? uu.y : uu.x;
+            const float yv = e ? yy.y : yy.x, d = yv - z;
+            const float us = uv > 0.f ? uv * nu1 / fmaf(uv * d, d, a.nu) : 0.f;
+            wv[e] = us * z;
+            w2v[e] = us * yv;
+          }
+          if (two) {
+            *reinterpret_cast<float2*>(a.w + gi) = make_float2(wv[0], wv[1]);
+            *reinterpret_cast<float2*>(a.w2 + gi) = make_float2(w2v[0], w2v[1]);
+          } else {
+            a.w[gi] = wv[0];
+            a.w2[gi] = w2v[0];
+          }
         }
       });
     } else {
       float* wt = a.w + tplane + (long long)(g.B + i0) * g.P + g.B + j0;
       const int pmax = min(B, g.H - i0), qmax = min(B, g.W - j0);
-      for_region(B, [&](int p, int q) {
-        if (p < pmax && q < qmax)
-          wt[(long long)p * g.P + q] = stg[p * B + q] * (tile_at(wk, p + 2 * hc, q + 2 * hc) * kFScale);
+      for_region_pairs(B, [&](int p, int q) {
+        if (p < pmax && q < qmax) {
+          const float2 zz = tile_pair_at(wk, p + 2 * hc, q + 2 * hc);
+          const float2 uu = *reinterpret_cast<const float2*>(stg + p * B + q);
+          const float w0 = uu.x * (zz.x * kFScale), w1 = uu.y * (zz.y * kFScale);
+          float* o = wt + (long long)p * g.P + q;
+          if (q + 1 < qmax)
+            *reinterpret_cast<float2*>(o) = make_float2(w0, w1);
+          else
+            o[0] = w0;
+        }
       });
     }
     __syncthreads();
