@@ -525,6 +525,46 @@ __device__ void c2r_rows(float2* buf, const TwTab& T, int k0 = 0, int k1 = 64, b
   if (sync) __syncthreads();
 }
 
+// merge and inverse row FFTs of the J row pairs k[0..J), the results handed
+// to f(k, column, value) (value: real part row 2k, imaginary part row
+// 2k + 1; unscaled) instead of stored
+template <int J, class F>
+__device__ __forceinline__ void rows_inverse_apply(float2* buf, const int (&k)[J], const TwTab& T,
+                                                   int lane, F& f) {
+  float2 v[J][4];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    float2* r = buf + 2 * k[j] * kFP;
+    merge_pair(r, lane);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[j][q] = r[rsw(32 * q + lane)];
+  }
+  warp_ifft_dit<J>(v, T, lane);
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) f(k[j], 32 * q + lane, v[j][q]);
+}
+
+// c2r_rows with the results handed to f (see rows_inverse_apply); no
+// closing barrier
+template <class F>
+__device__ void c2r_rows_apply(float2* buf, const TwTab& T, int k0, int k1, F& f) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = k0 + warp; k < k1; k += 3 * kWarps) {
+    if (k + 2 * kWarps < k1) {
+      const int kk[3] = {k, k + kWarps, k + 2 * kWarps};
+      rows_inverse_apply<3>(buf, kk, T, lane, f);
+    } else if (k + kWarps < k1) {
+      const int kk[2] = {k, k + kWarps};
+      rows_inverse_apply<2>(buf, kk, T, lane, f);
+    } else {
+      const int kk[1] = {k};
+      rows_inverse_apply<1>(buf, kk, T, lane, f);
+    }
+  }
+}
+
 // inverse real 2D transform in place (unscaled); rows of the pairs [k0, k1)
 __device__ void c2r_2d(float2* buf, const TwTab& T, int k0 = 0, int k1 = 64) {
   all_columns<true>(buf, T);
@@ -563,18 +603,17 @@ __device__ __forceinline__ void columns_product(const float2* src, float2* dst,
     }
 }
 
-// dst = C2R(src . k^) (unscaled), rows of the pairs [k0, 64); src is left
-// intact; no closing barrier (the caller's next barrier orders it)
-__device__ void c2r_2d_product(const float2* src, float2* dst, const SpecRegs& kr,
-                               const TwTab& T, int k0) {
+// the column pass of dst = C2R(src . k^): dst's columns = IFFT(src . k^)
+// along the column; src is left intact; no closing barrier (the rows,
+// c2r_rows_apply, follow the caller's barrier)
+__device__ void columns_product_pass(const float2* src, float2* dst, const SpecRegs& kr,
+                                     const TwTab& T) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0)
     columns_product<true>(src, dst, kr, 0, T, warp, lane);
   else
     columns_product<false>(src, dst, kr, 0, T, warp, lane);
   columns_product<false>(src, dst, kr, 2, T, warp, lane);
-  __syncthreads();
-  c2r_rows(dst, T, k0, 64, false);
 }
 
 // values of the tile pixels (P, Q) and (P, Q + 1) after c2r_2d (unscaled),
@@ -699,7 +738,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
   }
 }
 
-// column slot m of c2r_2d_phase_sum (DN: slot 0, columns 0 and 64)
+// column slot m of phase_sum_columns (DN: slot 0, columns 0 and 64)
 template <bool DN>
 __device__ __forceinline__ void phase_sum_column(const float2* xs, const float2* kt, int R2,
                                                  float2* dst, const TwTab& T, int m, int lane) {
@@ -732,11 +771,12 @@ __device__ __forceinline__ void phase_sum_column(const float2* xs, const float2*
   }
 }
 
-// r > 1: dst = C2R(sum_phi x^_phi . k^_phi) with both spectra read from
-// global memory (x^ from this tile's scratch, L2-resident), column by
-// column; no closing barrier (the caller's next barrier orders it)
-__device__ void c2r_2d_phase_sum(const float2* xs, const float2* kt, int R2, float2* dst,
-                                 const TwTab& T, int k0) {
+// r > 1: the column pass of dst = C2R(sum_phi x^_phi . k^_phi) with both
+// spectra read from global memory (x^ from this tile's scratch,
+// L2-resident), column by column; no closing barrier (the rows,
+// c2r_rows_apply, follow the caller's barrier)
+__device__ void phase_sum_columns(const float2* xs, const float2* kt, int R2, float2* dst,
+                                  const TwTab& T) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int m = warp; m < 64; m += kWarps) {  // column slots; slot 0: columns 0 and 64
     if (m == 0)
@@ -744,13 +784,13 @@ __device__ void c2r_2d_phase_sum(const float2* xs, const float2* kt, int R2, flo
     else
       phase_sum_column<false>(xs, kt, R2, dst, T, m, lane);
   }
-  __syncthreads();
-  c2r_rows(dst, T, k0, 64, false);
 }
 
 // the forward pass of one tile (tile index `tile` = ty gx + tx of its job)
 // for the exposures [t_begin, t_end); starts and ends at a CTA barrier, so
-// a persistent CTA can run many
+// a persistent CTA can run many. STUDENT = false compiles the Gaussian
+// weights only (the split launch, which never runs the heavy-tailed model).
+template <bool STUDENT = true>
 __device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int tx, int tile,
                                  float2* fsm, const TwTab& T, int t_begin, int t_end) {
   float2* xh = fsm;
@@ -796,21 +836,25 @@ __device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int
       });
     }
     cp_async_commit();
-    if (R2 == 1) {
-      c2r_2d_product(xh, wk, kr, T, hc);  // z is read at rows [2 hc, 128)
-      // the next spectrum loads during the epilogue and the next column pass
-      if (t + 1 < t_end) load_spec_cols(kr, a.spec + (long long)(t + 1) * per);
-    } else {
-      c2r_2d_phase_sum(xs, a.spec + (long long)t * R2 * per, R2, wk, T, hc);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    if (a.nu > 0.f) {
+    if (R2 == 1)
+      columns_product_pass(xh, wk, kr, T);
+    else
+      phase_sum_columns(xs, a.spec + (long long)t * R2 * per, R2, wk, T);
+    const int pmax = min(B, g.H - i0), qmax = min(B, g.W - j0);
+    const long long base = tplane + (long long)(g.B + i0) * g.P + g.B + j0;
+    if (STUDENT && a.nu > 0.f) {
       // heavy-tailed weights u' = u (nu+1) / (nu + u (y - z)^2): both u' z
-      // (denominator) and u' y (numerator) go to planes
+      // (denominator) and u' y (numerator) go to planes. The rows are stored
+      // (pairs [hc, 64): z at rows [2 hc, 128)) and the weights computed
+      // after a barrier, by column pairs (the y loads of a fused form stall
+      // the row pass)
+      __syncthreads();
+      c2r_rows(wk, T, hc, 64, false);
+      // the next spectrum loads during the epilogue and the next column pass
+      if (R2 == 1 && t + 1 < t_end) load_spec_cols(kr, a.spec + (long long)(t + 1) * per);
+      cp_async_wait_all();
+      __syncthreads();
       const float nu1 = a.nu + 1.f;
-      const long long base = tplane + (long long)(g.B + i0) * g.P + g.B + j0;
-      const int pmax = min(B, g.H - i0), qmax = min(B, g.W - j0);
       for_region_pairs(B, [&](int p, int q) {
         if (p < pmax && q < qmax) {
           const long long gi = base + (long long)p * g.P + q;
@@ -838,22 +882,26 @@ __device__ void fft_forward_tile(const Shape& s, const FftLaunch& a, int ty, int
         }
       });
     } else {
-      float* wt = a.w + tplane + (long long)(g.B + i0) * g.P + g.B + j0;
-      const int pmax = min(B, g.H - i0), qmax = min(B, g.W - j0);
-      for_region_pairs(B, [&](int p, int q) {
-        if (p < pmax && q < qmax) {
-          const float2 zz = tile_pair_at(wk, p + 2 * hc, q + 2 * hc);
-          const float2 uu = *reinterpret_cast<const float2*>(stg + p * B + q);
-          const float w0 = uu.x * (zz.x * kFScale), w1 = uu.y * (zz.y * kFScale);
-          float* o = wt + (long long)p * g.P + q;
-          if (q + 1 < qmax)
-            *reinterpret_cast<float2*>(o) = make_float2(w0, w1);
-          else
-            o[0] = w0;
+      // this warp's columns are done: the next spectrum loads during the rows
+      if (R2 == 1 && t + 1 < t_end) load_spec_cols(kr, a.spec + (long long)(t + 1) * per);
+      cp_async_wait_all();
+      __syncthreads();  // every column done, u landed
+      // the inverse rows of the pairs [hc, 64) (z at rows [2 hc, 128)) go
+      // straight from registers to the w plane: z(p, q) is row 2k + e - 2 hc,
+      // column c - 2 hc of the value (k, c) (e = 0 real part, 1 imaginary)
+      float* wt = a.w + base;
+      auto out = [&](int k, int c, float2 v) {
+        const int q = c - 2 * hc;
+        if (q < 0 || q >= qmax) return;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int p = 2 * k + e - 2 * hc;
+          if (p < pmax) wt[(long long)p * g.P + q] = stg[p * B + q] * ((e ? v.y : v.x) * kFScale);
         }
-      });
+      };
+      c2r_rows_apply(wk, T, hc, 64, out);
     }
-    __syncthreads();
+    __syncthreads();  // wk and stg are free for the next exposure
   }
 }
 
@@ -1104,14 +1152,14 @@ __global__ void __launch_bounds__(kFThreads, 1)
   const int Wf = tiles / P, R = tiles - Wf * P;
   for (int i = 0; i < Wf; ++i) {
     const int tile = b + P * i;
-    fft_forward_tile(s, a, tile / gxt, tile % gxt, tile, fsm, T, 0, n);
+    fft_forward_tile<false>(s, a, tile / gxt, tile % gxt, tile, fsm, T, 0, n);
   }
   const long long U = (long long)R * n, base = (long long)Wf * P * n;
   const long long u_end = split_start(U, P, b + 1);
   for (long long u = split_start(U, P, b); u < u_end;) {
     const int tile = (int)((base + u) / n), t0 = (int)((base + u) % n);
     const int t1 = (int)min((long long)n, t0 + (u_end - u));
-    fft_forward_tile(s, a, tile / gxt, tile % gxt, tile, fsm, T, t0, t1);
+    fft_forward_tile<false>(s, a, tile / gxt, tile % gxt, tile, fsm, T, t0, t1);
     u += t1 - t0;
   }
 }
