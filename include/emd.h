@@ -123,7 +123,10 @@ int emd_set_frames(emd_ctx *ctx, const float *y, const float *v,
 int emd_set_x(emd_ctx *ctx, const float *x0);
 
 /* Run k >= 0 iterations of Eq. (2) on the current iterate (stream-ordered,
- * asynchronous). EMD_ETIMEOUT if a bounded device wait gave up. */
+ * asynchronous). A bounded device-side wait that gives up (the FP32
+ * halo-exchange kernel's dependency waits; the FFT form's split launch,
+ * where part of a tile waits for the part before it) sets the context's
+ * error word: the next emd_get_x or emd_loglik returns EMD_ETIMEOUT. */
 int emd_iterate(emd_ctx *ctx, int k);
 
 /* Streaming (frame-by-frame) EM, the order-dependent alternative the paper

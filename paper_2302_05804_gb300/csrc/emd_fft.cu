@@ -36,7 +36,11 @@
 // Per iteration: fft_forward_kernel (per tile: x^ once, then for each
 // exposure z = IFFT(x^ k_t^), w_t = u_t z written to a plane) and
 // fft_adjoint_kernel (per tile: sum_t FFT(w_t) conj(k_t^), one inverse
-// transform, the update of Eq. (2)).
+// transform, the update of Eq. (2)), one CTA per tile; or, for r = 1
+// Gaussian with at least as many tiles as SMs, their split forms
+// (fft_forward_split_kernel, fft_adjoint_split_kernel: one persistent CTA
+// per SM, whole waves of tiles, then the last wave's tiles cut into
+// exposure ranges across all CTAs).
 #include <math.h>
 
 #include "emd_internal.cuh"
