@@ -126,7 +126,9 @@ int emd_set_x(emd_ctx *ctx, const float *x0);
  * asynchronous). A bounded device-side wait that gives up (the FP32
  * halo-exchange kernel's dependency waits; the FFT form's split launch,
  * where part of a tile waits for the part before it) sets the context's
- * error word: the next emd_get_x or emd_loglik returns EMD_ETIMEOUT. */
+ * error word: the next emd_get_x or emd_loglik returns EMD_ETIMEOUT, and the
+ * iterate is then not valid (set it again with emd_set_x); the context's
+ * wait state is cleared for the next iterations. */
 int emd_iterate(emd_ctx *ctx, int k);
 
 /* Streaming (frame-by-frame) EM, the order-dependent alternative the paper

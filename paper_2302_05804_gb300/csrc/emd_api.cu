@@ -105,7 +105,8 @@ struct emd_ctx {
   float* fft_w2 = nullptr;
   float2* fft_scratch = nullptr;
   float2* fft_partials = nullptr;  // split launch (r = 1 Gaussian): partial accumulators
-  int* fft_counters = nullptr;     // and per-tile arrival counts
+  int* fft_counters = nullptr;     // and per-tile flags
+  size_t fft_counters_bytes = 0;
   int fft_split_ctas = 0;          // persistent CTAs of the split launch (one per SM)
   int fft_bound = -1;              // noise model the pointers are laid out for (-1: none)
   bool fft_ready = false;
@@ -185,6 +186,9 @@ int check_device_error(emd_ctx* c) {
   CK(cudaStreamSynchronize(c->st));
   if (h) CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
   if (h & emd::kErrTimeout) {
+    // a split FFT launch whose wait gave up may have left tile flags raised:
+    // clear them so that the next launch starts from a clean state
+    if (c->fft_counters) CK(cudaMemsetAsync(c->fft_counters, 0, c->fft_counters_bytes, c->st));
     set_err("a bounded device-side wait gave up");
     return EMD_ETIMEOUT;
   }
@@ -418,9 +422,9 @@ int ensure_fft_arena(emd_ctx* c) {
   c->fft_counters = parts ? reinterpret_cast<int*>(c->fft_arena + emd::fft_counters_offset(
                                                                       c->s, student, c->fft_split_ctas))
                           : nullptr;
-  if (c->fft_counters)
-    CK(cudaMemsetAsync(c->fft_counters, 0,
-                       need - emd::fft_counters_offset(c->s, student, c->fft_split_ctas), c->st));
+  c->fft_counters_bytes =
+      c->fft_counters ? need - emd::fft_counters_offset(c->s, student, c->fft_split_ctas) : 0;
+  if (c->fft_counters) CK(cudaMemsetAsync(c->fft_counters, 0, c->fft_counters_bytes, c->st));
   c->fft_bound = (int)student;
   c->fft_ready = false;
   return EMD_OK;
